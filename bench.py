@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the state-vector hot path on GB300.
+
+Default workload (the headline metric, one JSON line on stdout):
+  30-qubit fused layered circuit, complex64: 20 layers of Haar-angle U3 on
+  every qubit plus CZ on even then odd neighbour pairs (1180 gates), fused into
+  <= 5-qubit blocks.  One step = |0..0> initialisation + the whole circuit +
+  the per-qubit <Z> read-out, on a state (8 GiB) far larger than L2.
+
+value = effective HBM GB/s = algorithmic bytes of the step's kernels (each pass
+over the state reads and writes 2^n amplitudes; initialisation writes them once;
+the read-out reads them once) / device time of the step, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: replicas only (each rank simulates its own copy of the workload; no
+collective on the data path).  --impl reference times the CPU oracle on the
+host cores instead, on bounded samples of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gate-apply HBM GB/s (% peak) at 30q c64; adjoint grads/s; serving req/s + p99"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--layers", type=int, default=20)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--fuse", type=int, default=5)
+    ap.add_argument("--block-mode", type=int, default=0)
+    ap.add_argument("--ops-per-pass", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-gates", type=int, default=0, help="oracle sample size (0 = auto)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_indices):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for row in csv.reader(fh):
+                if len(row) < 9:
+                    continue
+                try:
+                    idx = int(row[0])
+                except ValueError:
+                    continue
+                if gpu_indices is not None and idx not in gpu_indices:
+                    continue
+                try:
+                    sm.append(float(row[1]))
+                    smax.append(float(row[2]))
+                except ValueError:
+                    pass
+                for nm, v in zip(names, row[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from workloads import fused_layered_u3_cz
+    n = args.n
+    gates = fused_layered_u3_cz(n, args.layers, seed=0)
+    sample = args.cpu_sample_gates or (4 if n >= 28 else 59)
+    psi = np.zeros(2 ** n, dtype=np.complex128)
+    psi[0] = 1.0
+    t_steps = []
+    for s in range(args.warmup + args.steps):
+        g = gates[(s * sample) % len(gates):][:sample]
+        t0 = time.perf_counter()
+        psi = _oracle_inplace(oracle, n, g, psi)
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            t_steps.append(t1 - t0)
+    t = sum(t_steps)
+    # the oracle makes one pass per gate over a complex128 state (read + write)
+    bytes_ = args.steps * sample * 2 * (2 ** n) * 16
+    value = bytes_ / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers" % (n, args.layers), "n_qubits": n,
+                       "gates_per_step": sample},
+            "gates_per_s": args.steps * sample / t,
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.n_threads(), "kind": "oracle",
+                             "sample": "%d consecutive gates of the %d-gate circuit per step on a %d-qubit "
+                                       "complex128 state, one pass per gate" % (sample, len(gates), n)},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_inplace(oracle, n, gates, psi):
+    import ctypes
+    pk = oracle._Packed(gates, None)
+    rc = oracle.lib().og_apply_circuit(psi.ctypes.data_as(ctypes.c_void_p), n, pk.arr, pk.n)
+    assert rc == 0
+    return psi
+
+
+def cpu_baseline_sample(n, gates, sample_gates, plan_bytes_per_gate_gpu):
+    """The oracle on the host cores: a bounded sample of the same workload."""
+    import numpy as np
+
+    import oracle
+    avail = _mem_available_gb()
+    if avail is not None and avail < 2.5 * (2 ** n) * 16 / 1e9 + 4:
+        return {"value": None, "unit": "GB/s", "cores": oracle.n_threads(), "kind": "oracle",
+                "sample": "skipped: host has %.0f GB available, the %d-qubit complex128 oracle needs %.0f GB"
+                          % (avail, n, (2 ** n) * 16 / 1e9)}
+    psi = np.zeros(2 ** n, dtype=np.complex128)
+    psi[0] = 1.0
+    _oracle_inplace(oracle, n, gates[:1], psi)  # touch pages, warm threads
+    t0 = time.perf_counter()
+    _oracle_inplace(oracle, n, gates[1:1 + sample_gates], psi)
+    t = time.perf_counter() - t0
+    bytes_ = sample_gates * 2 * (2 ** n) * 16
+    return {"value": bytes_ / t / 1e9, "unit": "GB/s", "cores": oracle.n_threads(), "kind": "oracle",
+            "gates_per_s": sample_gates / t,
+            "sample": "gates 1..%d of the %d-gate circuit on a %d-qubit complex128 state, one pass per gate "
+                      "(%.1f s)" % (sample_gates, len(gates), n, t)}
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return None
+
+
+def read_traffic(kernel: str, stamp: str):
+    """Per-launch DRAM traffic from the committed ncu summary, when it was taken
+    on the current sources (the summary records the source stamp)."""
+    path = os.path.join(ROOT, "profiles", "%s.md" % kernel)
+    if not os.path.exists(path):
+        return None
+    tr, st = None, None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("traffic_bytes_per_launch_full_size:"):
+                tr = float(line.split(":", 1)[1])
+            if line.startswith("source_stamp:"):
+                st = line.split(":", 1)[1].strip()
+    return tr if (tr is not None and st == stamp) else None
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2608_09733_gb300 import build as _build
+    import paper_2608_09733_gb300 as sv
+    from workloads import fused_layered_u3_cz
+
+    _build.build()
+    sv.load()
+    stamp = _build._stamp()
+    n, dt = args.n, (sv.SV_C64 if args.dtype == "c64" else sv.SV_C128)
+    amp = 8 if dt == sv.SV_C64 else 16
+    tdt = torch.complex64 if dt == sv.SV_C64 else torch.complex128
+    gates = fused_layered_u3_cz(n, args.layers, seed=0)
+    G = sv.Gates(gates)
+    nblocks, npasses, _ = sv.sv_plan_info(n, dt, G, fuse_max_k=args.fuse, block_mode=args.block_mode,
+                                          ops_per_pass=args.ops_per_pass)
+    state = torch.empty(2 ** n, dtype=tdt, device="cuda")
+    zout = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sv.sv_init_basis(state, 0)
+        sv.sv_apply_circuit_ex(state, G, None, fuse_max_k=args.fuse, block_mode=args.block_mode,
+                               ops_per_pass=args.ops_per_pass)
+        sv.sv_expect_z_all(state, out=zout)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sv.sv_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sv.sv_profile_read(reset=True)
+    sv.sv_profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop(None) if rank == 0 else None
+
+    bytes_step = (2 * npasses + 2) * (2 ** n) * amp  # passes r+w, init write, read-out read
+    value = ws * args.steps * bytes_step / (ms / 1e3) / 1e9
+    gates_per_s = ws * args.steps * len(gates) / (ms / 1e3)
+    peaks, peak_src = measured_peaks()
+    sw = prof.get("sweep", {"launches": 0, "total_ms": float("nan"), "bytes": 0.0})
+    launches = sum(v["launches"] for v in prof.values()) + args.steps  # + init kernel per step
+    sweep_gbs = sw["bytes"] / (sw["total_ms"] / 1e3) / 1e9 if sw["launches"] else None
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    traffic = read_traffic("sweep_%dq_%s" % (n, args.dtype), stamp)
+
+    # e2e: the same workload through the host-buffer entry point (H2D/D2H inside)
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(2 ** n, dtype=tdt).pin_memory()
+        host_state = pinned.numpy()
+        sv.sv_run_host(n, dt, G, fuse_max_k=args.fuse, state_out=host_state)  # warm the buffers
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            sv.sv_run_host(n, dt, G, fuse_max_k=args.fuse, state_out=host_state)
+        te = time.perf_counter() - t0
+        e2e = {"value": ws * e2e_steps * bytes_step / te / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": len(gates) * 80, "d2h_bytes_per_step": (2 ** n) * amp + 8 * (n + 1),
+               "gates_per_s": ws * e2e_steps * len(gates) / te}
+        sv.sv_release_scratch()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(n, gates, args.cpu_sample_gates or 24, None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers_%s" % (n, args.layers, args.dtype),
+                       "n_qubits": n, "layers": args.layers, "gates": len(gates), "fuse_max_k": args.fuse,
+                       "block_mode": args.block_mode, "fused_blocks": nblocks, "passes_per_step": npasses,
+                       "l2": "inputs larger than L2 (state %.1f GiB)" % ((2 ** n) * amp / 2 ** 30),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "gates_per_s": gates_per_s,
+            "pct_of_hbm_peak": 100.0 * value / ws / peak,
+            "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": (sweep_gbs / peak) if sweep_gbs else None, "traffic": traffic,
+                         "peak_source": peak_src + " hbm_gbs",
+                         "launches": sw["launches"], "avg_launch_ms": sw["total_ms"] / max(1, sw["launches"])},
+            "kernels": prof,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

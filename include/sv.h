@@ -1,0 +1,248 @@
+/*
+ * sv.h -- C ABI of the GB300 state-vector library (libsv.so).
+ *
+ * The library applies quantum circuits to a dense state vector of 2^n complex
+ * amplitudes held in device memory, evaluates Pauli-string expectations and
+ * computes adjoint gradients.  It is the hot path of the state-vector engine of
+ * "Aicir: A Full-Stack Quantum Circuit Simulator with Ascend NPU Support":
+ * circuits are given as the paper states them (Sec. 4.2: gate family, target
+ * qubits before control qubits, optional control states, parameters bound from
+ * a shared vector), Hamiltonians as weighted Pauli strings (Sec. 4.2, Sec. 4.4).
+ *
+ * Conventions
+ *   - Qubit q is bit q of the basis index (little-endian).  For a k-qubit
+ *     matrix, targets[0] is the least significant bit of its row/column index.
+ *   - Rotations are R_P(theta) = exp(-i theta P / 2) (Sec. 9.1).
+ *   - U3(th, ph, la) = [[cos(th/2), -e^{i la} sin(th/2)],
+ *                       [e^{i ph} sin(th/2), e^{i(ph+la)} cos(th/2)]],
+ *     U2(ph, la) = U3(pi/2, ph, la), P(la) = diag(1, e^{i la}).
+ *   - A state is 2^n amplitudes, interleaved (re, im): float pairs for SV_C64,
+ *     double pairs for SV_C128, 16-byte aligned.  State memory belongs to the
+ *     caller (e.g. a torch tensor); the library never frees it.
+ *   - Gate matrices are built on the host in double precision and narrowed to
+ *     the state's precision only when they are handed to the GPU (Sec. 3.3,
+ *     Sec. 5.2).  Expectations and gradients are accumulated in double.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     return results in host memory synchronize that stream; all others only
+ *     enqueue work on it.
+ *
+ * Errors (Sec. 3.3: unsupported combinations raise at the boundary)
+ *   Every call validates its arguments before it touches the device and
+ *   returns an sv_status; it never aborts the process.  sv_last_error() gives
+ *   a message for the calling thread's last failure.  A failed call leaves
+ *   device memory untouched unless the failure is SV_ERR_CUDA, which reports
+ *   a CUDA runtime error (asynchronous errors surface at the next call that
+ *   synchronizes).
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SV_OK = 0,
+  SV_ERR_INVALID = 1,       /* bad argument: qubit out of range, repeated qubit, bad size ... */
+  SV_ERR_UNSUPPORTED = 2,   /* valid request this library does not run (e.g. no generator) */
+  SV_ERR_OOM = 3,           /* device allocation of library scratch failed */
+  SV_ERR_CUDA = 4,          /* CUDA runtime error */
+  SV_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+  SV_ERR_UNBOUND_PARAM = 6  /* a gate names a parameter slot that was not supplied (Sec. 4.2) */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* Gate families (Sec. 4.2 gate table).  Controlled forms (CX, CZ, CRX, CCX,
+ * controlled phase ...) are the base family with n_controls > 0. */
+typedef enum {
+  SV_GATE_I = 0, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_H,
+  SV_GATE_S, SV_GATE_SDG, SV_GATE_T, SV_GATE_TDG, SV_GATE_SX,
+  SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ, SV_GATE_P, SV_GATE_U2, SV_GATE_U3,
+  SV_GATE_SWAP, SV_GATE_RXX, SV_GATE_RYY, SV_GATE_RZZ,
+  SV_GATE_UNITARY,
+  SV_GATE_COUNT_
+} sv_gate_type;
+
+#define SV_MAX_TARGETS 5
+#define SV_MAX_CONTROLS 5
+#define SV_MAX_QUBITS 34
+
+/* One circuit operation (Sec. 4.2).
+ *   type             sv_gate_type
+ *   n_targets        1 for one-qubit families, 2 for SWAP/RXX/RYY/RZZ,
+ *                    1..5 for SV_GATE_UNITARY
+ *   targets          target qubits; targets[0] = least significant matrix bit
+ *   n_controls       0..5 control qubits, distinct from the targets
+ *   control_zero_mask bit j set: controls[j] enables the gate when it is |0>
+ *                    (the paper's control state 0); clear: when it is |1>
+ *   param_slot[i]    -1: angle i is params[i]; >= 0: angle i is
+ *                    param_values[param_slot[i]] of the call (a shared
+ *                    parameter vector); a slot beyond the supplied vector is
+ *                    SV_ERR_UNBOUND_PARAM
+ *   params           angles: RX/RY/RZ/P/RXX/RYY/RZZ use params[0]; U2 uses
+ *                    (phi, lambda); U3 uses (theta, phi, lambda)
+ *   matrix           SV_GATE_UNITARY only: host pointer to 2^k x 2^k complex
+ *                    entries, row-major, interleaved (re, im) doubles; read
+ *                    during the call only (the caller keeps ownership) */
+typedef struct sv_gate {
+  int32_t type;
+  int32_t n_targets;
+  int32_t targets[SV_MAX_TARGETS];
+  int32_t n_controls;
+  int32_t controls[SV_MAX_CONTROLS];
+  uint32_t control_zero_mask;
+  int32_t param_slot[3];
+  double params[3];
+  const double* matrix;
+} sv_gate;
+
+/* A weighted Pauli string c * P with P|b> = i^{nY} (-1)^{popcount(b & z)}
+ * |b xor x> (Sec. 4.4): bit q of x_mask/z_mask set means X/Z on qubit q, both
+ * set means Y.  Bits at or above n_qubits are SV_ERR_INVALID. */
+typedef struct sv_pauli_term {
+  uint64_t x_mask;
+  uint64_t z_mask;
+  double coeff;
+} sv_pauli_term;
+
+/* Version of this ABI (major * 100 + minor). */
+int sv_version(void);
+
+/* Message for the calling thread's last failed call ("" if none).  The
+ * pointer stays valid until the thread's next failing call. */
+const char* sv_last_error(void);
+
+/* Writes the basis state |basis_index> (Sec. 5.3: a run starts from
+ * |0..0>) into `state` (device, 2^n amplitudes of dtype). */
+sv_status sv_init_basis(void* state, int n_qubits, sv_dtype dtype, uint64_t basis_index, void* stream);
+
+/* Applies the gates, in order, to `state` in place (Sec. 4.3 execution,
+ * Sec. 5.3 gate application).
+ *   state         device, 2^n amplitudes of dtype, modified in place
+ *   gates         host array of n_gates records (read during the call)
+ *   param_values  host array of n_param_values doubles bound to slots (may
+ *                 be NULL when no gate uses a slot)
+ *   fuse_max_k    0: no fusion; 2..5: the paper's fusion (Sec. 4.3 `fuse`,
+ *                 Sec. 9.2): consecutive gates are joined, without changing
+ *                 their order, into blocks of at most fuse_max_k qubits, each
+ *                 applied as one dense 2^k x 2^k matrix; 1 or >5 is invalid.
+ * Whatever the fusion setting, the library runs several consecutive gates or
+ * blocks per pass over HBM when their qubits fit one shared-memory tile; the
+ * order of operations on any qubit is never changed.
+ * Enqueues kernels on `stream`; the call returns before they finish. */
+sv_status sv_apply_circuit(void* state, int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                           const double* param_values, size_t n_param_values, int fuse_max_k, void* stream);
+
+/* Execution options of sv_apply_circuit_ex.
+ *   fuse_max_k      as in sv_apply_circuit (0, or 2..5)
+ *   block_mode      SV_BLOCK_AUTO: a fused block runs as its dense 2^k x 2^k
+ *                   matrix when that takes fewer multiply-adds per amplitude
+ *                   than its gates, else as its gates inside the same pass
+ *                   (identical up to rounding); SV_BLOCK_DENSE: every fused
+ *                   block of two or more gates runs as its dense matrix, the
+ *                   paper's form (Sec. 9.2)
+ *   ops_per_pass    0: as many operations per pass over the state as fit a
+ *                   tile; 1: one operation per pass (the plain per-gate path,
+ *                   used as a baseline); other values cap the count */
+typedef enum { SV_BLOCK_AUTO = 0, SV_BLOCK_DENSE = 1 } sv_block_mode;
+typedef struct sv_exec_opts {
+  int32_t fuse_max_k;
+  int32_t block_mode;
+  int32_t ops_per_pass;
+  int32_t reserved;
+} sv_exec_opts;
+
+/* sv_apply_circuit with explicit options (opts NULL = all zero). */
+sv_status sv_apply_circuit_ex(void* state, int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                              const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
+                              void* stream);
+
+/* Expectation of each term, <psi|P_j|psi> (without c_j), evaluated by the
+ * matrix-free Pauli action (Sec. 4.4), accumulated in double.
+ *   state        device, not modified
+ *   terms        host array of n_terms (1..4096)
+ *   out          n_terms doubles: host memory when out_on_device == 0 (the
+ *                call synchronizes `stream`), else device memory (the call
+ *                only enqueues work)
+ * Uses library-owned device scratch (allocated on first use per stream). */
+sv_status sv_expect(const void* state, int n_qubits, sv_dtype dtype, const sv_pauli_term* terms, size_t n_terms,
+                    double* out, int out_on_device, void* stream);
+
+/* <Z_q> for every qubit q and their sum, in one read-only pass:
+ * <Z_q> = sum_b |psi_b|^2 (-1)^{b_q} (Sec. 5.3 probabilities; Sec. 4.4).
+ *   out  n_qubits + 1 doubles: out[q] = <Z_q>, out[n_qubits] = sum_q <Z_q>;
+ *        host or device memory as selected by out_on_device (see sv_expect).
+ * Uses library-owned device scratch (allocated on first use per stream). */
+sv_status sv_expect_z_all(const void* state, int n_qubits, sv_dtype dtype, double* out, int out_on_device,
+                          void* stream);
+
+/* Planning summary of a circuit without running it (opts as in
+ * sv_apply_circuit_ex, NULL = all zero): number of fused blocks (the paper's
+ * fusion when 2 <= fuse_max_k <= 5, else the gate count), the number of
+ * passes over the state the library would make, and, if
+ * block_starts is not NULL, the index of the first gate of each block
+ * (block_starts must hold n_gates + 1 ints; block_starts[blocks] = n_gates). */
+sv_status sv_plan_info(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                       const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
+                       int* out_blocks, int* out_sweeps, int* block_starts);
+
+/* End-to-end call on HOST buffers: copies `state_in` (host, 2^n amplitudes of
+ * dtype; NULL means |0..0>) to a library-owned device buffer, applies the
+ * circuit as sv_apply_circuit does, evaluates <Z_q> for all qubits into
+ * out_z (host, n_qubits + 1 doubles, as sv_expect_z_all) and, when
+ * state_out is not NULL, copies the final state back to it (host).  The
+ * device buffer is kept per stream and reused by later calls of the same
+ * or smaller size.  Synchronizes `stream`. */
+sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const sv_gate* gates, size_t n_gates,
+                      const double* param_values, size_t n_param_values, int fuse_max_k, double* out_z,
+                      void* state_out, void* stream);
+
+/* ---- library-owned states ------------------------------------------------
+ * For callers without their own device allocator.  A handle owns one device
+ * buffer of 2^n amplitudes of dtype, bound to `stream` (Sec. 4.1: the dense
+ * State; Sec. 5.1: conversion to the host is an explicit exit). */
+typedef struct sv_state* sv_handle;
+
+/* Allocates a state initialised to |0..0>.  SV_ERR_OOM if cudaMalloc fails. */
+sv_status sv_alloc(int n_qubits, sv_dtype dtype, void* stream, sv_handle* out);
+/* Frees the state (after synchronizing its stream).  NULL is a no-op. */
+sv_status sv_free(sv_handle h);
+/* Device pointer of the state's amplitudes (for the pointer-based calls). */
+void* sv_state_ptr(sv_handle h);
+/* Copies 2^n amplitudes of the handle's dtype from `src` (host memory when
+ * src_is_device == 0, else device memory) into the state.  Synchronizes. */
+sv_status sv_set_state(sv_handle h, const void* src, int src_is_device);
+/* Copies the state into `dst` (host or device as selected).  Synchronizes. */
+sv_status sv_get_state(sv_handle h, void* dst, int dst_is_device);
+
+/* ---- kernel timing ---------------------------------------------------------
+ * When enabled, the library brackets each of its kernel launches with a pair
+ * of CUDA events recorded on the launching stream, so the per-launch device
+ * time is measured where the work runs (median-free totals; the caller times
+ * whole steps itself).  Entries aggregate by kernel family. */
+typedef struct sv_profile_entry {
+  char name[32];       /* kernel family, e.g. "sweep", "expect_z_all" */
+  int64_t launches;
+  double total_ms;     /* sum of event-measured launch durations */
+  double bytes;        /* sum of algorithmic HBM bytes of those launches */
+} sv_profile_entry;
+
+/* on != 0 starts recording (clearing earlier records); 0 stops. */
+sv_status sv_profile_enable(int on);
+/* Waits for the recorded events and writes up to max_entries aggregates;
+ * *n_out = number of families.  reset != 0 clears the records. */
+sv_status sv_profile_read(sv_profile_entry* out, int max_entries, int* n_out, int reset);
+
+/* Releases the library's device scratch buffers of every stream (after a
+ * device synchronize).  Later calls allocate them again. */
+sv_status sv_release_scratch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_H */

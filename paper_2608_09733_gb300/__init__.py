@@ -1,0 +1,30 @@
+"""GB300-native state-vector hot path (sm_103a CUDA behind a C ABI).
+
+The package holds the CUDA kernels and host runtime (``csrc/``, built into
+``_build/libsv.so`` by ``build.py``), the ctypes binding with the ABI's names
+(``binding``), the torch autograd wrapper of the adjoint gradient and the
+serving loop.
+"""
+
+from .binding import (  # noqa: F401
+    SV_C64,
+    SV_C128,
+    Gates,
+    SvError,
+    SvState,
+    load,
+    pauli_terms,
+    sv_apply_circuit,
+    sv_apply_circuit_ex,
+    SV_BLOCK_AUTO,
+    SV_BLOCK_DENSE,
+    sv_expect,
+    sv_expect_z_all,
+    sv_init_basis,
+    sv_plan_info,
+    sv_profile_enable,
+    sv_profile_read,
+    sv_release_scratch,
+    sv_run_host,
+    sv_version,
+)

@@ -1,0 +1,339 @@
+"""ctypes binding of libsv.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls (see
+include/sv.h) and does nothing but convert Python arguments (gate records,
+Pauli terms, torch tensors, the current torch stream) into the C structs and
+pointers of the ABI, call it, and raise ``SvError`` on a non-OK status.  All
+arithmetic runs in the library's CUDA kernels; there is no CPU path.  When
+libsv.so has not been built, loading fails with an error that says how to
+build it.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
+
+SV_C64, SV_C128 = 0, 1
+STATUS = {0: "SV_OK", 1: "SV_ERR_INVALID", 2: "SV_ERR_UNSUPPORTED", 3: "SV_ERR_OOM", 4: "SV_ERR_CUDA",
+          5: "SV_ERR_TIMEOUT", 6: "SV_ERR_UNBOUND_PARAM"}
+
+GATE_TYPES = {
+    "i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,
+    "rx": 10, "ry": 11, "rz": 12, "p": 13, "u2": 14, "u3": 15,
+    "swap": 16, "rxx": 17, "ryy": 18, "rzz": 19, "unitary": 20,
+}
+
+# Every symbol include/sv.h declares (checked by the CPU tests).
+EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "sv_apply_circuit_ex", "sv_expect",
+           "sv_expect_z_all",
+           "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
+           "sv_release_scratch", "sv_profile_enable", "sv_profile_read"]
+
+
+class SvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), message))
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class SvGate(ctypes.Structure):
+    _fields_ = [
+        ("type", ctypes.c_int32),
+        ("n_targets", ctypes.c_int32),
+        ("targets", ctypes.c_int32 * 5),
+        ("n_controls", ctypes.c_int32),
+        ("controls", ctypes.c_int32 * 5),
+        ("control_zero_mask", ctypes.c_uint32),
+        ("param_slot", ctypes.c_int32 * 3),
+        ("params", ctypes.c_double * 3),
+        ("matrix", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class SvExecOpts(ctypes.Structure):
+    _fields_ = [("fuse_max_k", ctypes.c_int32), ("block_mode", ctypes.c_int32), ("ops_per_pass", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+SV_BLOCK_AUTO, SV_BLOCK_DENSE = 0, 1
+
+
+class SvProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+class SvPauliTerm(ctypes.Structure):
+    _fields_ = [("x_mask", ctypes.c_uint64), ("z_mask", ctypes.c_uint64), ("coeff", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Loads libsv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsv.so is not built (%s); run `python -m paper_2608_09733_gb300.build` "
+                               "or __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, vp, sz, cd = ctypes.POINTER, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double
+        ci = ctypes.c_int
+        sig = {
+            "sv_version": ([], ci),
+            "sv_last_error": ([], ctypes.c_char_p),
+            "sv_init_basis": ([vp, ci, ci, ctypes.c_uint64, vp], ci),
+            "sv_apply_circuit": ([vp, ci, ci, P(SvGate), sz, P(cd), sz, ci, vp], ci),
+            "sv_expect": ([vp, ci, ci, P(SvPauliTerm), sz, vp, ci, vp], ci),
+            "sv_expect_z_all": ([vp, ci, ci, vp, ci, vp], ci),
+            "sv_apply_circuit_ex": ([vp, ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), vp], ci),
+            "sv_plan_info": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), P(ci), P(ci), P(ci)], ci),
+            "sv_run_host": ([ci, ci, vp, P(SvGate), sz, P(cd), sz, ci, P(cd), vp, vp], ci),
+            "sv_alloc": ([ci, ci, vp, P(vp)], ci),
+            "sv_free": ([vp], ci),
+            "sv_state_ptr": ([vp], vp),
+            "sv_set_state": ([vp, vp, ci], ci),
+            "sv_get_state": ([vp, vp, ci], ci),
+            "sv_release_scratch": ([], ci),
+            "sv_profile_enable": ([ci], ci),
+            "sv_profile_read": ([P(SvProfileEntry), ci, P(ci), ci], ci),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SvError(status, load().sv_last_error().decode(errors="replace"))
+
+
+# ---------------------------------------------------------------- marshalling
+
+class Gates:
+    """A ctypes array of SvGate built from gate records (workloads.Gate or any
+    object with name/targets/controls/control_states/params/slots/matrix)."""
+
+    def __init__(self, gates):
+        self._keep = []
+        self.n = len(gates)
+        self.arr = (SvGate * max(1, self.n))()
+        for i, g in enumerate(gates):
+            o = self.arr[i]
+            o.type = GATE_TYPES[g.name]
+            o.n_targets = len(g.targets)
+            o.n_controls = len(g.controls)
+            for j, q in enumerate(g.targets):
+                o.targets[j] = q
+            mask = 0
+            for j, q in enumerate(g.controls):
+                o.controls[j] = q
+                if int(g.control_states[j]) == 0:
+                    mask |= 1 << j
+            o.control_zero_mask = mask
+            slots = list(g.slots) + [-1] * (3 - len(g.slots))
+            params = list(g.params) + [0.0] * (3 - len(g.params))
+            for j in range(3):
+                o.param_slot[j] = int(slots[j])
+                o.params[j] = float(params[j])
+            if g.name == "unitary":
+                buf = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128)).view(np.float64).reshape(-1)
+                buf = np.ascontiguousarray(buf)
+                self._keep.append(buf)
+                o.matrix = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def pauli_terms(terms) -> "ctypes.Array":
+    """ctypes array of SvPauliTerm from (paulis, qubits, coeff) records."""
+    arr = (SvPauliTerm * max(1, len(terms)))()
+    for j, t in enumerate(terms):
+        x = z = 0
+        for letter, q in zip(t.paulis, t.qubits):
+            if letter in "XY":
+                x |= 1 << q
+            if letter in "ZY":
+                z |= 1 << q
+        arr[j].x_mask, arr[j].z_mask, arr[j].coeff = x, z, float(t.coeff)
+    return arr
+
+
+def _params(param_values):
+    if param_values is None:
+        return None, 0, None
+    pv = np.ascontiguousarray(np.asarray(param_values, dtype=np.float64).reshape(-1))
+    return pv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pv.size, pv
+
+
+def _dtype_of(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return SV_C64
+    if t.dtype == torch.complex128:
+        return SV_C128
+    raise TypeError("state must be complex64 or complex128, got %s" % t.dtype)
+
+
+def _n_of(t) -> int:
+    n = int(t.numel()).bit_length() - 1
+    if t.numel() != (1 << n) or not t.is_contiguous():
+        raise ValueError("state must be a contiguous tensor of 2^n amplitudes")
+    return n
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- entry points
+
+def sv_version() -> int:
+    return int(load().sv_version())
+
+
+def sv_init_basis(state, basis_index: int = 0, stream=None):
+    _check(load().sv_init_basis(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state),
+                                int(basis_index), _stream(stream)))
+
+
+def sv_apply_circuit(state, gates, param_values=None, fuse_max_k: int = 0, stream=None):
+    g = gates if isinstance(gates, Gates) else Gates(gates)
+    pp, npv, _keep = _params(param_values)
+    _check(load().sv_apply_circuit(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), g.arr, g.n,
+                                   pp, npv, int(fuse_max_k), _stream(stream)))
+
+
+def _opts(fuse_max_k=0, block_mode=0, ops_per_pass=0):
+    o = SvExecOpts()
+    o.fuse_max_k, o.block_mode, o.ops_per_pass = int(fuse_max_k), int(block_mode), int(ops_per_pass)
+    return o
+
+
+def sv_apply_circuit_ex(state, gates, param_values=None, fuse_max_k: int = 0, block_mode: int = 0,
+                        ops_per_pass: int = 0, stream=None):
+    g = gates if isinstance(gates, Gates) else Gates(gates)
+    pp, npv, _keep = _params(param_values)
+    o = _opts(fuse_max_k, block_mode, ops_per_pass)
+    _check(load().sv_apply_circuit_ex(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), g.arr, g.n,
+                                      pp, npv, ctypes.byref(o), _stream(stream)))
+
+
+def sv_expect(state, terms, out=None, stream=None) -> np.ndarray:
+    """<P_j> per term; into a device float64 tensor `out` if given (async),
+    else returned as a host array."""
+    arr = terms if isinstance(terms, ctypes.Array) else pauli_terms(terms)
+    nt = len(arr) if isinstance(terms, ctypes.Array) else len(terms)
+    if out is None:
+        host = np.zeros(nt, dtype=np.float64)
+        _check(load().sv_expect(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), arr, nt,
+                                host.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
+        return host
+    _check(load().sv_expect(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), arr, nt,
+                            ctypes.c_void_p(out.data_ptr()), 1, _stream(stream)))
+    return out
+
+
+def sv_expect_z_all(state, out=None, stream=None):
+    """(<Z_q> for all q, their sum) as a host array of n + 1, or written into a
+    device float64 tensor `out` (async)."""
+    n = _n_of(state)
+    if out is None:
+        host = np.zeros(n + 1, dtype=np.float64)
+        _check(load().sv_expect_z_all(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state),
+                                      host.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
+        return host
+    _check(load().sv_expect_z_all(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state),
+                                  ctypes.c_void_p(out.data_ptr()), 1, _stream(stream)))
+    return out
+
+
+def sv_plan_info(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, block_mode: int = 0,
+                 ops_per_pass: int = 0):
+    """(number of blocks, number of HBM passes, block start indices)."""
+    g = gates if isinstance(gates, Gates) else Gates(gates)
+    pp, npv, _keep = _params(param_values)
+    nb, ns = ctypes.c_int(), ctypes.c_int()
+    starts = (ctypes.c_int * (g.n + 1))()
+    o = _opts(fuse_max_k, block_mode, ops_per_pass)
+    _check(load().sv_plan_info(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), ctypes.byref(nb), ctypes.byref(ns),
+                               starts))
+    return nb.value, ns.value, [starts[i] for i in range(nb.value + 1)]
+
+
+def sv_run_host(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, state_in=None,
+                state_out=None, stream=None) -> np.ndarray:
+    """End-to-end on host buffers (numpy): returns (<Z_q>..., sum)."""
+    g = gates if isinstance(gates, Gates) else Gates(gates)
+    pp, npv, _keep = _params(param_values)
+    out = np.zeros(n + 1, dtype=np.float64)
+    sin = ctypes.c_void_p(state_in.ctypes.data) if state_in is not None else None
+    sout = ctypes.c_void_p(state_out.ctypes.data) if state_out is not None else None
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    _check(load().sv_run_host(n, dtype, sin, g.arr, g.n, pp, npv, int(fuse_max_k),
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sout, st))
+    return out
+
+
+class SvState:
+    """A library-owned state (sv_alloc / sv_free)."""
+
+    def __init__(self, n: int, dtype: int, stream=None):
+        self.n, self.dtype = n, dtype
+        h = ctypes.c_void_p()
+        st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+        _check(load().sv_alloc(n, dtype, st, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def ptr(self) -> int:
+        return load().sv_state_ptr(self.handle)
+
+    def set(self, host: np.ndarray):
+        _check(load().sv_set_state(self.handle, ctypes.c_void_p(host.ctypes.data), 0))
+
+    def get(self) -> np.ndarray:
+        out = np.zeros(1 << self.n, dtype=np.complex64 if self.dtype == SV_C64 else np.complex128)
+        _check(load().sv_get_state(self.handle, ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def free(self):
+        if self.handle:
+            _check(load().sv_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sv_release_scratch():
+    _check(load().sv_release_scratch())
+
+
+def sv_profile_enable(on: bool = True):
+    _check(load().sv_profile_enable(1 if on else 0))
+
+
+def sv_profile_read(reset: bool = True) -> dict:
+    """{family: {"launches", "total_ms", "bytes"}} of the launches recorded
+    since profiling was enabled (waits for their events)."""
+    arr = (SvProfileEntry * 64)()
+    n = ctypes.c_int()
+    _check(load().sv_profile_read(arr, 64, ctypes.byref(n), 1 if reset else 0))
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
+                                   "bytes": float(arr[i].bytes)} for i in range(min(n.value, 64))}

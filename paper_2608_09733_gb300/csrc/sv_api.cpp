@@ -1,0 +1,551 @@
+// sv_api.cpp -- the extern "C" boundary declared in include/sv.h.
+//
+// Every entry point validates its arguments on the host before it touches the
+// device (Sec. 3.3: unsupported combinations raise at their boundary; the
+// distributed path likewise checks before allocating), converts the gate
+// records into device programs and launches the kernels on the caller's
+// stream.  Device pointers are checked to be device (or managed) memory of the
+// current device, 16-byte aligned and, where the driver reports the owning
+// allocation, large enough for 2^n amplitudes, so that a wrong pointer or size
+// is an error status rather than an out-of-bounds access.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+thread_local std::string g_last_error;
+
+[[noreturn]] void fail(sv_status s, const std::string& m) { throw Error{s, m}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(SV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename F>
+sv_status guarded(F&& f) {
+  try {
+    f();
+    return SV_OK;
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return SV_ERR_OOM;
+  } catch (...) {
+    g_last_error = "unexpected host exception";
+    return SV_ERR_INVALID;
+  }
+}
+
+size_t amp_bytes(sv_dtype d) { return d == SV_C64 ? 8 : 16; }
+
+void check_dtype_n(int n, sv_dtype dtype) {
+  if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+  if (n < 1 || n > SV_MAX_QUBITS) fail(SV_ERR_INVALID, "n_qubits must be in 1..34");
+}
+
+// cuMemGetAddressRange through the runtime's driver entry point (no link-time
+// dependency on libcuda).
+using AddrRangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+AddrRangeFn addr_range_fn() {
+  static AddrRangeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (AddrRangeFn) nullptr;
+    }
+    return (AddrRangeFn)p;
+  }();
+  return fn;
+}
+
+void check_device_buffer(const void* p, size_t bytes, const char* what) {
+  if (!p) fail(SV_ERR_INVALID, std::string(what) + " is NULL");
+  if ((uintptr_t)p % 16) fail(SV_ERR_INVALID, std::string(what) + " is not 16-byte aligned");
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(SV_ERR_INVALID, std::string(what) + " is not a CUDA pointer");
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    fail(SV_ERR_INVALID, std::string(what) + " is not device memory");
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (at.type == cudaMemoryTypeDevice && at.device != dev)
+    fail(SV_ERR_INVALID, std::string(what) + " belongs to another device than the current one");
+  if (AddrRangeFn fn = addr_range_fn()) {
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS) {
+      if ((uintptr_t)p + bytes > (uintptr_t)base + size)
+        fail(SV_ERR_INVALID, std::string(what) + " is smaller than the requested size");
+    }
+  }
+}
+
+// ----------------------------------------------------------- scratch per stream
+
+struct Workspace {
+  double* scratch = nullptr;
+  size_t scratch_cap = 0;  // doubles
+  double* out = nullptr;   // device results staged for host copies
+  size_t out_cap = 0;      // doubles
+  void* state = nullptr;   // sv_run_host state buffer
+  size_t state_cap = 0;    // bytes
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+void grow(void** p, size_t* cap, size_t want, cudaStream_t stream, const char* what) {
+  if (*cap >= want) return;
+  if (*p) {
+    cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  cudaError_t e = cudaMalloc(p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    fail(SV_ERR_OOM, std::string("cudaMalloc of ") + what + " failed: " + cudaGetErrorString(e));
+  }
+  *cap = want;
+}
+
+Workspace& workspace(cudaStream_t stream, size_t scratch_doubles, size_t out_doubles, size_t state_bytes) {
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace& w = g_ws[{dev, stream}];
+  size_t sc = w.scratch_cap * sizeof(double), oc = w.out_cap * sizeof(double);
+  grow((void**)&w.scratch, &sc, scratch_doubles * sizeof(double), stream, "reduction scratch");
+  grow((void**)&w.out, &oc, std::max<size_t>(out_doubles, 64) * sizeof(double), stream, "result buffer");
+  w.scratch_cap = sc / sizeof(double);
+  w.out_cap = oc / sizeof(double);
+  if (state_bytes) grow(&w.state, &w.state_cap, state_bytes, stream, "state buffer");
+  return w;
+}
+
+// ----------------------------------------------------------- kernel timing
+
+struct ProfRec {
+  std::string family;
+  cudaEvent_t e0, e1;
+  double bytes;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
+}  // namespace
+
+Prof::Prof(cudaStream_t s, const char* fam, double b) : stream(s), family(fam), bytes(b) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    e0 = e1 = nullptr;
+    return;
+  }
+  cudaEventRecord(e0, stream);
+}
+
+void Prof::done() {
+  if (!e0) return;
+  cudaEventRecord(e1, stream);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back({family, e0, e1, bytes});
+  e0 = e1 = nullptr;
+}
+
+namespace {
+
+// ----------------------------------------------------------- programs
+
+template <typename R>
+void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
+  std::memset(&P.h, 0, sizeof(P.h));
+  P.h.n = plan.n;
+  P.h.m = sw.m;
+  P.h.L = sw.L;
+  P.h.nops = (int)sw.ops.size();
+  int loc[64];
+  for (int q = 0; q < 64; q++) loc[q] = -1;
+  for (int i = 0; i < sw.m; i++) {
+    P.h.tq[i] = (int8_t)sw.tq[i];
+    loc[sw.tq[i]] = i;
+  }
+  int coef = 0;
+  for (size_t oi = 0; oi < sw.ops.size(); oi++) {
+    const LOp& op = plan.ops[sw.ops[oi]];
+    DevOp d;
+    std::memset(&d, 0, sizeof(d));
+    d.kind = op.kind;
+    d.k = (uint8_t)op.k;
+    int sp[5], ns = 0;
+    for (int i = 0; i < op.k; i++) {
+      int l = loc[op.q[i]];
+      d.gq[i] = (uint8_t)op.q[i];
+      if (op.kind == OPK_DIAG) {
+        d.pos[i] = l < 0 ? 0xFF : (uint8_t)l;
+      } else {
+        if (l < 0) fail(SV_ERR_INVALID, "internal: target outside the tile");
+        d.pos[i] = (uint8_t)l;
+        sp[ns++] = l;
+      }
+    }
+    for (int i = 1; i < ns; i++)
+      for (int j = i; j > 0 && sp[j - 1] > sp[j]; j--) std::swap(sp[j], sp[j - 1]);
+    for (int i = 0; i < ns; i++) d.spos[i] = (uint8_t)sp[i];
+    for (int i = 0; i < op.nc; i++) {
+      int l = loc[op.c[i]];
+      if (l >= 0) {
+        d.lmask |= 1u << l;
+        if (op.cs[i]) d.lval |= 1u << l;
+      } else {
+        d.xmask |= 1ull << op.c[i];
+        if (op.cs[i]) d.xval |= 1ull << op.c[i];
+      }
+    }
+    d.coef = (uint32_t)coef;
+    for (const cplx& v : op.m) {
+      if (coef >= SweepProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: coefficient pool overflow");
+      P.coef[coef].re = (R)v.real();
+      P.coef[coef].im = (R)v.imag();
+      coef++;
+    }
+    P.ops[oi] = d;
+  }
+  P.h.ncoef = coef;
+}
+
+template <typename R>
+void run_plan(void* state, const Plan& plan, cudaStream_t stream) {
+  static thread_local std::unique_ptr<SweepProgram<R>> prog;
+  if (!prog) prog.reset(new SweepProgram<R>());
+  const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << plan.n);  // read + write the state
+  for (const Sweep& sw : plan.sweeps) {
+    build_program<R>(plan, sw, *prog);
+    Prof pr(stream, "sweep", bytes);
+    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), *prog, stream), "sweep launch");
+    pr.done();
+  }
+}
+
+sv_exec_opts opts_of(const sv_exec_opts* o) {
+  sv_exec_opts r;
+  std::memset(&r, 0, sizeof(r));
+  if (o) r = *o;
+  return r;
+}
+
+sv_exec_opts fuse_opts(int fuse) {
+  sv_exec_opts r = opts_of(nullptr);
+  r.fuse_max_k = fuse;
+  return r;
+}
+
+void apply_circuit(void* state, int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* pv,
+                   size_t npv, const sv_exec_opts& opts, cudaStream_t stream) {
+  Plan plan = make_plan(n, dtype, gates, n_gates, pv, npv, opts);
+  if (dtype == SV_C64)
+    run_plan<float>(state, plan, stream);
+  else
+    run_plan<double>(state, plan, stream);
+}
+
+void expect_z_all_dev(const void* state, int n, sv_dtype dtype, double* out_dev, cudaStream_t stream) {
+  Workspace& w = workspace(stream, expect_z_all_scratch_doubles(n), n + 1, 0);
+  Prof pr(stream, "expect_z_all", (double)amp_bytes(dtype) * (double)(1ull << n));
+  struct Done {
+    Prof& p;
+    ~Done() { p.done(); }
+  } done_{pr};
+  if (dtype == SV_C64)
+    cuda_check(launch_expect_z_all<float>((const Cx<float>*)state, n, w.scratch, w.scratch_cap, out_dev, stream),
+               "expect_z_all launch");
+  else
+    cuda_check(launch_expect_z_all<double>((const Cx<double>*)state, n, w.scratch, w.scratch_cap, out_dev, stream),
+               "expect_z_all launch");
+}
+
+}  // namespace
+}  // namespace sv
+
+using namespace sv;
+
+struct sv_state {
+  void* ptr;
+  int n;
+  sv_dtype dtype;
+  cudaStream_t stream;
+  size_t bytes;
+};
+
+extern "C" {
+
+int sv_version(void) { return 100; }
+
+const char* sv_last_error(void) { return g_last_error.c_str(); }
+
+sv_status sv_init_basis(void* state, int n_qubits, sv_dtype dtype, uint64_t basis_index, void* stream) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    if (basis_index >= (1ull << n_qubits)) fail(SV_ERR_INVALID, "basis_index out of range");
+    check_device_buffer(state, amp_bytes(dtype) << n_qubits, "state");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SV_C64)
+      cuda_check(launch_init_basis<float>((Cx<float>*)state, n_qubits, basis_index, s), "init launch");
+    else
+      cuda_check(launch_init_basis<double>((Cx<double>*)state, n_qubits, basis_index, s), "init launch");
+  });
+}
+
+sv_status sv_apply_circuit(void* state, int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                           const double* param_values, size_t n_param_values, int fuse_max_k, void* stream) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    check_device_buffer(state, amp_bytes(dtype) << n_qubits, "state");
+    apply_circuit(state, n_qubits, dtype, gates, n_gates, param_values, n_param_values, fuse_opts(fuse_max_k),
+                  (cudaStream_t)stream);
+  });
+}
+
+sv_status sv_apply_circuit_ex(void* state, int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                              const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
+                              void* stream) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    check_device_buffer(state, amp_bytes(dtype) << n_qubits, "state");
+    apply_circuit(state, n_qubits, dtype, gates, n_gates, param_values, n_param_values, opts_of(opts),
+                  (cudaStream_t)stream);
+  });
+}
+
+sv_status sv_expect(const void* state, int n_qubits, sv_dtype dtype, const sv_pauli_term* terms, size_t n_terms,
+                    double* out, int out_on_device, void* stream) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    if (n_terms < 1 || n_terms > 4096) fail(SV_ERR_INVALID, "n_terms must be in 1..4096");
+    if (!terms) fail(SV_ERR_INVALID, "terms is NULL");
+    if (!out) fail(SV_ERR_INVALID, "out is NULL");
+    const uint64_t all = (1ull << n_qubits) - 1ull;
+    for (size_t j = 0; j < n_terms; j++)
+      if ((terms[j].x_mask | terms[j].z_mask) & ~all)
+        fail(SV_ERR_INVALID, "term " + std::to_string(j) + " names a qubit beyond n_qubits");
+    check_device_buffer(state, amp_bytes(dtype) << n_qubits, "state");
+    if (out_on_device) check_device_buffer(out, n_terms * sizeof(double), "out");
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace& w = workspace(s, expect_terms_scratch_doubles(n_qubits, (int)n_terms), n_terms, 0);
+    double* dst = out_on_device ? out : w.out;
+    Prof pr(s, "expect_terms", (double)amp_bytes(dtype) * (double)(1ull << n_qubits));
+    if (dtype == SV_C64)
+      cuda_check(launch_expect_terms<float>((const Cx<float>*)state, n_qubits, terms, (int)n_terms, w.scratch,
+                                            w.scratch_cap, dst, s),
+                 "expect launch");
+    else
+      cuda_check(launch_expect_terms<double>((const Cx<double>*)state, n_qubits, terms, (int)n_terms, w.scratch,
+                                             w.scratch_cap, dst, s),
+                 "expect launch");
+    pr.done();
+    if (!out_on_device) {
+      cuda_check(cudaMemcpyAsync(out, w.out, n_terms * sizeof(double), cudaMemcpyDeviceToHost, s), "result copy");
+      cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
+  });
+}
+
+sv_status sv_expect_z_all(const void* state, int n_qubits, sv_dtype dtype, double* out, int out_on_device,
+                          void* stream) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    if (!out) fail(SV_ERR_INVALID, "out is NULL");
+    check_device_buffer(state, amp_bytes(dtype) << n_qubits, "state");
+    if (out_on_device) check_device_buffer(out, (n_qubits + 1) * sizeof(double), "out");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (out_on_device) {
+      expect_z_all_dev(state, n_qubits, dtype, out, s);
+    } else {
+      Workspace& w = workspace(s, expect_z_all_scratch_doubles(n_qubits), n_qubits + 1, 0);
+      expect_z_all_dev(state, n_qubits, dtype, w.out, s);
+      cuda_check(cudaMemcpyAsync(out, w.out, (n_qubits + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
+                 "result copy");
+      cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
+  });
+}
+
+sv_status sv_plan_info(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                       const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
+                       int* out_blocks, int* out_sweeps, int* block_starts) {
+  return guarded([&] {
+    Plan plan = make_plan(n_qubits, dtype, gates, n_gates, param_values, n_param_values, opts_of(opts));
+    int nb = (int)plan.block_starts.size() - 1;
+    if (out_blocks) *out_blocks = nb;
+    if (out_sweeps) *out_sweeps = (int)plan.sweeps.size();
+    if (block_starts)
+      for (size_t i = 0; i < plan.block_starts.size(); i++) block_starts[i] = plan.block_starts[i];
+  });
+}
+
+sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const sv_gate* gates, size_t n_gates,
+                      const double* param_values, size_t n_param_values, int fuse_max_k, double* out_z,
+                      void* state_out, void* stream) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    if (!out_z) fail(SV_ERR_INVALID, "out_z is NULL");
+    Plan plan = make_plan(n_qubits, dtype, gates, n_gates, param_values, n_param_values, fuse_opts(fuse_max_k));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = amp_bytes(dtype) << n_qubits;
+    Workspace& w = workspace(s, expect_z_all_scratch_doubles(n_qubits), n_qubits + 1, bytes);
+    if (state_in) {
+      cuda_check(cudaMemcpyAsync(w.state, state_in, bytes, cudaMemcpyHostToDevice, s), "state upload");
+    } else if (dtype == SV_C64) {
+      cuda_check(launch_init_basis<float>((Cx<float>*)w.state, n_qubits, 0, s), "init launch");
+    } else {
+      cuda_check(launch_init_basis<double>((Cx<double>*)w.state, n_qubits, 0, s), "init launch");
+    }
+    if (dtype == SV_C64)
+      run_plan<float>(w.state, plan, s);
+    else
+      run_plan<double>(w.state, plan, s);
+    expect_z_all_dev(w.state, n_qubits, dtype, w.out, s);
+    cuda_check(cudaMemcpyAsync(out_z, w.out, (n_qubits + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
+               "result copy");
+    if (state_out)
+      cuda_check(cudaMemcpyAsync(state_out, w.state, bytes, cudaMemcpyDeviceToHost, s), "state download");
+    cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  });
+}
+
+sv_status sv_alloc(int n_qubits, sv_dtype dtype, void* stream, sv_handle* out) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    if (!out) fail(SV_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<sv_state> h(new sv_state{nullptr, n_qubits, dtype, (cudaStream_t)stream, amp_bytes(dtype) << n_qubits});
+    cudaError_t e = cudaMalloc(&h->ptr, h->bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(SV_ERR_OOM, std::string("cudaMalloc of the state failed: ") + cudaGetErrorString(e));
+    }
+    cudaError_t le = dtype == SV_C64 ? launch_init_basis<float>((Cx<float>*)h->ptr, n_qubits, 0, h->stream)
+                                     : launch_init_basis<double>((Cx<double>*)h->ptr, n_qubits, 0, h->stream);
+    if (le != cudaSuccess) {
+      cudaFree(h->ptr);
+      cuda_check(le, "init launch");
+    }
+    *out = h.release();
+  });
+}
+
+sv_status sv_free(sv_handle h) {
+  return guarded([&] {
+    if (!h) return;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaFree(h->ptr);
+    delete h;
+    cuda_check(e, "cudaStreamSynchronize");
+  });
+}
+
+void* sv_state_ptr(sv_handle h) { return h ? h->ptr : nullptr; }
+
+sv_status sv_set_state(sv_handle h, const void* src, int src_is_device) {
+  return guarded([&] {
+    if (!h || !src) fail(SV_ERR_INVALID, "NULL handle or source");
+    if (src_is_device) check_device_buffer(src, h->bytes, "src");
+    cuda_check(cudaMemcpyAsync(h->ptr, src, h->bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               h->stream),
+               "state copy");
+    cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  });
+}
+
+sv_status sv_get_state(sv_handle h, void* dst, int dst_is_device) {
+  return guarded([&] {
+    if (!h || !dst) fail(SV_ERR_INVALID, "NULL handle or destination");
+    if (dst_is_device) check_device_buffer(dst, h->bytes, "dst");
+    cuda_check(cudaMemcpyAsync(dst, h->ptr, h->bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               h->stream),
+               "state copy");
+    cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  });
+}
+
+sv_status sv_profile_enable(int on) {
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (on) {
+      for (auto& r : g_prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+      }
+      g_prof.clear();
+    }
+    g_prof_on = on != 0;
+  });
+}
+
+sv_status sv_profile_read(sv_profile_entry* out, int max_entries, int* n_out, int reset) {
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<sv_profile_entry> agg;
+    for (auto& r : g_prof) {
+      cuda_check(cudaEventSynchronize(r.e1), "cudaEventSynchronize");
+      float ms = 0.f;
+      cuda_check(cudaEventElapsedTime(&ms, r.e0, r.e1), "cudaEventElapsedTime");
+      sv_profile_entry* e = nullptr;
+      for (auto& a : agg)
+        if (r.family == a.name) e = &a;
+      if (!e) {
+        agg.push_back(sv_profile_entry{});
+        e = &agg.back();
+        std::strncpy(e->name, r.family.c_str(), sizeof(e->name) - 1);
+      }
+      e->launches++;
+      e->total_ms += ms;
+      e->bytes += r.bytes;
+    }
+    if (n_out) *n_out = (int)agg.size();
+    for (int i = 0; i < (int)agg.size() && i < max_entries && out; i++) out[i] = agg[i];
+    if (reset) {
+      for (auto& r : g_prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+      }
+      g_prof.clear();
+    }
+  });
+}
+
+sv_status sv_release_scratch(void) {
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    if (g_ws.empty()) return;
+    cuda_check(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    for (auto& kv : g_ws) {
+      cudaFree(kv.second.scratch);
+      cudaFree(kv.second.out);
+      cudaFree(kv.second.state);
+    }
+    g_ws.clear();
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// sv_internal.h -- structures shared by the host planner (sv_plan.cpp, sv_api.cpp)
+// and the CUDA kernels (sv_sweep.cu, sv_reduce.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+
+namespace sv {
+
+using cplx = std::complex<double>;
+
+// ----------------------------------------------------------------- device program
+//
+// One "sweep" = one pass over the state in tiles of 2^m amplitudes.  A tile is
+// the set of amplitudes that share the bits outside the tile qubits tq[0..m-1]
+// (ascending; tq[i] == i for i < L so each tile is made of contiguous runs of
+// 2^L amplitudes).  The kernel gathers a tile into shared memory, applies the
+// program's ops in order, and scatters it back.  An op acts on *local* bit
+// positions (indices into tq); control qubits outside the tile are the same for
+// every amplitude of a tile and are tested once per tile.
+
+enum OpKind : uint8_t {
+  OPK_DENSE = 0,    // dense 2^k x 2^k complex matrix on local positions pos[0..k-1]
+  OPK_REAL = 1,     // dense matrix with all-real entries (k <= 2)
+  OPK_DIAG = 2,     // diagonal 2^k entries; the k bits may be local or external
+  OPK_ANTIDIAG = 3, // one qubit: out0 = a * v1, out1 = b * v0 (X, Y, CNOT ...)
+  OPK_SWAP = 4,     // two local positions: exchange |01> and |10>
+};
+
+constexpr int kMaxTileQ = 14;  // 2^14 amplitudes: 128 KiB (c64) of shared memory
+constexpr int kMaxOps = 96;
+constexpr int kProgramBytes = 32000;  // kernel parameter space is 32764 bytes
+
+struct DevOp {
+  uint8_t kind;
+  uint8_t k;            // matrix qubits
+  uint8_t pos[5];       // local positions, matrix order (pos[0] = least significant matrix bit);
+                        // OPK_DIAG: 0xFF marks an external qubit (see gq)
+  uint8_t spos[5];      // the local positions sorted ascending (group enumeration)
+  uint8_t gq[5];        // OPK_DIAG: global qubit of each matrix bit
+  uint8_t pad;
+  uint32_t lmask, lval; // controls inside the tile (local bit mask / required values)
+  uint64_t xmask, xval; // controls outside the tile (global bit mask / required values)
+  uint32_t coef;        // first coefficient in the program's pool
+  uint32_t pad2;
+};
+static_assert(sizeof(DevOp) == 56, "DevOp layout");
+
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+struct ProgramHeader {
+  int32_t n, m, L, nops;
+  int32_t ncoef, pad0;
+  int8_t tq[16];
+};
+
+template <typename R>
+struct SweepProgram {
+  static constexpr int kPool =
+      (kProgramBytes - (int)sizeof(ProgramHeader) - kMaxOps * (int)sizeof(DevOp)) / (int)sizeof(Cx<R>);
+  ProgramHeader h;
+  DevOp ops[kMaxOps];
+  Cx<R> coef[kPool];
+};
+
+// ----------------------------------------------------------------- host plan
+
+// A gate after lowering (a matrix in double precision) or a fused block.
+struct LOp {
+  OpKind kind = OPK_DENSE;
+  int k = 0;                 // matrix qubits
+  int q[5] = {0, 0, 0, 0, 0};  // global matrix qubits, q[0] = least significant matrix bit
+  int nc = 0;
+  int c[5] = {0, 0, 0, 0, 0};  // global control qubits
+  int cs[5] = {1, 1, 1, 1, 1}; // required control states
+  std::vector<cplx> m;       // DENSE/REAL: 2^k x 2^k row-major; DIAG: 2^k; ANTIDIAG: {a, b}
+  uint64_t touch = 0;        // every qubit the op reads (matrix qubits and controls)
+  uint64_t need = 0;         // qubits that must be inside the tile
+  int first_gate = 0;        // index of the first source gate (fusion bookkeeping)
+};
+
+struct Sweep {
+  int m = 0, L = 0;
+  int tq[kMaxTileQ];
+  std::vector<int> ops;      // indices into the LOp list, in application order
+};
+
+struct Plan {
+  int n = 0;
+  std::vector<LOp> ops;
+  std::vector<int> block_starts;  // first gate of each op (fusion blocks) + n_gates
+  std::vector<Sweep> sweeps;
+};
+
+// Errors carry a status and a message up to the C ABI.
+struct Error {
+  sv_status status;
+  std::string msg;
+};
+
+// Lowering (gate records -> double-precision matrices), the paper's greedy
+// fusion, and the tile scheduler.  Throw sv::Error on invalid input.
+void validate_gates(int n, const sv_gate* gates, size_t n_gates, size_t n_param_values);
+std::vector<cplx> gate_matrix(const sv_gate& g, const double* param_values);
+LOp lower_gate(const sv_gate& g, const double* param_values, int index);
+std::vector<LOp> fuse_greedy(int n, const sv_gate* gates, size_t n_gates, const double* param_values, int kmax,
+                             std::vector<int>* block_starts, bool dense_always);
+void classify(LOp& op);
+std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_q, int low_q, int coef_pool,
+                                   int ops_per_pass);
+Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
+               size_t n_param_values, const sv_exec_opts& opts);
+double op_cost(const LOp& op);
+int tile_qubits_for(sv_dtype dtype);
+int low_qubits_for(sv_dtype dtype);
+
+// ----------------------------------------------------------------- launches
+// (sv_sweep.cu / sv_reduce.cu).  All return cudaError_t of the launch.
+
+template <typename R>
+cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream);
+template <typename R>
+cudaError_t launch_init_basis(Cx<R>* state, int n, uint64_t index, cudaStream_t stream);
+
+// Reductions write fixed-order per-block partials into `scratch` and a final
+// kernel folds them into `out` (device doubles).
+template <typename R>
+cudaError_t launch_expect_z_all(const Cx<R>* state, int n, double* scratch, size_t scratch_doubles, double* out,
+                                cudaStream_t stream);
+template <typename R>
+cudaError_t launch_expect_terms(const Cx<R>* state, int n, const sv_pauli_term* terms, int n_terms, double* scratch,
+                                size_t scratch_doubles, double* out, cudaStream_t stream);
+size_t expect_z_all_scratch_doubles(int n);
+size_t expect_terms_scratch_doubles(int n, int n_terms);
+
+int device_sm_count();
+
+// Kernel timing (sv_profile_*): Prof p(stream, "sweep", bytes); launch; p.done();
+struct Prof {
+  Prof(cudaStream_t s, const char* family, double bytes);
+  void done();
+  cudaStream_t stream;
+  const char* family;
+  double bytes;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+}  // namespace sv

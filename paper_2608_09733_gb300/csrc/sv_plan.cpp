@@ -1,0 +1,439 @@
+// sv_plan.cpp -- host side of the gate-application path.
+//
+//  * validation of gate records at the boundary (Sec. 3.3: unsupported or
+//    unbound inputs raise instead of being approximated);
+//  * lowering of each gate to its matrix in double precision (Sec. 3.3 and
+//    Sec. 5.2: build at the widest precision, narrow at the device boundary);
+//  * classification into the fast paths the paper names (Sec. 5.3 real vs
+//    complex gates; Sec. 9.2 diagonal and permutation paths);
+//  * the paper's fusion (Sec. 4.3 `fuse`, Sec. 9.2): consecutive gates are
+//    joined, without reordering, while their qubits fit k;
+//  * the tile scheduler: packs consecutive operations whose non-diagonal
+//    qubits fit one shared-memory tile into a single pass over HBM.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+namespace {
+
+const int kTargetsOf[SV_GATE_COUNT_] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1,  // I..SX
+                                        1, 1, 1, 1, 1, 1,              // RX..U3
+                                        2, 2, 2, 2,                    // SWAP, RXX, RYY, RZZ
+                                        -1};                           // UNITARY
+const int kAnglesOf[SV_GATE_COUNT_] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 3, 0, 1, 1, 1, 0};
+
+[[noreturn]] void fail(sv_status s, const std::string& m) { throw Error{s, m}; }
+
+uint64_t gate_qubit_mask(const sv_gate& g) {
+  uint64_t m = 0;
+  for (int i = 0; i < g.n_targets; i++) m |= 1ull << g.targets[i];
+  for (int i = 0; i < g.n_controls; i++) m |= 1ull << g.controls[i];
+  return m;
+}
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+int tile_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? 12 : 11; }  // 32 KiB tiles
+int low_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? 5 : 4; }     // 256-byte runs
+
+void validate_gates(int n, const sv_gate* gates, size_t n_gates, size_t n_param_values) {
+  if (n_gates && !gates) fail(SV_ERR_INVALID, "gates is NULL");
+  for (size_t gi = 0; gi < n_gates; gi++) {
+    const sv_gate& g = gates[gi];
+    std::string at = "gate " + std::to_string(gi) + ": ";
+    if (g.type < 0 || g.type >= SV_GATE_COUNT_) fail(SV_ERR_INVALID, at + "unknown gate type");
+    int want = kTargetsOf[g.type];
+    if (want > 0 && g.n_targets != want) fail(SV_ERR_INVALID, at + "wrong number of targets for its family");
+    if (g.n_targets < 1 || g.n_targets > SV_MAX_TARGETS) fail(SV_ERR_INVALID, at + "n_targets out of range");
+    if (g.n_controls < 0 || g.n_controls > SV_MAX_CONTROLS) fail(SV_ERR_INVALID, at + "n_controls out of range");
+    uint64_t seen = 0;
+    for (int i = 0; i < g.n_targets + g.n_controls; i++) {
+      int q = i < g.n_targets ? g.targets[i] : g.controls[i - g.n_targets];
+      if (q < 0 || q >= n) fail(SV_ERR_INVALID, at + "qubit " + std::to_string(q) + " out of range");
+      if (seen & (1ull << q)) fail(SV_ERR_INVALID, at + "qubit " + std::to_string(q) + " repeated");
+      seen |= 1ull << q;
+    }
+    if (g.n_controls < 32 && (g.control_zero_mask >> g.n_controls) != 0)
+      fail(SV_ERR_INVALID, at + "control_zero_mask has bits beyond n_controls");
+    for (int i = 0; i < kAnglesOf[g.type]; i++) {
+      int s = g.param_slot[i];
+      if (s < -1) fail(SV_ERR_INVALID, at + "negative parameter slot");
+      if (s >= 0 && (size_t)s >= n_param_values)
+        fail(SV_ERR_UNBOUND_PARAM, at + "parameter slot " + std::to_string(s) + " is unbound");
+      double v = s >= 0 ? 0.0 : g.params[i];
+      if (!std::isfinite(v)) fail(SV_ERR_INVALID, at + "angle is not finite");
+    }
+    if (g.type == SV_GATE_UNITARY) {
+      if (!g.matrix) fail(SV_ERR_INVALID, at + "unitary gate without a matrix");
+      int d = 1 << g.n_targets;
+      // U^dagger U = I within 1e-6 (a user matrix that is not unitary is rejected)
+      double worst = 0.0;
+      for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) {
+          cplx acc = 0.0;
+          for (int k = 0; k < d; k++) {
+            cplx a(g.matrix[2 * (k * d + r)], -g.matrix[2 * (k * d + r) + 1]);
+            cplx b(g.matrix[2 * (k * d + c)], g.matrix[2 * (k * d + c) + 1]);
+            acc += a * b;
+          }
+          worst = std::max(worst, std::abs(acc - (r == c ? 1.0 : 0.0)));
+        }
+      if (!(worst < 1e-6)) fail(SV_ERR_INVALID, at + "matrix is not unitary");
+    }
+  }
+}
+
+// The matrix of a gate (without its controls), from the definitions of the
+// gate table (Sec. 4.2) and R_P(theta) = exp(-i theta P / 2) (Sec. 9.1).
+std::vector<cplx> gate_matrix(const sv_gate& g, const double* pv) {
+  auto ang = [&](int i) { return g.param_slot[i] >= 0 ? pv[g.param_slot[i]] : g.params[i]; };
+  const cplx j(0.0, 1.0);
+  const double h = 1.0 / std::sqrt(2.0);
+  switch (g.type) {
+    case SV_GATE_I: return {1.0, 0.0, 0.0, 1.0};
+    case SV_GATE_X: return {0.0, 1.0, 1.0, 0.0};
+    case SV_GATE_Y: return {0.0, -j, j, 0.0};
+    case SV_GATE_Z: return {1.0, 0.0, 0.0, -1.0};
+    case SV_GATE_H: return {h, h, h, -h};
+    case SV_GATE_S: return {1.0, 0.0, 0.0, j};
+    case SV_GATE_SDG: return {1.0, 0.0, 0.0, -j};
+    case SV_GATE_T: return {1.0, 0.0, 0.0, std::polar(1.0, M_PI / 4.0)};
+    case SV_GATE_TDG: return {1.0, 0.0, 0.0, std::polar(1.0, -M_PI / 4.0)};
+    case SV_GATE_SX: return {0.5 * (1.0 + j), 0.5 * (1.0 - j), 0.5 * (1.0 - j), 0.5 * (1.0 + j)};
+    case SV_GATE_RX: {
+      double c = std::cos(0.5 * ang(0)), s = std::sin(0.5 * ang(0));
+      return {c, -j * s, -j * s, c};
+    }
+    case SV_GATE_RY: {
+      double c = std::cos(0.5 * ang(0)), s = std::sin(0.5 * ang(0));
+      return {c, -s, s, c};
+    }
+    case SV_GATE_RZ: return {std::polar(1.0, -0.5 * ang(0)), 0.0, 0.0, std::polar(1.0, 0.5 * ang(0))};
+    case SV_GATE_P: return {1.0, 0.0, 0.0, std::polar(1.0, ang(0))};
+    case SV_GATE_U2:
+    case SV_GATE_U3: {
+      double th = g.type == SV_GATE_U2 ? M_PI / 2.0 : ang(0);
+      double ph = g.type == SV_GATE_U2 ? ang(0) : ang(1);
+      double la = g.type == SV_GATE_U2 ? ang(1) : ang(2);
+      double c = std::cos(0.5 * th), s = std::sin(0.5 * th);
+      return {c, -std::polar(s, la), std::polar(s, ph), std::polar(c, ph + la)};
+    }
+    case SV_GATE_SWAP: {
+      std::vector<cplx> m(16, 0.0);
+      m[0] = m[15] = 1.0;
+      m[1 * 4 + 2] = m[2 * 4 + 1] = 1.0;
+      return m;
+    }
+    case SV_GATE_RXX:
+    case SV_GATE_RYY: {
+      // cos(t/2) I - i sin(t/2) P(x)P; XX and YY are anti-diagonal, YY has
+      // -1 on its outer anti-diagonal corners and +1 on the inner ones.
+      double c = std::cos(0.5 * ang(0)), s = std::sin(0.5 * ang(0));
+      double outer = g.type == SV_GATE_RXX ? 1.0 : -1.0;
+      std::vector<cplx> m(16, 0.0);
+      for (int r = 0; r < 4; r++) m[r * 4 + r] = c;
+      m[0 * 4 + 3] = m[3 * 4 + 0] = -j * s * outer;
+      m[1 * 4 + 2] = m[2 * 4 + 1] = -j * s;
+      return m;
+    }
+    case SV_GATE_RZZ: {
+      // Z(x)Z = diag(1, -1, -1, 1)
+      cplx a = std::polar(1.0, -0.5 * ang(0)), b = std::polar(1.0, 0.5 * ang(0));
+      std::vector<cplx> m(16, 0.0);
+      m[0] = a; m[5] = b; m[10] = b; m[15] = a;
+      return m;
+    }
+    case SV_GATE_UNITARY: {
+      int d = 1 << g.n_targets;
+      std::vector<cplx> m(d * d);
+      for (int i = 0; i < d * d; i++) m[i] = cplx(g.matrix[2 * i], g.matrix[2 * i + 1]);
+      return m;
+    }
+    default: fail(SV_ERR_INVALID, "unknown gate type");
+  }
+}
+
+void classify(LOp& op) {
+  const int d = 1 << op.k;
+  const std::vector<cplx>& m = op.m;
+  op.touch = 0;
+  for (int i = 0; i < op.k; i++) op.touch |= 1ull << op.q[i];
+  for (int i = 0; i < op.nc; i++) op.touch |= 1ull << op.c[i];
+  uint64_t tq = 0;
+  for (int i = 0; i < op.k; i++) tq |= 1ull << op.q[i];
+
+  bool diag = true, real = true;
+  for (int r = 0; r < d; r++)
+    for (int c = 0; c < d; c++) {
+      const cplx& v = m[r * d + c];
+      if (r != c && v != 0.0) diag = false;
+      if (v.imag() != 0.0) real = false;
+    }
+  if (diag) {
+    std::vector<cplx> dd(d);
+    for (int r = 0; r < d; r++) dd[r] = m[r * d + r];
+    op.kind = OPK_DIAG;
+    op.m = dd;
+    op.need = 0;  // a diagonal never moves amplitudes: any tile can apply it
+    return;
+  }
+  if (op.k == 1 && m[0] == 0.0 && m[3] == 0.0) {
+    op.kind = OPK_ANTIDIAG;
+    op.m = {m[1], m[2]};
+    op.need = tq;
+    return;
+  }
+  if (op.k == 2) {
+    bool sw = true;
+    for (int r = 0; r < 4; r++)
+      for (int c = 0; c < 4; c++) {
+        int want_c = (r == 1) ? 2 : (r == 2) ? 1 : r;
+        if (m[r * 4 + c] != (c == want_c ? 1.0 : 0.0)) sw = false;
+      }
+    if (sw) {
+      op.kind = OPK_SWAP;
+      op.m.clear();
+      op.need = tq;
+      return;
+    }
+  }
+  op.kind = (real && op.k <= 2) ? OPK_REAL : OPK_DENSE;
+  op.need = tq;
+}
+
+LOp lower_gate(const sv_gate& g, const double* pv, int index) {
+  LOp op;
+  op.k = g.n_targets;
+  for (int i = 0; i < op.k; i++) op.q[i] = g.targets[i];
+  op.nc = g.n_controls;
+  for (int i = 0; i < op.nc; i++) {
+    op.c[i] = g.controls[i];
+    op.cs[i] = ((g.control_zero_mask >> i) & 1u) ? 0 : 1;
+  }
+  op.m = gate_matrix(g, pv);
+  op.first_gate = index;
+  classify(op);
+  return op;
+}
+
+// Applies gate g, re-indexed onto the block's local qubits, to a vector of
+// 2^nb amplitudes (used to build a fused block's matrix column by column).
+static void apply_local(std::vector<cplx>& v, int nb, const sv_gate& g, const std::vector<cplx>& U,
+                        const int* local_of) {
+  int k = g.n_targets, d = 1 << k;
+  int t[5];
+  for (int i = 0; i < k; i++) t[i] = local_of[g.targets[i]];
+  uint64_t cmask = 0, cval = 0;
+  for (int i = 0; i < g.n_controls; i++) {
+    int lq = local_of[g.controls[i]];
+    cmask |= 1ull << lq;
+    if (!((g.control_zero_mask >> i) & 1u)) cval |= 1ull << lq;
+  }
+  uint64_t tmask = 0;
+  for (int i = 0; i < k; i++) tmask |= 1ull << t[i];
+  std::vector<cplx> in(d);
+  for (uint64_t b = 0; b < (1ull << nb); b++) {
+    if (b & tmask) continue;  // enumerate group bases (target bits clear)
+    if ((b & cmask) != cval) continue;
+    for (int jj = 0; jj < d; jj++) {
+      uint64_t idx = b;
+      for (int i = 0; i < k; i++)
+        if ((jj >> i) & 1) idx |= 1ull << t[i];
+      in[jj] = v[idx];
+    }
+    for (int r = 0; r < d; r++) {
+      cplx acc = 0.0;
+      for (int c = 0; c < d; c++) acc += U[r * d + c] * in[c];
+      uint64_t idx = b;
+      for (int i = 0; i < k; i++)
+        if ((r >> i) & 1) idx |= 1ull << t[i];
+      v[idx] = acc;
+    }
+  }
+}
+
+// Arithmetic per amplitude of one operation in a pass (multiply-adds of the
+// complex matrix-vector product, counted as real flops), plus one
+// shared-memory round trip of the tile per operation.
+double op_cost(const LOp& op) {
+  const double pass = 8.0;
+  switch (op.kind) {
+    case OPK_DENSE: return 8.0 * (1 << op.k) + pass;
+    case OPK_REAL: return 4.0 * (1 << op.k) + pass;
+    case OPK_DIAG: return 6.0 + pass;
+    case OPK_ANTIDIAG: return 6.0 + pass;
+    default: return 1.0 + pass;
+  }
+}
+
+std::vector<LOp> fuse_greedy(int n, const sv_gate* gates, size_t n_gates, const double* pv, int kmax,
+                             std::vector<int>* block_starts, bool dense_always) {
+  (void)n;
+  std::vector<LOp> out;
+  size_t i = 0;
+  while (i < n_gates) {
+    size_t start = i;
+    uint64_t mask = gate_qubit_mask(gates[i]);
+    i++;
+    if (popc(mask) <= kmax) {
+      while (i < n_gates && popc(mask | gate_qubit_mask(gates[i])) <= kmax) {
+        mask |= gate_qubit_mask(gates[i]);
+        i++;
+      }
+    }
+    if (block_starts) block_starts->push_back((int)start);
+    if (i - start == 1) {
+      out.push_back(lower_gate(gates[start], pv, (int)start));
+      continue;
+    }
+    // dense block over the union of its gates' qubits, ascending
+    LOp op;
+    int local_of[64];
+    int nb = 0;
+    for (int q = 0; q < 64; q++)
+      if ((mask >> q) & 1ull) {
+        local_of[q] = nb;
+        op.q[nb++] = q;
+      }
+    op.k = nb;
+    int d = 1 << nb;
+    op.m.assign((size_t)d * d, 0.0);
+    std::vector<std::vector<cplx>> mats;
+    for (size_t g = start; g < i; g++) mats.push_back(gate_matrix(gates[g], pv));
+    std::vector<cplx> col(d);
+    for (int c = 0; c < d; c++) {
+      std::fill(col.begin(), col.end(), cplx(0.0));
+      col[c] = 1.0;
+      for (size_t g = start; g < i; g++) apply_local(col, nb, gates[g], mats[g - start], local_of);
+      for (int r = 0; r < d; r++) op.m[(size_t)r * d + c] = col[r];
+    }
+    op.first_gate = (int)start;
+    classify(op);
+    if (!dense_always) {
+      // keep the block's gates (same pass, same result up to rounding) when
+      // they cost less than the block's dense matrix
+      std::vector<LOp> parts;
+      double parts_cost = 0.0;
+      for (size_t g = start; g < i; g++) {
+        parts.push_back(lower_gate(gates[g], pv, (int)start));
+        parts_cost += op_cost(parts.back());
+      }
+      if (parts_cost < op_cost(op)) {
+        for (auto& pp : parts) out.push_back(std::move(pp));
+        continue;
+      }
+    }
+    out.push_back(std::move(op));
+  }
+  if (block_starts) block_starts->push_back((int)n_gates);
+  return out;
+}
+
+static int coef_count(const LOp& op) {
+  switch (op.kind) {
+    case OPK_DENSE:
+    case OPK_REAL: return 1 << (2 * op.k);
+    case OPK_DIAG: return 1 << op.k;
+    case OPK_ANTIDIAG: return 2;
+    default: return 0;
+  }
+}
+
+std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_q, int low_q, int coef_pool,
+                                   int ops_per_pass) {
+  const int max_ops = ops_per_pass > 0 ? std::min(ops_per_pass, kMaxOps) : kMaxOps;
+  std::vector<Sweep> out;
+  const int m_max = std::min(n, tile_q);
+  const int L0 = std::min(n, low_q);
+  const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+  std::vector<char> done(ops.size(), 0);
+  size_t first = 0, ndone = 0;
+  while (ndone < ops.size()) {
+    Sweep sw;
+    uint64_t S = (1ull << L0) - 1ull;
+    uint64_t blocked = 0;
+    int coef = 0;
+    for (size_t i = first; i < ops.size(); i++) {
+      if (done[i]) continue;
+      const LOp& op = ops[i];
+      if (op.touch & blocked) {
+        blocked |= op.touch;
+        if ((blocked & all) == all) break;
+        continue;
+      }
+      uint64_t S2 = S | op.need;
+      int c = coef_count(op);
+      if (popc(S2) <= m_max && (int)sw.ops.size() < max_ops && coef + c <= coef_pool) {
+        S = S2;
+        coef += c;
+        sw.ops.push_back((int)i);
+        done[i] = 1;
+        ndone++;
+      } else {
+        blocked |= op.touch;
+        if ((blocked & all) == all) break;
+      }
+    }
+    if (sw.ops.empty()) fail(SV_ERR_INVALID, "scheduler could not place an operation");
+    // fill the tile with the lowest remaining qubits (longer contiguous runs)
+    for (int q = 0; q < n && popc(S) < m_max; q++) S |= 1ull << q;
+    sw.m = 0;
+    for (int q = 0; q < n; q++)
+      if ((S >> q) & 1ull) sw.tq[sw.m++] = q;
+    sw.L = 0;
+    while (sw.L < sw.m && sw.tq[sw.L] == sw.L) sw.L++;
+    out.push_back(std::move(sw));
+    while (first < ops.size() && done[first]) first++;
+  }
+  return out;
+}
+
+Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
+               size_t n_param_values, const sv_exec_opts& opts) {
+  const int fuse_max_k = opts.fuse_max_k;
+  if (opts.block_mode != SV_BLOCK_AUTO && opts.block_mode != SV_BLOCK_DENSE) fail(SV_ERR_INVALID, "unknown block_mode");
+  if (opts.ops_per_pass < 0) fail(SV_ERR_INVALID, "ops_per_pass must be >= 0");
+  if (n < 1 || n > SV_MAX_QUBITS) fail(SV_ERR_INVALID, "n_qubits out of range");
+  if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+  if (fuse_max_k != 0 && (fuse_max_k < 2 || fuse_max_k > 5))
+    fail(SV_ERR_INVALID, "fuse_max_k must be 0 or 2..5 (Sec. 4.3: a positive setting is at least 2)");
+  if (n_param_values && !param_values) fail(SV_ERR_INVALID, "param_values is NULL");
+  validate_gates(n, gates, n_gates, n_param_values);
+  Plan p;
+  p.n = n;
+  if (fuse_max_k >= 2) {
+    p.ops = fuse_greedy(n, gates, n_gates, param_values, fuse_max_k, &p.block_starts,
+                        opts.block_mode == SV_BLOCK_DENSE);
+  } else {
+    p.ops.reserve(n_gates);
+    for (size_t i = 0; i < n_gates; i++) {
+      p.ops.push_back(lower_gate(gates[i], param_values, (int)i));
+      p.block_starts.push_back((int)i);
+    }
+    p.block_starts.push_back((int)n_gates);
+  }
+  // drop exact identities (e.g. the I gate): they move no amplitude
+  std::vector<LOp> kept;
+  kept.reserve(p.ops.size());
+  for (auto& op : p.ops) {
+    if (op.kind == OPK_DIAG) {
+      bool ident = true;
+      for (auto& v : op.m)
+        if (v != 1.0) ident = false;
+      if (ident) continue;
+    }
+    kept.push_back(std::move(op));
+  }
+  p.ops = std::move(kept);
+  int pool = dtype == SV_C64 ? SweepProgram<float>::kPool : SweepProgram<double>::kPool;
+  p.sweeps = schedule_sweeps(n, p.ops, tile_qubits_for(dtype), low_qubits_for(dtype), pool, opts.ops_per_pass);
+  return p;
+}
+
+}  // namespace sv

@@ -1,0 +1,97 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol that
+include/sv.h declares, plans exactly the paper's fusion blocks, and rejects
+bad input at the boundary -- all without touching a GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_09733_gb300 import binding as B
+from workloads import (Gate, fused_layered_u3_cz, hea_ring, layered_ry_rz_cnot, precision_sweep,
+                       random_circuit)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "sv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sv_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(svlib):
+    decl = declared_symbols()
+    assert len(decl) >= 10
+    assert sorted(B.EXPORTS) == decl
+    for name in decl:
+        assert hasattr(svlib, name), name
+    assert B.sv_version() == 100
+
+
+@pytest.mark.parametrize("kmax", [2, 3, 4, 5])
+@pytest.mark.parametrize("seed", range(3))
+def test_fusion_blocks_match_oracle_exactly(svlib, kmax, seed):
+    n = 9
+    gates = random_circuit(n, 120, seed=seed, max_controls=2, max_unitary_k=3)
+    ref = [a for (a, _, _, _) in oracle.fuse(n, gates, kmax)] + [len(gates)]
+    for dt in (B.SV_C64, B.SV_C128):
+        nb, ns, starts = B.sv_plan_info(n, dt, gates, fuse_max_k=kmax)
+        assert starts == ref
+        assert nb == len(ref) - 1
+
+
+def test_fusion_blocks_on_the_workloads(svlib):
+    for n, gates in [(12, layered_ry_rz_cnot(12, 10, 0)), (22, fused_layered_u3_cz(22, 20, 0)),
+                     (20, hea_ring(20, 10)), (10, precision_sweep(10, 40, 20, 0))]:
+        params = np.zeros(800)
+        for k in (2, 5):
+            ref = [a for (a, _, _, _) in oracle.fuse(n, gates, k, params)] + [len(gates)]
+            assert B.sv_plan_info(n, B.SV_C64, gates, params, fuse_max_k=k)[2] == ref
+
+
+def test_one_op_per_pass_makes_one_pass_per_gate(svlib):
+    gates = fused_layered_u3_cz(16, 2, 0)
+    nb, ns, _ = B.sv_plan_info(16, B.SV_C64, gates, ops_per_pass=1)
+    assert ns == len(gates) == nb
+    nb, ns, _ = B.sv_plan_info(16, B.SV_C64, gates)
+    assert ns < len(gates) // 4
+
+
+def _err(fn):
+    with pytest.raises(B.SvError) as e:
+        fn()
+    return e.value.name
+
+
+def test_boundary_rejects_bad_gates(svlib):
+    plan = lambda g, **kw: B.sv_plan_info(4, B.SV_C64, g, **kw)
+    assert _err(lambda: plan([Gate("h", [4])])) == "SV_ERR_INVALID"
+    assert _err(lambda: plan([Gate("x", [1], [1])])) == "SV_ERR_INVALID"
+    assert _err(lambda: plan([Gate("swap", [0, 0])])) == "SV_ERR_INVALID"
+    assert _err(lambda: plan([Gate("rx", [0], params=[0.0], slots=[3])], param_values=[0.1])) == \
+        "SV_ERR_UNBOUND_PARAM"
+    assert _err(lambda: plan([Gate("rx", [0], params=[0.0], slots=[0])])) == "SV_ERR_UNBOUND_PARAM"
+    assert _err(lambda: plan([Gate("unitary", [0], matrix=np.array([[1, 1], [0, 1]]))])) == "SV_ERR_INVALID"
+    assert _err(lambda: plan([Gate("h", [0])], fuse_max_k=1)) == "SV_ERR_INVALID"
+    assert _err(lambda: plan([Gate("h", [0])], fuse_max_k=6)) == "SV_ERR_INVALID"
+    assert _err(lambda: B.sv_plan_info(0, B.SV_C64, [])) == "SV_ERR_INVALID"
+    assert _err(lambda: B.sv_plan_info(35, B.SV_C64, [])) == "SV_ERR_INVALID"
+    assert _err(lambda: B.sv_plan_info(4, 7, [])) == "SV_ERR_INVALID"
+    # a valid plan after the failures still works, and the error text names the gate
+    assert plan([Gate("h", [0])])[0] == 1
+    with pytest.raises(B.SvError) as e:
+        plan([Gate("h", [0]), Gate("h", [9])])
+    assert "gate 1" in str(e.value)
+
+
+def test_host_pointer_is_rejected_before_any_launch(svlib):
+    # a host buffer passed as the state must be refused at the boundary (it
+    # would otherwise be dereferenced by a kernel); on a machine without a GPU
+    # the pointer query itself fails, which is also a refusal
+    buf = np.zeros(16, dtype=np.complex64)
+    st = svlib.sv_init_basis(ctypes.c_void_p(buf.ctypes.data), 4, B.SV_C64, 0, None)
+    assert st in (1, 4)  # SV_ERR_INVALID, or SV_ERR_CUDA when no driver is present
