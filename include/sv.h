@@ -190,6 +190,33 @@ sv_status sv_plan_info(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_
                        const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
                        int* out_blocks, int* out_sweeps, int* block_starts);
 
+/* Gradients of f_b(theta) = <0|U^dag(theta_b) H U(theta_b)|0> (Sec. 4.2) for a
+ * batch of parameter vectors of one circuit template, by the adjoint method:
+ * one forward pass storing the state every `checkpoint_every` gates, then
+ * lambda = H psi (Sec. 4.4 matrix-free Pauli action) and one reverse pass that
+ * un-applies the gates from psi and lambda and adds Im <lambda|G|psi> for
+ * every rotation U = exp(-i theta G / 2) (equal to the parameter-shift
+ * derivative of Sec. 4.2).  At each checkpoint the reverse pass replaces psi
+ * by the stored forward state, which bounds the complex64 uncompute drift.
+ *   gates            template; parameterised gates (param_slot[0] >= 0) must
+ *                    be RX, RY, RZ, P, RXX, RYY or RZZ (else
+ *                    SV_ERR_UNSUPPORTED); every gate has <= 2 targets
+ *   params           host, batch x n_params doubles, row-major; row b binds
+ *                    the slots of state b
+ *   terms            H = sum_j coeff_j P_j, 1..4096 terms
+ *   checkpoint_every gates between stored states (0 = no checkpoints);
+ *                    device memory grows by batch * 2^n amplitudes per stored
+ *                    state
+ *   out_grad         host, batch x n_params (slots no gate uses get 0; a slot
+ *                    used by several gates gets the sum of their terms)
+ *   out_value        host, batch values f_b
+ * Library-owned device buffers (psi, lambda, checkpoints, tables) are kept
+ * per stream and reused.  1 <= n_qubits <= 30, 1 <= batch <= 65535.
+ * Synchronizes `stream`. */
+sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
+                          int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
+                          double* out_grad, double* out_value, void* stream);
+
 /* End-to-end call on HOST buffers: copies `state_in` (host, 2^n amplitudes of
  * dtype; NULL means |0..0>) to a library-owned device buffer, applies the
  * circuit as sv_apply_circuit does, evaluates <Z_q> for all qubits into

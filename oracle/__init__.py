@@ -31,7 +31,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sv_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-MAXQ = 6
+MAXQ = 10
 
 KINDS = {
     "i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,

@@ -47,7 +47,7 @@ enum {
   OK_SWAP, OK_RXX, OK_RYY, OK_RZZ, OK_UNITARY, OK_NKINDS
 };
 
-#define OG_MAXQ 6
+#define OG_MAXQ 10
 
 typedef struct {
   int32_t kind;

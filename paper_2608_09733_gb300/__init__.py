@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     SvState,
     load,
     pauli_terms,
+    sv_adjoint_grad,
     sv_apply_circuit,
     sv_apply_circuit_ex,
     SV_BLOCK_AUTO,
@@ -28,3 +29,5 @@ from .binding import (  # noqa: F401
     sv_run_host,
     sv_version,
 )
+
+from .autograd import AdjointExpectation, adjoint_expectation  # noqa: E402,F401

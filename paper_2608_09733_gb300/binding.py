@@ -34,7 +34,7 @@ GATE_TYPES = {
 EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "sv_apply_circuit_ex", "sv_expect",
            "sv_expect_z_all",
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
-           "sv_release_scratch", "sv_profile_enable", "sv_profile_read"]
+           "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad"]
 
 
 class SvError(RuntimeError):
@@ -105,6 +105,7 @@ def load():
             "sv_get_state": ([vp, vp, ci], ci),
             "sv_release_scratch": ([], ci),
             "sv_profile_enable": ([ci], ci),
+            "sv_adjoint_grad": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(SvPauliTerm), sz, ci, P(cd), P(cd), vp], ci),
             "sv_profile_read": ([P(SvProfileEntry), ci, P(ci), ci], ci),
         }
         for name, (args, res) in sig.items():
@@ -337,3 +338,23 @@ def sv_profile_read(reset: bool = True) -> dict:
     _check(load().sv_profile_read(arr, 64, ctypes.byref(n), 1 if reset else 0))
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
                                    "bytes": float(arr[i].bytes)} for i in range(min(n.value, 64))}
+
+
+def sv_adjoint_grad(n: int, dtype: int, gates, params, terms, checkpoint_every: int = 0, stream=None):
+    """(values (batch,), gradients (batch, n_params)) for a (batch, n_params)
+    array of parameter vectors (host float64)."""
+    g = gates if isinstance(gates, Gates) else Gates(gates)
+    pv = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if pv.ndim == 1:
+        pv = pv.reshape(1, -1)
+    batch, npar = pv.shape
+    arr = terms if isinstance(terms, ctypes.Array) else pauli_terms(terms)
+    nt = len(arr)
+    grad = np.zeros((batch, npar), dtype=np.float64)
+    val = np.zeros(batch, dtype=np.float64)
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    _check(load().sv_adjoint_grad(n, dtype, g.arr, g.n, pv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), batch,
+                                  npar, arr, nt, int(checkpoint_every),
+                                  grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st))
+    return val, grad

@@ -1,0 +1,350 @@
+// sv_adjoint_host.cpp -- sv_adjoint_grad: batched adjoint gradients with
+// state checkpoints.
+//
+// For each of B parameter vectors of one circuit template (Sec. 4.2: the
+// structure stays fixed while the parameter values change):
+//   1. forward pass psi = U_N .. U_1 |0>, storing psi after every
+//      `checkpoint_every` gates;
+//   2. lambda = H psi with H = sum_j c_j P_j applied matrix-free (Sec. 4.4);
+//      f = Re <psi|lambda>;
+//   3. reverse pass over the gates: each rotation adds Im <lambda|G|psi> to its
+//      slot's gradient, then psi and lambda are un-applied; at a checkpoint
+//      boundary psi is replaced by the stored forward state, so complex64
+//      uncompute drift never accumulates over more than `checkpoint_every`
+//      gates.  (The paper's own checkpointing discards and recomputes states,
+//      Sec. 7.3; here stored states re-anchor the uncompute.)
+// Per-state gate matrices are built on the host in double precision and
+// narrowed once (Sec. 3.3, Sec. 5.2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+bool is_rotation(int t) {
+  return t == SV_GATE_RX || t == SV_GATE_RY || t == SV_GATE_RZ || t == SV_GATE_P || t == SV_GATE_RXX ||
+         t == SV_GATE_RYY || t == SV_GATE_RZZ;
+}
+bool rotation_is_diagonal(int t) { return t == SV_GATE_RZ || t == SV_GATE_P || t == SV_GATE_RZZ; }
+
+// Generator G of U = exp(-i theta G / 2) on the targets: dense d x d, or the
+// d diagonal entries for the diagonal families.
+std::vector<cplx> generator_of(int t) {
+  const cplx j(0.0, 1.0);
+  switch (t) {
+    case SV_GATE_RX: return {0.0, 1.0, 1.0, 0.0};
+    case SV_GATE_RY: return {0.0, -j, j, 0.0};
+    case SV_GATE_RZ: return {1.0, -1.0};
+    case SV_GATE_P: return {0.0, -2.0};  // diag(1, e^{i t}) = exp(-i t (Z - I) / 2)
+    case SV_GATE_RZZ: return {1.0, -1.0, -1.0, 1.0};
+    case SV_GATE_RXX: {
+      std::vector<cplx> m(16, 0.0);
+      m[0 * 4 + 3] = m[1 * 4 + 2] = m[2 * 4 + 1] = m[3 * 4 + 0] = 1.0;
+      return m;
+    }
+    case SV_GATE_RYY: {
+      std::vector<cplx> m(16, 0.0);
+      m[0 * 4 + 3] = m[3 * 4 + 0] = -1.0;
+      m[1 * 4 + 2] = m[2 * 4 + 1] = 1.0;
+      return m;
+    }
+    default: return {};
+  }
+}
+
+struct AGate {
+  LOp op;               // kind / qubits / controls; m = U for constant gates
+  bool param = false;
+  int slot = -1;
+  int pidx = -1;        // index among the parameterised gates
+  std::vector<cplx> gen;
+};
+
+template <typename R>
+void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, const Sweep& sw, int n, int batch,
+                  int npg, bool reverse, BatchProgram<R>& P) {
+  std::memset(&P.h, 0, sizeof(P.h));
+  P.h.n = n;
+  P.h.m = sw.m;
+  P.h.L = sw.L;
+  P.h.batch = batch;
+  P.h.ngrad_total = npg;
+  int loc[64];
+  for (int q = 0; q < 64; q++) loc[q] = -1;
+  for (int i = 0; i < sw.m; i++) {
+    P.h.tq[i] = (int8_t)sw.tq[i];
+    loc[sw.tq[i]] = i;
+  }
+  int pool = 0, nacc = 0;
+  auto put = [&](const std::vector<cplx>& v) {
+    int at = pool;
+    for (const cplx& c : v) {
+      if (pool >= BatchProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: batch program pool overflow");
+      P.pool[pool].re = (R)c.real();
+      P.pool[pool].im = (R)c.imag();
+      pool++;
+    }
+    return at;
+  };
+  if ((int)sw.ops.size() > kBatchOps) fail(SV_ERR_INVALID, "internal: too many ops in a batch program");
+  for (size_t oi = 0; oi < sw.ops.size(); oi++) {
+    const AGate& g = ag[order[sw.ops[oi]]];
+    const LOp& op = g.op;
+    BOp d;
+    std::memset(&d, 0, sizeof(d));
+    d.kind = op.kind;
+    d.k = (uint8_t)op.k;
+    int sp[2], ns = 0;
+    for (int i = 0; i < op.k; i++) {
+      int l = loc[op.q[i]];
+      d.gq[i] = (uint8_t)op.q[i];
+      if (op.kind == OPK_DIAG) {
+        d.pos[i] = l < 0 ? 0xFF : (uint8_t)l;
+      } else {
+        if (l < 0) fail(SV_ERR_INVALID, "internal: target outside the tile");
+        d.pos[i] = (uint8_t)l;
+        sp[ns++] = l;
+      }
+    }
+    if (ns == 2 && sp[0] > sp[1]) std::swap(sp[0], sp[1]);
+    for (int i = 0; i < ns; i++) d.spos[i] = (uint8_t)sp[i];
+    for (int i = 0; i < op.nc; i++) {
+      int l = loc[op.c[i]];
+      if (l >= 0) {
+        d.lmask |= 1u << l;
+        if (op.cs[i]) d.lval |= 1u << l;
+      } else {
+        d.xmask |= 1ull << op.c[i];
+        if (op.cs[i]) d.xval |= 1ull << op.c[i];
+      }
+    }
+    d.dagger = reverse ? 1 : 0;
+    if (g.param) {
+      d.table = 1;
+      d.coef = (uint32_t)g.pidx;
+      if (reverse) {
+        if (nacc >= kBatchGacc) fail(SV_ERR_INVALID, "internal: too many gradient ops in a program");
+        d.grad = 1;
+        d.gacc = (uint8_t)nacc++;
+        d.gidx = (uint32_t)g.pidx;
+        d.gen = (uint32_t)put(g.gen);
+      }
+    } else {
+      d.coef = (uint32_t)put(op.m);
+    }
+    P.ops[oi] = d;
+  }
+  P.h.nops = (int)sw.ops.size();
+  P.h.ngacc = nacc;
+}
+
+template <typename R>
+void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const double* params, int batch, int npar,
+                 const sv_pauli_term* terms, size_t nterms, int ckpt, double* out_grad, double* out_value,
+                 cudaStream_t stream) {
+  // ---- lower the template
+  std::vector<AGate> ag(ng);
+  int npg = 0;
+  for (size_t i = 0; i < ng; i++) {
+    const sv_gate& g = gates[i];
+    bool any_slot = false;
+    const int nang = g.type == SV_GATE_U3 ? 3 : g.type == SV_GATE_U2 ? 2 : is_rotation(g.type) ? 1 : 0;
+    for (int a = 0; a < nang; a++)
+      if (g.param_slot[a] >= 0) any_slot = true;
+    if (g.n_targets > 2)
+      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) + ": the adjoint path takes gates of <= 2 targets");
+    AGate& a = ag[i];
+    if (any_slot) {
+      if (!is_rotation(g.type) || g.param_slot[0] < 0)
+        fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) +
+                                     ": a parameterised gate needs a generator, exp(-i theta G / 2) "
+                                     "(RX, RY, RZ, P, RXX, RYY, RZZ)");
+      a.param = true;
+      a.slot = g.param_slot[0];
+      a.pidx = npg++;
+      a.gen = generator_of(g.type);
+      LOp& op = a.op;
+      op.k = g.n_targets;
+      for (int t = 0; t < op.k; t++) op.q[t] = g.targets[t];
+      op.nc = g.n_controls;
+      for (int c = 0; c < op.nc; c++) {
+        op.c[c] = g.controls[c];
+        op.cs[c] = ((g.control_zero_mask >> c) & 1u) ? 0 : 1;
+      }
+      op.kind = rotation_is_diagonal(g.type) ? OPK_DIAG : OPK_DENSE;
+      op.touch = 0;
+      uint64_t tm = 0;
+      for (int t = 0; t < op.k; t++) tm |= 1ull << op.q[t];
+      for (int c = 0; c < op.nc; c++) op.touch |= 1ull << op.c[c];
+      op.touch |= tm;
+      op.need = op.kind == OPK_DIAG ? 0 : tm;
+      op.m.assign(op.kind == OPK_DIAG ? (1 << op.k) : (1 << (2 * op.k)), 0.0);  // sizes the pool use
+    } else {
+      a.op = lower_gate(g, nullptr, (int)i);
+      if (a.op.kind == OPK_REAL) a.op.kind = OPK_DENSE;
+    }
+    a.op.first_gate = (int)i;
+  }
+
+  // ---- per-state tables of the parameterised gates (double, then narrowed)
+  const size_t N = 1ull << n;
+  const size_t sbytes = sizeof(Cx<R>) * N * (size_t)batch;
+  std::vector<Cx<R>> table((size_t)std::max(npg, 1) * batch * kTableStride);
+  for (size_t i = 0; i < ng; i++) {
+    if (!ag[i].param) continue;
+    for (int b = 0; b < batch; b++) {
+      std::vector<cplx> U = gate_matrix(gates[i], params + (size_t)b * npar);
+      Cx<R>* row = &table[((size_t)ag[i].pidx * batch + b) * kTableStride];
+      int d = 1 << gates[i].n_targets;
+      if (ag[i].op.kind == OPK_DIAG)
+        for (int r = 0; r < d; r++) row[r] = {(R)U[r * d + r].real(), (R)U[r * d + r].imag()};
+      else
+        for (int e = 0; e < d * d; e++) row[e] = {(R)U[e].real(), (R)U[e].imag()};
+    }
+  }
+
+  // ---- device buffers (library-owned, per stream, grow-only)
+  const int c = ckpt > 0 ? ckpt : (int)ng + 1;
+  const int nck = ng > 0 ? (int)((ng - 1) / c) : 0;  // stored states after c, 2c, ... gates
+  const int tile_q = tile_qubits_for(dtype), low_q = low_qubits_for(dtype);
+  const int m = std::min(n, tile_q);
+  const int grid_x = batch_grid_x(n, m, batch);
+  Cx<R>* psi = (Cx<R>*)scratch_buffer(stream, "adj_psi", sbytes);
+  Cx<R>* lam = (Cx<R>*)scratch_buffer(stream, "adj_lam", sbytes);
+  Cx<R>* ck = nck ? (Cx<R>*)scratch_buffer(stream, "adj_ckpt", sbytes * nck) : nullptr;
+  Cx<R>* dtab = (Cx<R>*)scratch_buffer(stream, "adj_table", table.size() * sizeof(Cx<R>));
+  double* gscr = (double*)scratch_buffer(stream, "adj_gscratch", sizeof(double) * (size_t)batch * std::max(npg, 1) * grid_x);
+  double* gout = (double*)scratch_buffer(stream, "adj_gout", sizeof(double) * (size_t)batch * std::max(npg, 1));
+  double* dots = (double*)scratch_buffer(stream, "adj_dot", sizeof(double) * batch_dot_scratch_doubles(batch));
+  double* vout = (double*)scratch_buffer(stream, "adj_val", sizeof(double) * batch);
+  cuda_check(cudaMemcpyAsync(dtab, table.data(), table.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice, stream),
+             "table upload");
+
+  std::unique_ptr<BatchProgram<R>> prog(new BatchProgram<R>());
+  const int pool_cap = BatchProgram<R>::kPool / 2;
+  const double sweep_bytes_f = 2.0 * (double)sbytes, sweep_bytes_r = 4.0 * (double)sbytes;
+
+  // ---- forward, segment by segment
+  cuda_check(launch_batch_init<R>(psi, n, batch, stream), "batch init");
+  for (int seg = 0; (size_t)seg * c < ng; seg++) {
+    size_t g0 = (size_t)seg * c, g1 = std::min(ng, g0 + c);
+    std::vector<int> order;
+    std::vector<LOp> ops;
+    for (size_t i = g0; i < g1; i++) {
+      order.push_back((int)i);
+      ops.push_back(ag[i].op);
+    }
+    std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, pool_cap, 64);
+    for (const Sweep& sw : sws) {
+      fill_program<R>(ag, order, sw, n, batch, npg, false, *prog);
+      Prof pr(stream, "batch_sweep_fwd", sweep_bytes_f);
+      cuda_check(launch_batch_sweep<R>(psi, nullptr, dtab, gscr, grid_x, *prog, false, stream), "forward sweep");
+      pr.done();
+    }
+    if (g1 < ng && seg + 1 <= nck)
+      cuda_check(cudaMemcpyAsync(ck + (size_t)seg * N * batch, psi, sbytes, cudaMemcpyDeviceToDevice, stream),
+                 "checkpoint store");
+  }
+
+  // ---- lambda = H psi, grouped by x mask; f = Re <psi|lambda>
+  {
+    std::vector<char> used(nterms, 0);
+    bool first = true;
+    for (size_t t0 = 0; t0 < nterms; t0++) {
+      if (used[t0]) continue;
+      std::vector<uint64_t> zs;
+      std::vector<double> cs;
+      for (size_t t = t0; t < nterms; t++)
+        if (!used[t] && terms[t].x_mask == terms[t0].x_mask) {
+          used[t] = 1;
+          zs.push_back(terms[t].z_mask);
+          cs.push_back(terms[t].coeff);
+        }
+      Prof pr(stream, "pauli_accum", 3.0 * (double)sbytes);
+      cuda_check(launch_pauli_accum<R>(psi, lam, n, batch, terms[t0].x_mask, zs.data(), cs.data(), (int)zs.size(),
+                                       !first, stream),
+                 "H psi");
+      pr.done();
+      first = false;
+    }
+    cuda_check(launch_batch_dot<R>(psi, lam, n, batch, dots, vout, stream), "value");
+  }
+
+  // ---- reverse, segment by segment, re-anchoring psi at checkpoints
+  int nseg = ng ? (int)((ng + c - 1) / c) : 0;
+  for (int seg = nseg - 1; seg >= 0; seg--) {
+    size_t g0 = (size_t)seg * c, g1 = std::min(ng, g0 + c);
+    std::vector<int> order;
+    std::vector<LOp> ops;
+    for (size_t i = g1; i-- > g0;) {
+      order.push_back((int)i);
+      ops.push_back(ag[i].op);
+    }
+    std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, pool_cap, 64);
+    for (const Sweep& sw : sws) {
+      fill_program<R>(ag, order, sw, n, batch, npg, true, *prog);
+      Prof pr(stream, "batch_sweep_rev", sweep_bytes_r);
+      cuda_check(launch_batch_sweep<R>(psi, lam, dtab, gscr, grid_x, *prog, true, stream), "reverse sweep");
+      pr.done();
+    }
+    if (seg >= 1 && seg <= nck)  // psi is now psi after seg*c gates: take the stored copy
+      cuda_check(cudaMemcpyAsync(psi, ck + (size_t)(seg - 1) * N * batch, sbytes, cudaMemcpyDeviceToDevice, stream),
+                 "checkpoint load");
+  }
+  if (npg) cuda_check(launch_grad_finish(gscr, batch, npg, grid_x, gout, stream), "gradient reduce");
+
+  // ---- results to the host; slots shared by several gates add up
+  std::vector<double> gh((size_t)batch * std::max(npg, 1), 0.0);
+  if (npg)
+    cuda_check(cudaMemcpyAsync(gh.data(), gout, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost, stream),
+               "gradient copy");
+  cuda_check(cudaMemcpyAsync(out_value, vout, sizeof(double) * batch, cudaMemcpyDeviceToHost, stream), "value copy");
+  cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  std::fill(out_grad, out_grad + (size_t)batch * npar, 0.0);
+  for (size_t i = 0; i < ng; i++) {
+    if (!ag[i].param) continue;
+    for (int b = 0; b < batch; b++) out_grad[(size_t)b * npar + ag[i].slot] += gh[(size_t)b * npg + ag[i].pidx];
+  }
+}
+
+}  // namespace
+}  // namespace sv
+
+using namespace sv;
+
+extern "C" sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                     const double* params, int batch, int n_params, const sv_pauli_term* terms,
+                                     size_t n_terms, int checkpoint_every, double* out_grad, double* out_value,
+                                     void* stream) {
+  return guarded([&] {
+    if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+    if (n_qubits < 1 || n_qubits > 30) fail(SV_ERR_INVALID, "n_qubits must be in 1..30 for the adjoint");
+    if (batch < 1 || batch > 65535) fail(SV_ERR_INVALID, "batch must be in 1..65535");
+    if (n_params < 0) fail(SV_ERR_INVALID, "n_params must be >= 0");
+    if (n_params > 0 && !params) fail(SV_ERR_INVALID, "params is NULL");
+    if (checkpoint_every < 0) fail(SV_ERR_INVALID, "checkpoint_every must be >= 0");
+    if (n_terms < 1 || n_terms > 4096 || !terms) fail(SV_ERR_INVALID, "n_terms must be in 1..4096");
+    if (!out_grad && n_params > 0) fail(SV_ERR_INVALID, "out_grad is NULL");
+    if (!out_value) fail(SV_ERR_INVALID, "out_value is NULL");
+    const uint64_t all = (1ull << n_qubits) - 1ull;
+    for (size_t j = 0; j < n_terms; j++)
+      if ((terms[j].x_mask | terms[j].z_mask) & ~all)
+        fail(SV_ERR_INVALID, "term " + std::to_string(j) + " names a qubit beyond n_qubits");
+    validate_gates(n_qubits, gates, n_gates, (size_t)n_params);
+    for (int b = 0; b < batch; b++)
+      for (int p = 0; p < n_params; p++)
+        if (!std::isfinite(params[(size_t)b * n_params + p])) fail(SV_ERR_INVALID, "a parameter is not finite");
+    static double dummy_grad;
+    double* og = n_params > 0 ? out_grad : &dummy_grad;
+    if (dtype == SV_C64)
+      run_adjoint<float>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                         og, out_value, (cudaStream_t)stream);
+    else
+      run_adjoint<double>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                          og, out_value, (cudaStream_t)stream);
+  });
+}

@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <tuple>
 
 #include "sv_internal.h"
 
@@ -23,29 +24,6 @@ namespace sv {
 namespace {
 
 thread_local std::string g_last_error;
-
-[[noreturn]] void fail(sv_status s, const std::string& m) { throw Error{s, m}; }
-
-void cuda_check(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) fail(SV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-template <typename F>
-sv_status guarded(F&& f) {
-  try {
-    f();
-    return SV_OK;
-  } catch (const Error& e) {
-    g_last_error = e.msg;
-    return e.status;
-  } catch (const std::bad_alloc&) {
-    g_last_error = "host allocation failed";
-    return SV_ERR_OOM;
-  } catch (...) {
-    g_last_error = "unexpected host exception";
-    return SV_ERR_INVALID;
-  }
-}
 
 size_t amp_bytes(sv_dtype d) { return d == SV_C64 ? 8 : 16; }
 
@@ -71,6 +49,10 @@ AddrRangeFn addr_range_fn() {
   return fn;
 }
 
+}  // namespace
+
+void set_last_error(const std::string& m) { g_last_error = m; }
+
 void check_device_buffer(const void* p, size_t bytes, const char* what) {
   if (!p) fail(SV_ERR_INVALID, std::string(what) + " is NULL");
   if ((uintptr_t)p % 16) fail(SV_ERR_INVALID, std::string(what) + " is not 16-byte aligned");
@@ -95,6 +77,8 @@ void check_device_buffer(const void* p, size_t bytes, const char* what) {
     }
   }
 }
+
+namespace {
 
 // ----------------------------------------------------------- scratch per stream
 
@@ -140,6 +124,21 @@ Workspace& workspace(cudaStream_t stream, size_t scratch_doubles, size_t out_dou
   if (state_bytes) grow(&w.state, &w.state_cap, state_bytes, stream, "state buffer");
   return w;
 }
+
+std::map<std::tuple<int, cudaStream_t, std::string>, std::pair<void*, size_t>> g_named;
+
+}  // namespace
+
+void* scratch_buffer(cudaStream_t stream, const char* name, size_t bytes) {
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto& e = g_named[std::make_tuple(dev, stream, std::string(name))];
+  grow(&e.first, &e.second, bytes < 256 ? 256 : bytes, stream, name);
+  return e.first;
+}
+
+namespace {
 
 // ----------------------------------------------------------- kernel timing
 
@@ -545,6 +544,8 @@ sv_status sv_release_scratch(void) {
       cudaFree(kv.second.state);
     }
     g_ws.clear();
+    for (auto& kv : g_named) cudaFree(kv.second.first);
+    g_named.clear();
   });
 }
 

@@ -72,6 +72,54 @@ struct SweepProgram {
   Cx<R> coef[kPool];
 };
 
+// ----------------------------------------------------------------- batched programs
+//
+// The adjoint gradient runs B states of one circuit template side by side
+// (Sec. 4.1 BatchSV: a batch of states evolved together; parameter values
+// differ per state).  A batched op takes its coefficients either from the
+// program pool (constant gates) or from a per-state table built on the host in
+// double precision (parameterised gates).  In reverse mode each op first adds
+// Im <lambda|G|psi> over the tile (G the gate's generator, with its control
+// projector) and then applies the conjugate transpose to psi and lambda.
+
+struct BOp {
+  uint8_t kind;         // OPK_DENSE / OPK_DIAG / OPK_ANTIDIAG / OPK_SWAP, k <= 2
+  uint8_t k;
+  uint8_t pos[2];       // local positions (matrix order); OPK_DIAG: 0xFF = external
+  uint8_t spos[2];      // sorted local positions
+  uint8_t gq[2];        // global qubits (OPK_DIAG external bits)
+  uint8_t table;        // 1: coefficients from the per-state table row `coef`
+  uint8_t dagger;       // 1: apply the conjugate transpose
+  uint8_t grad;         // 1: accumulate Im <lambda|G|psi> into gradient `gidx`
+  uint8_t gacc;         // local accumulator index of a gradient op
+  uint32_t lmask, lval;
+  uint64_t xmask, xval;
+  uint32_t coef;        // pool offset, or table row when `table`
+  uint32_t gen;         // pool offset of the generator (d x d dense, or d diagonal entries)
+  uint32_t gidx;        // index of the parameterised gate (gradient scratch row)
+  uint32_t pad;
+};
+static_assert(sizeof(BOp) == 56, "BOp layout");
+
+constexpr int kBatchOps = 128;
+constexpr int kBatchGacc = 64;   // gradient accumulators per program
+constexpr int kTableStride = 16; // complex entries per (gate, state) table row
+
+struct BatchHeader {
+  int32_t n, m, L, nops;
+  int32_t batch, ngacc, ngrad_total, pad;
+  int8_t tq[16];
+};
+
+template <typename R>
+struct BatchProgram {
+  static constexpr int kPool =
+      (kProgramBytes - (int)sizeof(BatchHeader) - kBatchOps * (int)sizeof(BOp)) / (int)sizeof(Cx<R>);
+  BatchHeader h;
+  BOp ops[kBatchOps];
+  Cx<R> pool[kPool];
+};
+
 // ----------------------------------------------------------------- host plan
 
 // A gate after lowering (a matrix in double precision) or a fused block.
@@ -107,6 +155,36 @@ struct Error {
   std::string msg;
 };
 
+[[noreturn]] inline void fail(sv_status s, const std::string& m) { throw Error{s, m}; }
+inline void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(SV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+void set_last_error(const std::string& m);
+
+// Runs f, mapping sv::Error and host exceptions to an sv_status.
+template <typename F>
+sv_status guarded(F&& f) {
+  try {
+    f();
+    return SV_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return SV_ERR_OOM;
+  } catch (...) {
+    set_last_error("unexpected host exception");
+    return SV_ERR_INVALID;
+  }
+}
+
+// Device pointer checks (device/managed memory of the current device, 16-byte
+// aligned, inside its allocation) and library-owned scratch: one grow-only
+// buffer per (device, stream, name).
+void check_device_buffer(const void* p, size_t bytes, const char* what);
+void* scratch_buffer(cudaStream_t stream, const char* name, size_t bytes);
+
 // Lowering (gate records -> double-precision matrices), the paper's greedy
 // fusion, and the tile scheduler.  Throw sv::Error on invalid input.
 void validate_gates(int n, const sv_gate* gates, size_t n_gates, size_t n_param_values);
@@ -140,6 +218,27 @@ template <typename R>
 cudaError_t launch_expect_terms(const Cx<R>* state, int n, const sv_pauli_term* terms, int n_terms, double* scratch,
                                 size_t scratch_doubles, double* out, cudaStream_t stream);
 size_t expect_z_all_scratch_doubles(int n);
+
+// Batched kernels (sv_adjoint.cu).  psi/lam hold `batch` states of 2^n
+// amplitudes back to back.  `table` is [gates][batch][kTableStride].
+template <typename R>
+cudaError_t launch_batch_sweep(Cx<R>* psi, Cx<R>* lam, const Cx<R>* table, double* gscratch, int grid_x,
+                               const BatchProgram<R>& prog, bool reverse, cudaStream_t stream);
+int batch_grid_x(int n, int m, int batch);
+template <typename R>
+cudaError_t launch_batch_init(Cx<R>* psi, int n, int batch, cudaStream_t stream);
+// lam (=|+=) sum_j c_j P_j psi over the terms sharing one x mask
+template <typename R>
+cudaError_t launch_pauli_accum(const Cx<R>* psi, Cx<R>* lam, int n, int batch, uint64_t x, const uint64_t* z,
+                               const double* c, int nt, bool accumulate, cudaStream_t stream);
+// out[b] = Re <psi_b|lam_b> (partials in scratch: batch x grid doubles)
+template <typename R>
+cudaError_t launch_batch_dot(const Cx<R>* psi, const Cx<R>* lam, int n, int batch, double* scratch, double* out,
+                             cudaStream_t stream);
+size_t batch_dot_scratch_doubles(int batch);
+// out[b * ngrad + g] = sum over grid_x of gscratch[(b * ngrad + g) * grid_x + c]
+cudaError_t launch_grad_finish(const double* gscratch, int batch, int ngrad, int grid_x, double* out,
+                               cudaStream_t stream);
 size_t expect_terms_scratch_doubles(int n, int n_terms);
 
 int device_sm_count();

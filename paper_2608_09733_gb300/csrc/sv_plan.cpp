@@ -26,8 +26,6 @@ const int kTargetsOf[SV_GATE_COUNT_] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1,  // I..SX
                                         -1};                           // UNITARY
 const int kAnglesOf[SV_GATE_COUNT_] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 3, 0, 1, 1, 1, 0};
 
-[[noreturn]] void fail(sv_status s, const std::string& m) { throw Error{s, m}; }
-
 uint64_t gate_qubit_mask(const sv_gate& g) {
   uint64_t m = 0;
   for (int i = 0; i < g.n_targets; i++) m |= 1ull << g.targets[i];
