@@ -54,6 +54,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="oracle sample size (0 = auto)")
+    ap.add_argument("--workload", choices=["gates", "adjoint", "serving"], default="gates")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--seq-duration", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -227,6 +232,75 @@ def read_traffic(kernel: str, stamp: str):
     return tr if (tr is not None and st == stamp) else None
 
 
+# ------------------------------------------------------------------ other workloads
+
+def bench_adjoint(args):
+    """20-qubit hardware-efficient ansatz, 10 layers (400 parameters), H =
+    sum Z_i Z_i+1 + 0.7 sum X_i, batch of 64 parameter vectors, complex64,
+    checkpoints every 2 layers: full gradient vectors per second, batched vs
+    one vector per call."""
+    import torch
+    import paper_2608_09733_gb300 as sv
+    from workloads import hea_hamiltonian, hea_params, hea_ring
+    n, layers, batch = 20, 10, args.batch
+    gates = sv.Gates(hea_ring(n, layers))
+    terms = sv.pauli_terms(hea_hamiltonian(n, 0.7))
+    P = 2 * n * layers
+    th = hea_params(batch, P, seed=0)
+    ck = 2 * 3 * n
+    for _ in range(args.warmup):
+        sv.sv_adjoint_grad(n, sv.SV_C64, gates, th, terms, checkpoint_every=ck)
+    sv.sv_profile_enable(True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sv.sv_adjoint_grad(n, sv.SV_C64, gates, th, terms, checkpoint_every=ck)
+    t = time.perf_counter() - t0
+    prof = sv.sv_profile_read(reset=True)
+    sv.sv_profile_enable(False)
+    # one vector per call (the plain path), a few rows
+    rows = min(8, batch)
+    sv.sv_adjoint_grad(n, sv.SV_C64, gates, th[:1], terms, checkpoint_every=ck)
+    t1 = time.perf_counter()
+    for b in range(rows):
+        sv.sv_adjoint_grad(n, sv.SV_C64, gates, th[b:b + 1], terms, checkpoint_every=ck)
+    t1 = time.perf_counter() - t1
+    peaks, src = measured_peaks()
+    rev = prof.get("batch_sweep_rev", {"bytes": 0, "total_ms": float("nan"), "launches": 0})
+    gbs = rev["bytes"] / (rev["total_ms"] / 1e3) / 1e9 if rev["launches"] else None
+    print(json.dumps({
+        "metric": "adjoint grads/s (20q HEA, 400 params, batch 64, c64)", "value": args.steps * batch / t,
+        "unit": "grads/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "hea_adjoint_20q_10layers_batch%d_ckpt2layers" % batch},
+        "one_vector_per_call_grads_per_s": rows / t1,
+        "roofline": {"bound": "hbm", "kernel": "k_batch_sweep<reverse>", "achieved": gbs,
+                     "peak": float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)), "unit": "GB/s",
+                     "frac": gbs / float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if gbs else None},
+        "kernels": prof}), flush=True)
+
+
+def bench_serving(args):
+    """Poisson arrivals (default 2000 req/s for 60 s) of layered U3 + CNOT
+    ladder circuits, n uniform 8..26, depth 5..40, sum <Z_i> each, complex64,
+    150 GB admission budget; against one request at a time."""
+    import paper_2608_09733_gb300 as sv
+    from paper_2608_09733_gb300.serving import Server, run_sequential
+    from workloads import serving_stream
+    stream = serving_stream(rate=args.rate, duration=args.duration, seed=0)
+    warm = serving_stream(rate=200.0, duration=0.2, seed=99)
+    srv = Server(sv.SV_C64, budget_bytes=150e9)
+    srv.run(warm)
+    stats, _ = srv.run(stream, time_limit=args.duration + 30.0)
+    seq_stream = [r for r in stream if r[0] < args.seq_duration]
+    seq, _ = run_sequential(seq_stream, sv.SV_C64, time_limit=args.seq_duration + 30.0)
+    print(json.dumps({
+        "metric": "serving req/s + p99 (Poisson %.0f req/s, n 8-26, depth 5-40, c64)" % args.rate,
+        "value": stats.req_per_s, "unit": "req/s", "n_gpus": 1, "higher_is_better": True, "dtype": "c64",
+        "data": "synthetic", "config": {"workload": "serving_poisson_%.0fhz_%.0fs" % (args.rate, args.duration),
+                                        "budget_gb": 150},
+        "served": stats.as_dict(), "sequential": seq.as_dict()}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -234,6 +308,14 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload != "gates":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2608_09733_gb300 import build as _build
+        _build.build()
+        if rank == 0:
+            (bench_adjoint if args.workload == "adjoint" else bench_serving)(args)
         return
 
     import numpy as np

@@ -217,6 +217,21 @@ sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, si
                           int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
                           double* out_grad, double* out_value, void* stream);
 
+/* ---- serving: packed small states -------------------------------------------
+ * Runs many small independent circuits in ONE kernel launch: request b gets one
+ * CTA that keeps its whole state (2^n amplitudes, n <= SV_SMALL_MAX_QUBITS) in
+ * shared memory from |0..0> to the end, applies its gates (the same lowering,
+ * fast paths and register phases as sv_apply_circuit) and writes
+ * out_sum_z[b] = sum_q <Z_q>.  Small states never touch HBM; this packs the
+ * launch-bound small requests of a serving stream (the paper's NPU runs of small
+ * states were launch-bound, Sec. 9.3).
+ *   n_qubits[b], gates[b], n_gates[b]  request b (host arrays, no slots)
+ *   out_sum_z  n_requests doubles, host (call synchronizes) or device (async)
+ * Library-owned pinned staging and device program buffers are kept per stream. */
+#define SV_SMALL_MAX_QUBITS 12
+sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits, const sv_gate* const* gates,
+                             const size_t* n_gates, double* out_sum_z, int out_on_device, void* stream);
+
 /* End-to-end call on HOST buffers: copies `state_in` (host, 2^n amplitudes of
  * dtype; NULL means |0..0>) to a library-owned device buffer, applies the
  * circuit as sv_apply_circuit does, evaluates <Z_q> for all qubits into

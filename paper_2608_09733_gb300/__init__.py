@@ -27,6 +27,9 @@ from .binding import (  # noqa: F401
     sv_profile_read,
     sv_release_scratch,
     sv_run_host,
+    sv_run_batch_small,
+    GateArray,
+    layered_u3_cnot_gates,
     sv_version,
 )
 

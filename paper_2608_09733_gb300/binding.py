@@ -34,7 +34,7 @@ GATE_TYPES = {
 EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "sv_apply_circuit_ex", "sv_expect",
            "sv_expect_z_all",
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
-           "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad"]
+           "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small"]
 
 
 class SvError(RuntimeError):
@@ -106,6 +106,7 @@ def load():
             "sv_release_scratch": ([], ci),
             "sv_profile_enable": ([ci], ci),
             "sv_adjoint_grad": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(SvPauliTerm), sz, ci, P(cd), P(cd), vp], ci),
+            "sv_run_batch_small": ([ci, ci, P(ci), P(P(SvGate)), P(sz), vp, ci, vp], ci),
             "sv_profile_read": ([P(SvProfileEntry), ci, P(ci), ci], ci),
         }
         for name, (args, res) in sig.items():
@@ -122,6 +123,51 @@ def _check(status: int):
 
 
 # ---------------------------------------------------------------- marshalling
+
+# numpy view of SvGate with the same field offsets (the matrix pointer as u8)
+GATE_DTYPE = np.dtype({
+    "names": ["type", "n_targets", "targets", "n_controls", "controls", "control_zero_mask", "param_slot", "params",
+              "matrix"],
+    "formats": ["<i4", "<i4", ("<i4", 5), "<i4", ("<i4", 5), "<u4", ("<i4", 3), ("<f8", 3), "<u8"],
+    "offsets": [getattr(SvGate, f).offset for f in ("type", "n_targets", "targets", "n_controls", "controls",
+                                                     "control_zero_mask", "param_slot", "params", "matrix")],
+    "itemsize": ctypes.sizeof(SvGate),
+})
+
+
+class GateArray:
+    """SvGate records held in a numpy structured array (built without a
+    per-gate Python loop); quacks like ``Gates``."""
+
+    def __init__(self, arr: np.ndarray):
+        assert arr.dtype == GATE_DTYPE
+        self.np = np.ascontiguousarray(arr)
+        self.n = len(self.np)
+        self.arr = self.np.ctypes.data_as(ctypes.POINTER(SvGate))
+
+
+def layered_u3_cnot_gates(n: int, angles: np.ndarray) -> GateArray:
+    """Gate records of ``depth`` layers of U3(angles[d, q]) on every qubit
+    followed by the CNOT ladder q -> q+1 (the serving workload's circuit)."""
+    depth = angles.shape[0]
+    per = 2 * n - 1
+    a = np.zeros(depth * per, dtype=GATE_DTYPE)
+    a["param_slot"][:] = -1
+    base = (np.arange(depth) * per)[:, None]
+    u3 = (base + np.arange(n)[None, :]).ravel()
+    a["type"][u3] = GATE_TYPES["u3"]
+    a["n_targets"][u3] = 1
+    a["targets"][u3, 0] = np.tile(np.arange(n), depth)
+    a["params"][u3] = angles.reshape(-1, 3)
+    if n > 1:
+        cx = (base + n + np.arange(n - 1)[None, :]).ravel()
+        a["type"][cx] = GATE_TYPES["x"]
+        a["n_targets"][cx] = 1
+        a["targets"][cx, 0] = np.tile(np.arange(1, n), depth)
+        a["n_controls"][cx] = 1
+        a["controls"][cx, 0] = np.tile(np.arange(n - 1), depth)
+    return GateArray(a)
+
 
 class Gates:
     """A ctypes array of SvGate built from gate records (workloads.Gate or any
@@ -211,7 +257,7 @@ def sv_init_basis(state, basis_index: int = 0, stream=None):
 
 
 def sv_apply_circuit(state, gates, param_values=None, fuse_max_k: int = 0, stream=None):
-    g = gates if isinstance(gates, Gates) else Gates(gates)
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     _check(load().sv_apply_circuit(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), g.arr, g.n,
                                    pp, npv, int(fuse_max_k), _stream(stream)))
@@ -225,7 +271,7 @@ def _opts(fuse_max_k=0, block_mode=0, ops_per_pass=0):
 
 def sv_apply_circuit_ex(state, gates, param_values=None, fuse_max_k: int = 0, block_mode: int = 0,
                         ops_per_pass: int = 0, stream=None):
-    g = gates if isinstance(gates, Gates) else Gates(gates)
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     o = _opts(fuse_max_k, block_mode, ops_per_pass)
     _check(load().sv_apply_circuit_ex(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), g.arr, g.n,
@@ -264,7 +310,7 @@ def sv_expect_z_all(state, out=None, stream=None):
 def sv_plan_info(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, block_mode: int = 0,
                  ops_per_pass: int = 0):
     """(number of blocks, number of HBM passes, block start indices)."""
-    g = gates if isinstance(gates, Gates) else Gates(gates)
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     nb, ns = ctypes.c_int(), ctypes.c_int()
     starts = (ctypes.c_int * (g.n + 1))()
@@ -277,7 +323,7 @@ def sv_plan_info(n: int, dtype: int, gates, param_values=None, fuse_max_k: int =
 def sv_run_host(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, state_in=None,
                 state_out=None, stream=None) -> np.ndarray:
     """End-to-end on host buffers (numpy): returns (<Z_q>..., sum)."""
-    g = gates if isinstance(gates, Gates) else Gates(gates)
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     out = np.zeros(n + 1, dtype=np.float64)
     sin = ctypes.c_void_p(state_in.ctypes.data) if state_in is not None else None
@@ -343,7 +389,7 @@ def sv_profile_read(reset: bool = True) -> dict:
 def sv_adjoint_grad(n: int, dtype: int, gates, params, terms, checkpoint_every: int = 0, stream=None):
     """(values (batch,), gradients (batch, n_params)) for a (batch, n_params)
     array of parameter vectors (host float64)."""
-    g = gates if isinstance(gates, Gates) else Gates(gates)
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pv = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
     if pv.ndim == 1:
         pv = pv.reshape(1, -1)
@@ -358,3 +404,21 @@ def sv_adjoint_grad(n: int, dtype: int, gates, params, terms, checkpoint_every: 
                                   grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                   val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st))
     return val, grad
+
+
+def sv_run_batch_small(n_qubits, gate_sets, dtype: int = SV_C64, out=None, stream=None):
+    """Packed launch of small requests: gate_sets[b] (Gates/GateArray or a
+    gate list) on n_qubits[b] qubits; returns sum_q <Z_q> per request (host),
+    or writes them into the device float64 tensor ``out`` (async)."""
+    nreq = len(gate_sets)
+    gs = [g if isinstance(g, (Gates, GateArray)) else Gates(g) for g in gate_sets]
+    nq = (ctypes.c_int * nreq)(*[int(x) for x in n_qubits])
+    ptrs = (ctypes.POINTER(SvGate) * nreq)(*[ctypes.cast(g.arr, ctypes.POINTER(SvGate)) for g in gs])
+    ng = (ctypes.c_size_t * nreq)(*[g.n for g in gs])
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    if out is None:
+        host = np.zeros(nreq, dtype=np.float64)
+        _check(load().sv_run_batch_small(nreq, dtype, nq, ptrs, ng, host.ctypes.data_as(ctypes.c_void_p), 0, st))
+        return host
+    _check(load().sv_run_batch_small(nreq, dtype, nq, ptrs, ng, ctypes.c_void_p(out.data_ptr()), 1, st))
+    return out

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -140,6 +142,36 @@ void* scratch_buffer(cudaStream_t stream, const char* name, size_t bytes) {
 
 namespace {
 
+// Pinned host staging per (device, stream, name), grow-only; `ready` is
+// recorded after the last copy out of it, so a rewrite waits for that copy.
+struct Pinned {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ready = nullptr;
+};
+std::map<std::tuple<int, cudaStream_t, std::string>, Pinned> g_pinned;
+
+Pinned& pinned_buffer(cudaStream_t stream, const char* name, size_t bytes) {
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Pinned& pb = g_pinned[std::make_tuple(dev, stream, std::string(name))];
+  if (!pb.ready) cuda_check(cudaEventCreateWithFlags(&pb.ready, cudaEventDisableTiming), "cudaEventCreate");
+  cuda_check(cudaEventSynchronize(pb.ready), "cudaEventSynchronize");
+  if (pb.cap < bytes) {
+    if (pb.p) cudaFreeHost(pb.p);
+    pb.p = nullptr;
+    pb.cap = 0;
+    cudaError_t e = cudaHostAlloc(&pb.p, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(SV_ERR_OOM, std::string("cudaHostAlloc of ") + name + " failed");
+    }
+    pb.cap = bytes;
+  }
+  return pb;
+}
+
 // ----------------------------------------------------------- kernel timing
 
 struct ProfRec {
@@ -176,6 +208,10 @@ namespace {
 
 // ----------------------------------------------------------- programs
 
+// Converts one sweep of the plan into the kernel's program: each op gets local
+// positions and control masks; consecutive ops whose moving qubits fit four
+// register slots form one register phase; dense k >= 3 blocks and wide
+// diagonals get a shared-memory phase of their own.
 template <typename R>
 void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
   std::memset(&P.h, 0, sizeof(P.h));
@@ -189,23 +225,36 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
     P.h.tq[i] = (int8_t)sw.tq[i];
     loc[sw.tq[i]] = i;
   }
-  int coef = 0;
+  const bool reg_ok = sw.m >= kRegQ && sw.m - kRegQ <= 8;
+  struct Tmp {
+    DevOp d;
+    std::vector<cplx> m;
+    bool smem;
+    uint32_t need;  // local positions that must be register slots
+  };
+  std::vector<Tmp> ts(sw.ops.size());
   for (size_t oi = 0; oi < sw.ops.size(); oi++) {
     const LOp& op = plan.ops[sw.ops[oi]];
-    DevOp d;
+    Tmp& t = ts[oi];
+    DevOp& d = t.d;
     std::memset(&d, 0, sizeof(d));
     d.kind = op.kind;
     d.k = (uint8_t)op.k;
+    t.m = op.m;
+    t.need = 0;
+    for (int i = 0; i < 5; i++) d.rs[i] = 0xFF;
     int sp[5], ns = 0;
+    const bool diag = op.kind == OPK_DIAG;
     for (int i = 0; i < op.k; i++) {
       int l = loc[op.q[i]];
       d.gq[i] = (uint8_t)op.q[i];
-      if (op.kind == OPK_DIAG) {
+      if (diag) {
         d.pos[i] = l < 0 ? 0xFF : (uint8_t)l;
       } else {
         if (l < 0) fail(SV_ERR_INVALID, "internal: target outside the tile");
         d.pos[i] = (uint8_t)l;
         sp[ns++] = l;
+        t.need |= 1u << l;
       }
     }
     for (int i = 1; i < ns; i++)
@@ -221,16 +270,137 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
         if (op.cs[i]) d.xval |= 1ull << op.c[i];
       }
     }
-    d.coef = (uint32_t)coef;
-    for (const cplx& v : op.m) {
+    if (diag) {
+      // diag(1, .., 1, -1): a sign flip where every matrix bit is 1 (Z, CZ, CCZ)
+      const int dd = 1 << op.k;
+      bool sign = true;
+      for (int r = 0; r < dd; r++)
+        if (op.m[r] != (r == dd - 1 ? cplx(-1.0) : cplx(1.0))) sign = false;
+      if (sign) {
+        d.kind = OPK_SIGN;
+        t.m.clear();
+        for (int i = 0; i < op.k; i++) {
+          if (d.pos[i] != 0xFF) {
+            d.lmask |= 1u << d.pos[i];
+            d.lval |= 1u << d.pos[i];
+          } else {
+            d.xmask |= 1ull << op.q[i];
+            d.xval |= 1ull << op.q[i];
+          }
+        }
+      }
+    }
+    if (op.kind == OPK_ANTIDIAG && op.m.size() == 2 && op.m[0] == cplx(1.0) && op.m[1] == cplx(1.0)) d.pad = 1;
+    const bool wide = (op.kind == OPK_DENSE || op.kind == OPK_REAL) ? op.k >= 3 : (diag && d.kind == OPK_DIAG && op.k >= 3);
+    t.smem = !reg_ok || wide;
+  }
+
+  // phases
+  int nph = 0;
+  auto add_phase = [&](PhaseKind kind, int first, int nops, uint32_t need) {
+    if (nph >= kMaxPhases) fail(SV_ERR_INVALID, "internal: too many phases");
+    Phase& ph = P.ph[nph++];
+    std::memset(&ph, 0, sizeof(ph));
+    ph.kind = kind;
+    ph.first = (uint8_t)first;
+    ph.nops = (uint8_t)nops;
+    if (kind != PH_REG) return;
+    // register slots: the needed positions, then local bit 0 (16-byte
+    // shared-memory accesses), then the highest free positions
+    uint32_t rp = need;
+    if (__builtin_popcount(rp) < kRegQ && !(rp & 1u)) rp |= 1u;
+    for (int q = sw.m - 1; q >= 0 && __builtin_popcount(rp) < kRegQ; q--) rp |= 1u << q;
+    int slot_of[32];
+    int ns2 = 0, nt = 0;
+    for (int q = 0; q < sw.m; q++) {
+      if ((rp >> q) & 1u) {
+        slot_of[q] = ns2;
+        ph.rp[ns2++] = (uint8_t)q;
+      } else {
+        slot_of[q] = -1;
+        ph.tpos[nt++] = (uint8_t)q;
+      }
+    }
+    ph.ntpos = (uint8_t)nt;
+    for (int o = first; o < first + nops; o++) {
+      Tmp& t = ts[o];
+      DevOp& d = t.d;
+      for (int i = 0; i < d.k; i++)
+        d.rs[i] = (d.pos[i] != 0xFF && slot_of[d.pos[i]] >= 0) ? (uint8_t)slot_of[d.pos[i]] : 0xFF;
+      d.rmask = d.rval = 0;
+      d.tmask = d.tval = 0;
+      for (int q = 0; q < sw.m; q++) {
+        if (!((d.lmask >> q) & 1u)) continue;
+        const bool v = (d.lval >> q) & 1u;
+        if (slot_of[q] >= 0) {
+          d.rmask |= 1u << slot_of[q];
+          if (v) d.rval |= 1u << slot_of[q];
+        } else {
+          d.tmask |= 1u << q;
+          if (v) d.tval |= 1u << q;
+        }
+      }
+      // two-qubit register ops want rs[0] < rs[1]: swap the matrix qubit order
+      if (d.k == 2 && d.kind != OPK_DIAG && d.kind != OPK_SIGN && d.rs[0] > d.rs[1]) {
+        std::swap(d.rs[0], d.rs[1]);
+        std::swap(d.pos[0], d.pos[1]);
+        std::swap(d.gq[0], d.gq[1]);
+        if (t.m.size() == 16) {
+          std::vector<cplx> mt(16);
+          auto sw2 = [](int x) { return ((x & 1) << 1) | ((x >> 1) & 1); };
+          for (int r = 0; r < 4; r++)
+            for (int c = 0; c < 4; c++) mt[r * 4 + c] = t.m[sw2(r) * 4 + sw2(c)];
+          t.m = mt;
+        }
+      }
+    }
+  };
+  int cur_first = -1, cur_n = 0;
+  uint32_t cur_need = 0;
+  for (int o = 0; o < (int)ts.size(); o++) {
+    if (ts[o].smem) {
+      if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
+      cur_n = 0;
+      cur_need = 0;
+      add_phase(PH_SMEM, o, 1, 0);
+      continue;
+    }
+    if (cur_n && __builtin_popcount(cur_need | ts[o].need) <= kRegQ && cur_n < 255) {
+      cur_need |= ts[o].need;
+      cur_n++;
+    } else {
+      if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
+      cur_first = o;
+      cur_n = 1;
+      cur_need = ts[o].need;
+    }
+  }
+  if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
+  P.h.nphases = nph;
+
+  int coef = 0;
+  for (size_t oi = 0; oi < ts.size(); oi++) {
+    ts[oi].d.coef = (uint32_t)coef;
+    for (const cplx& v : ts[oi].m) {
       if (coef >= SweepProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: coefficient pool overflow");
       P.coef[coef].re = (R)v.real();
       P.coef[coef].im = (R)v.imag();
       coef++;
     }
-    P.ops[oi] = d;
+    P.ops[oi] = ts[oi].d;
   }
   P.h.ncoef = coef;
+  static const bool debug = std::getenv("SV_DEBUG_PLAN") != nullptr;
+  if (debug) {
+    std::fprintf(stderr, "[sv plan] sweep m=%d L=%d ops=%d phases=%d:", sw.m, sw.L, P.h.nops, nph);
+    for (int p = 0; p < nph; p++) {
+      std::fprintf(stderr, " %s(", P.ph[p].kind == PH_REG ? "R" : "S");
+      for (int o = P.ph[p].first; o < P.ph[p].first + P.ph[p].nops; o++)
+        std::fprintf(stderr, "%s%d%s", o > P.ph[p].first ? "," : "", (int)P.ops[o].kind, P.ops[o].k > 1 ? "w" : "");
+      std::fprintf(stderr, ")");
+    }
+    std::fprintf(stderr, "\n");
+  }
 }
 
 template <typename R>
@@ -394,6 +564,10 @@ sv_status sv_plan_info(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_
                        int* out_blocks, int* out_sweeps, int* block_starts) {
   return guarded([&] {
     Plan plan = make_plan(n_qubits, dtype, gates, n_gates, param_values, n_param_values, opts_of(opts));
+    if (std::getenv("SV_DEBUG_PLAN")) {  // print the device programs (host only)
+      std::unique_ptr<SweepProgram<float>> pf(new SweepProgram<float>());
+      for (const Sweep& sw : plan.sweeps) build_program<float>(plan, sw, *pf);
+    }
     int nb = (int)plan.block_starts.size() - 1;
     if (out_blocks) *out_blocks = nb;
     if (out_sweeps) *out_sweeps = (int)plan.sweeps.size();
@@ -533,6 +707,77 @@ sv_status sv_profile_read(sv_profile_entry* out, int max_entries, int* n_out, in
   });
 }
 
+}  // extern "C"
+
+namespace sv {
+namespace {
+template <typename R>
+void run_batch_small(int nreq, sv_dtype dtype, const int* nq, const sv_gate* const* gates, const size_t* ng,
+                     double* out, int out_on_device, cudaStream_t stream) {
+  std::vector<Plan> plans;
+  plans.reserve(nreq);
+  size_t nprog = 0;
+  int max_n = 1;
+  sv_exec_opts o;
+  std::memset(&o, 0, sizeof(o));
+  for (int b = 0; b < nreq; b++) {
+    plans.push_back(make_plan(nq[b], dtype, gates[b], ng[b], nullptr, 0, o, nq[b]));
+    nprog += plans.back().sweeps.size();
+    max_n = std::max(max_n, nq[b]);
+  }
+  const size_t prog_bytes = sizeof(SweepProgram<R>) * nprog;
+  const size_t idx_bytes = sizeof(int) * (2 * (size_t)nreq + 1);
+  const size_t total = prog_bytes + idx_bytes;
+  Pinned& pb = pinned_buffer(stream, "small_batch_staging", total);
+  SweepProgram<R>* hp = reinterpret_cast<SweepProgram<R>*>(pb.p);
+  int* hfirst = reinterpret_cast<int*>(reinterpret_cast<char*>(pb.p) + prog_bytes);
+  int* hnq = hfirst + nreq + 1;
+  size_t k = 0;
+  for (int b = 0; b < nreq; b++) {
+    hfirst[b] = (int)k;
+    hnq[b] = nq[b];
+    for (const Sweep& sw : plans[b].sweeps) build_program<R>(plans[b], sw, hp[k++]);
+  }
+  hfirst[nreq] = (int)k;
+  char* dbuf = (char*)scratch_buffer(stream, "small_batch_programs", total);
+  cuda_check(cudaMemcpyAsync(dbuf, pb.p, total, cudaMemcpyHostToDevice, stream), "program upload");
+  cuda_check(cudaEventRecord(pb.ready, stream), "cudaEventRecord");
+  const SweepProgram<R>* dp = reinterpret_cast<const SweepProgram<R>*>(dbuf);
+  const int* dfirst = reinterpret_cast<const int*>(dbuf + prog_bytes);
+  const int* dnq = dfirst + nreq + 1;
+  double* dout = out_on_device ? out : (double*)scratch_buffer(stream, "small_batch_out", sizeof(double) * nreq);
+  Prof pr(stream, "small_batch", 0.0);
+  cuda_check(launch_small_batch<R>(dp, dfirst, dnq, nreq, max_n, dout, stream), "small batch launch");
+  pr.done();
+  if (!out_on_device) {
+    cuda_check(cudaMemcpyAsync(out, dout, sizeof(double) * nreq, cudaMemcpyDeviceToHost, stream), "result copy");
+    cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  }
+}
+}  // namespace
+}  // namespace sv
+
+extern "C" {
+
+sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits, const sv_gate* const* gates,
+                             const size_t* n_gates, double* out_sum_z, int out_on_device, void* stream) {
+  return guarded([&] {
+    if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+    if (n_requests < 1 || n_requests > 65535) fail(SV_ERR_INVALID, "n_requests must be in 1..65535");
+    if (!n_qubits || !gates || !n_gates || !out_sum_z) fail(SV_ERR_INVALID, "NULL argument");
+    for (int b = 0; b < n_requests; b++)
+      if (n_qubits[b] < 1 || n_qubits[b] > SV_SMALL_MAX_QUBITS)
+        fail(SV_ERR_INVALID, "request " + std::to_string(b) + ": n_qubits must be in 1..12 for the packed launch");
+    if (out_on_device) check_device_buffer(out_sum_z, sizeof(double) * n_requests, "out_sum_z");
+    if (dtype == SV_C64)
+      run_batch_small<float>(n_requests, dtype, n_qubits, gates, n_gates, out_sum_z, out_on_device,
+                             (cudaStream_t)stream);
+    else
+      run_batch_small<double>(n_requests, dtype, n_qubits, gates, n_gates, out_sum_z, out_on_device,
+                              (cudaStream_t)stream);
+  });
+}
+
 sv_status sv_release_scratch(void) {
   return guarded([&] {
     std::lock_guard<std::mutex> lk(g_ws_mu);
@@ -546,6 +791,11 @@ sv_status sv_release_scratch(void) {
     g_ws.clear();
     for (auto& kv : g_named) cudaFree(kv.second.first);
     g_named.clear();
+    for (auto& kv : g_pinned) {
+      if (kv.second.p) cudaFreeHost(kv.second.p);
+      if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+    }
+    g_pinned.clear();
   });
 }
 

@@ -31,26 +31,51 @@ enum OpKind : uint8_t {
   OPK_DIAG = 2,     // diagonal 2^k entries; the k bits may be local or external
   OPK_ANTIDIAG = 3, // one qubit: out0 = a * v1, out1 = b * v0 (X, Y, CNOT ...)
   OPK_SWAP = 4,     // two local positions: exchange |01> and |10>
+  OPK_SIGN = 5,     // negate the amplitudes whose bits match (CZ, Z, CCZ ...): no coefficients
 };
 
 constexpr int kMaxTileQ = 14;  // 2^14 amplitudes: 128 KiB (c64) of shared memory
 constexpr int kMaxOps = 96;
+constexpr int kMaxPhases = 96;
+constexpr int kRegQ = 4;        // register qubits of a phase: 16 amplitudes per thread
 constexpr int kProgramBytes = 32000;  // kernel parameter space is 32764 bytes
 
+// An op as the kernel sees it.  Positions are local tile bits (indices into
+// tq).  In a register phase, rs[] gives the register slot of each matrix bit
+// (0xFF: not in registers), and the controls are split into the register part
+// (rmask/rval over slots), the thread part (tmask/tval over local bits held by
+// the thread index) and the part outside the tile (xmask/xval, global bits).
 struct DevOp {
   uint8_t kind;
   uint8_t k;            // matrix qubits
   uint8_t pos[5];       // local positions, matrix order (pos[0] = least significant matrix bit);
-                        // OPK_DIAG: 0xFF marks an external qubit (see gq)
+                        // OPK_DIAG/OPK_SIGN: 0xFF marks an external qubit (see gq)
   uint8_t spos[5];      // the local positions sorted ascending (group enumeration)
-  uint8_t gq[5];        // OPK_DIAG: global qubit of each matrix bit
-  uint8_t pad;
-  uint32_t lmask, lval; // controls inside the tile (local bit mask / required values)
+  uint8_t gq[5];        // global qubit of each matrix bit
+  uint8_t rs[5];        // register slot of each matrix bit in its phase, 0xFF if none
+  uint8_t rmask, rval;  // control bits on register slots
+  uint32_t lmask, lval; // all local controls (shared-memory path)
+  uint32_t tmask, tval; // local controls held by the thread index (register path)
   uint64_t xmask, xval; // controls outside the tile (global bit mask / required values)
   uint32_t coef;        // first coefficient in the program's pool
-  uint32_t pad2;
+  uint32_t pad;
 };
-static_assert(sizeof(DevOp) == 56, "DevOp layout");
+static_assert(sizeof(DevOp) == 64, "DevOp layout");
+
+enum PhaseKind : uint8_t { PH_REG = 0, PH_SMEM = 1 };
+
+// A run of ops applied with the same amplitude-to-thread mapping.  PH_REG:
+// thread t holds the 16 amplitudes whose local bits at rp[] vary and whose
+// other local bits are t deposited into tpos[] (ascending); PH_SMEM: one op
+// applied group by group straight in shared memory (dense k >= 3 and wide
+// diagonals).
+struct Phase {
+  uint8_t kind, first, nops, ntpos;
+  uint8_t rp[kRegQ];
+  uint8_t tpos[kMaxTileQ];
+  uint8_t pad[2];
+};
+static_assert(sizeof(Phase) == 24, "Phase layout");
 
 template <typename R>
 struct Cx {
@@ -59,16 +84,18 @@ struct Cx {
 
 struct ProgramHeader {
   int32_t n, m, L, nops;
-  int32_t ncoef, pad0;
+  int32_t ncoef, nphases;
   int8_t tq[16];
 };
 
 template <typename R>
 struct SweepProgram {
-  static constexpr int kPool =
-      (kProgramBytes - (int)sizeof(ProgramHeader) - kMaxOps * (int)sizeof(DevOp)) / (int)sizeof(Cx<R>);
+  static constexpr int kPool = (kProgramBytes - (int)sizeof(ProgramHeader) - kMaxOps * (int)sizeof(DevOp) -
+                                kMaxPhases * (int)sizeof(Phase)) /
+                               (int)sizeof(Cx<R>);
   ProgramHeader h;
   DevOp ops[kMaxOps];
+  Phase ph[kMaxPhases];
   Cx<R> coef[kPool];
 };
 
@@ -196,7 +223,7 @@ void classify(LOp& op);
 std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_q, int low_q, int coef_pool,
                                    int ops_per_pass);
 Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
-               size_t n_param_values, const sv_exec_opts& opts);
+               size_t n_param_values, const sv_exec_opts& opts, int tile_q_override = 0);
 double op_cost(const LOp& op);
 int tile_qubits_for(sv_dtype dtype);
 int low_qubits_for(sv_dtype dtype);
@@ -208,6 +235,11 @@ template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream);
 template <typename R>
 cudaError_t launch_init_basis(Cx<R>* state, int n, uint64_t index, cudaStream_t stream);
+// One CTA per small request (whole state in shared memory): request b runs
+// programs first_prog[b] .. first_prog[b+1]-1 and writes sum_q <Z_q> to out[b].
+template <typename R>
+cudaError_t launch_small_batch(const SweepProgram<R>* progs, const int* first_prog, const int* nq, int n_requests,
+                               int max_n, double* out, cudaStream_t stream);
 
 // Reductions write fixed-order per-block partials into `scratch` and a final
 // kernel folds them into `out` (device doubles).

@@ -256,17 +256,28 @@ static void apply_local(std::vector<cplx>& v, int nb, const sv_gate& g, const st
   }
 }
 
-// Arithmetic per amplitude of one operation in a pass (multiply-adds of the
-// complex matrix-vector product, counted as real flops), plus one
-// shared-memory round trip of the tile per operation.
+// Cost per amplitude of one operation inside a pass, in the kernel's terms:
+// the multiply-adds of its complex matrix-vector product as real flops, plus
+// the overhead of the path it takes.  One- and two-qubit ops run on register
+// groups (a few integer ops of overhead); wider dense blocks and diagonals run
+// group by group in shared memory (an address computation and a shared-memory
+// round trip per amplitude).  A sign flip (Z, CZ) and a bit flip (X, CNOT)
+// cost almost nothing.
 double op_cost(const LOp& op) {
-  const double pass = 8.0;
+  const bool wide = op.k >= 3;
   switch (op.kind) {
-    case OPK_DENSE: return 8.0 * (1 << op.k) + pass;
-    case OPK_REAL: return 4.0 * (1 << op.k) + pass;
-    case OPK_DIAG: return 6.0 + pass;
-    case OPK_ANTIDIAG: return 6.0 + pass;
-    default: return 1.0 + pass;
+    case OPK_DENSE: return 8.0 * (1 << op.k) + (wide ? 40.0 : 2.0);
+    case OPK_REAL: return 4.0 * (1 << op.k) + (wide ? 40.0 : 2.0);
+    case OPK_DIAG: {
+      const int d = 1 << op.k;
+      bool sign = true;
+      for (int r = 0; r < d && r < (int)op.m.size(); r++)
+        if (op.m[r] != (r == d - 1 ? cplx(-1.0) : cplx(1.0))) sign = false;
+      if (sign) return 1.0;
+      return wide ? 60.0 : 10.0;
+    }
+    case OPK_ANTIDIAG: return (op.m.size() == 2 && op.m[0] == cplx(1.0) && op.m[1] == cplx(1.0)) ? 1.0 : 6.0;
+    default: return 1.0;
   }
 }
 
@@ -393,7 +404,7 @@ std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_
 }
 
 Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
-               size_t n_param_values, const sv_exec_opts& opts) {
+               size_t n_param_values, const sv_exec_opts& opts, int tile_q_override) {
   const int fuse_max_k = opts.fuse_max_k;
   if (opts.block_mode != SV_BLOCK_AUTO && opts.block_mode != SV_BLOCK_DENSE) fail(SV_ERR_INVALID, "unknown block_mode");
   if (opts.ops_per_pass < 0) fail(SV_ERR_INVALID, "ops_per_pass must be >= 0");
@@ -430,7 +441,8 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
   }
   p.ops = std::move(kept);
   int pool = dtype == SV_C64 ? SweepProgram<float>::kPool : SweepProgram<double>::kPool;
-  p.sweeps = schedule_sweeps(n, p.ops, tile_qubits_for(dtype), low_qubits_for(dtype), pool, opts.ops_per_pass);
+  const int tile_q = tile_q_override > 0 ? tile_q_override : tile_qubits_for(dtype);
+  p.sweeps = schedule_sweeps(n, p.ops, tile_q, low_qubits_for(dtype), pool, opts.ops_per_pass);
   return p;
 }
 

@@ -1,20 +1,25 @@
 // sv_sweep.cu -- gate application kernels for sm_103a.
 //
-// One launch makes one pass over the state (the "sweep").  The state is cut
+// One launch makes one pass over the state (a "sweep").  The state is cut
 // into tiles of 2^m amplitudes; a tile is the set of amplitudes whose bits
 // outside the tile qubits tq[] are fixed, i.e. the paper's group of amplitudes
 // "that differ only on the target qubits" (Sec. 5.3), widened from the k
 // targets of one gate to the m qubits of every operation the pass applies.
 // Group members are found by bit insertion instead of the paper's index table
 // I_T (no 2^n integer array is stored).  The low L tile qubits are 0..L-1, so a
-// tile is 2^(m-L) contiguous runs of 2^L amplitudes (256 bytes): each run is
-// read and written with coalesced 16-byte accesses.
+// tile is 2^(m-L) contiguous runs of 2^L amplitudes (256 bytes), read and
+// written with coalesced 16-byte accesses.
 //
-// Inside the tile every operation of the program is applied in shared memory:
-// dense k <= 5 matrices (single gates or the paper's fused blocks), real
-// matrices with half the multiplies (Sec. 5.3: a real gate needs 2 real
-// products, a complex one 4), diagonal gates (no amplitude moves), and the
-// permutation gates X/CNOT/SWAP (Sec. 9.2: diagonal and permutation paths).
+// Inside the tile the ops run in phases.  In a register phase each thread
+// holds 16 amplitudes that differ only on four "register" tile qubits and
+// applies every consecutive op whose moving qubits are among them with plain
+// FMAs on registers: dense and real one-/two-qubit matrices (Sec. 5.3: a real
+// gate needs half the products), diagonal gates and sign flips (CZ, Z) which
+// move nothing, and X/CNOT/SWAP which only permute registers (Sec. 9.2:
+// diagonal and permutation paths).  Shared memory is read and written once per
+// phase, with an XOR swizzle of 16-byte granules so the strided register
+// groups do not collide in banks.  Dense k >= 3 operations (the paper's fused
+// blocks) run group by group straight in shared memory.
 #include <cuda_runtime.h>
 
 #include "sv_internal.h"
@@ -45,6 +50,17 @@ __device__ __forceinline__ uint64_t ins0_64(uint64_t x, int p) {
   return ((x >> p) << (p + 1)) | lo;
 }
 
+// Shared-memory slot of local amplitude l: the 16-byte granule index has its
+// low three bits XORed with the next three (bit 0 of a complex64 index, the
+// amplitude inside its granule, is left alone).
+template <typename R>
+__device__ __forceinline__ uint32_t phys(uint32_t l) {
+  if constexpr (sizeof(Cx<R>) == 8)
+    return l ^ ((l >> 3) & 14u);
+  else
+    return l ^ ((l >> 3) & 7u);
+}
+
 // Offset of local amplitude l (m bits) from the tile base in the global state.
 __device__ __forceinline__ uint64_t local_offset(uint32_t l, const ProgramHeader& h) {
   uint64_t off = l & ((1u << h.L) - 1u);
@@ -56,60 +72,235 @@ __device__ __forceinline__ uint64_t local_offset(uint32_t l, const ProgramHeader
   return off;
 }
 
-// ---------------------------------------------------------------- ops
+// ---------------------------------------------------------------- register ops
 
-template <typename R>
-__device__ __forceinline__ void op_dense1(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, bool real) {
-  const int p = op.pos[0];
+constexpr int NR = 1 << kRegQ;  // amplitudes per thread in a register phase
+
+template <typename R, int S>
+__device__ __forceinline__ void r_dense1(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_t rmask, uint32_t rval, bool real) {
   const Cx<R> u00 = cf[0], u01 = cf[1], u10 = cf[2], u11 = cf[3];
-  for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 1); g += blockDim.x) {
-    uint32_t i0 = ins0(g, p);
-    if ((i0 & op.lmask) != op.lval) continue;
-    uint32_t i1 = i0 | (1u << p);
-    Cx<R> a = s[i0], b = s[i1];
-    Cx<R> o0, o1;
-    if (real) {
-      o0 = {fma(u00.re, a.re, u01.re * b.re), fma(u00.re, a.im, u01.re * b.im)};
-      o1 = {fma(u10.re, a.re, u11.re * b.re), fma(u10.re, a.im, u11.re * b.im)};
-    } else {
-      o0 = cfma(u01, b, cmul(u00, a));
-      o1 = cfma(u11, b, cmul(u10, a));
+  if (rmask == 0 && !real) {  // the common case: no control among the register slots
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+      if (j & (1 << S)) continue;
+      const int j1 = j | (1 << S);
+      const Cx<R> a = v[j], b = v[j1];
+      v[j] = cfma(u01, b, cmul(u00, a));
+      v[j1] = cfma(u11, b, cmul(u10, a));
     }
-    s[i0] = o0;
-    s[i1] = o1;
+    return;
+  }
+  if (real) {
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+      if (j & (1 << S)) continue;
+      if ((j & rmask) != rval) continue;
+      const int j1 = j | (1 << S);
+      const Cx<R> a = v[j], b = v[j1];
+      v[j] = {fma(u00.re, a.re, u01.re * b.re), fma(u00.re, a.im, u01.re * b.im)};
+      v[j1] = {fma(u10.re, a.re, u11.re * b.re), fma(u10.re, a.im, u11.re * b.im)};
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+      if (j & (1 << S)) continue;
+      if ((j & rmask) != rval) continue;
+      const int j1 = j | (1 << S);
+      const Cx<R> a = v[j], b = v[j1];
+      v[j] = cfma(u01, b, cmul(u00, a));
+      v[j1] = cfma(u11, b, cmul(u10, a));
+    }
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void op_antidiag(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf) {
-  const int p = op.pos[0];
+template <typename R, int S>
+__device__ __forceinline__ void r_anti1(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_t rmask, uint32_t rval, bool flip) {
   const Cx<R> a01 = cf[0], a10 = cf[1];
-  for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 1); g += blockDim.x) {
-    uint32_t i0 = ins0(g, p);
-    if ((i0 & op.lmask) != op.lval) continue;
-    uint32_t i1 = i0 | (1u << p);
-    Cx<R> a = s[i0], b = s[i1];
-    s[i0] = cmul(a01, b);
-    s[i1] = cmul(a10, a);
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    if ((j & rmask) != rval) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> a = v[j], b = v[j1];
+    if (flip) {
+      v[j] = b;
+      v[j1] = a;
+    } else {
+      v[j] = cmul(a01, b);
+      v[j1] = cmul(a10, a);
+    }
+  }
+}
+
+template <typename R, int A, int B>
+__device__ __forceinline__ void r_dense2(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_t rmask, uint32_t rval) {
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & ((1 << A) | (1 << B))) continue;
+    if ((j & rmask) != rval) continue;
+    const int i0 = j, i1 = j | (1 << A), i2 = j | (1 << B), i3 = j | (1 << A) | (1 << B);
+    const Cx<R> x0 = v[i0], x1 = v[i1], x2 = v[i2], x3 = v[i3];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      Cx<R> acc = cmul(cf[r * 4 + 0], x0);
+      acc = cfma(cf[r * 4 + 1], x1, acc);
+      acc = cfma(cf[r * 4 + 2], x2, acc);
+      acc = cfma(cf[r * 4 + 3], x3, acc);
+      v[r == 0 ? i0 : r == 1 ? i1 : r == 2 ? i2 : i3] = acc;
+    }
+  }
+}
+
+template <typename R, int A, int B>
+__device__ __forceinline__ void r_swap(Cx<R> (&v)[NR], uint32_t rmask, uint32_t rval) {
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & ((1 << A) | (1 << B))) continue;
+    if ((j & rmask) != rval) continue;
+    const Cx<R> t = v[j | (1 << A)];
+    v[j | (1 << A)] = v[j | (1 << B)];
+    v[j | (1 << B)] = t;
   }
 }
 
 template <typename R>
-__device__ __forceinline__ void op_swap(Cx<R>* s, int tsz, const DevOp& op) {
-  const int p0 = op.pos[0], p1 = op.pos[1];
-  const int q0 = op.spos[0], q1 = op.spos[1];
-  for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 2); g += blockDim.x) {
-    uint32_t b = ins0(ins0(g, q0), q1);
-    if ((b & op.lmask) != op.lval) continue;
-    uint32_t i01 = b | (1u << p0), i10 = b | (1u << p1);
-    Cx<R> t = s[i01];
-    s[i01] = s[i10];
-    s[i10] = t;
+__device__ __forceinline__ void r_sign(Cx<R> (&v)[NR], uint32_t rmask, uint32_t rval) {
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if ((j & rmask) != rval) continue;
+    v[j].re = -v[j].re;
+    v[j].im = -v[j].im;
   }
 }
+
+// Diagonal op with k <= 2 matrix bits, each held by a register slot, by the
+// thread index, or fixed for the tile.
+template <typename R>
+__device__ __forceinline__ void r_diag(Cx<R> (&v)[NR], const DevOp& op, const Cx<R>* cf, uint32_t tb, uint64_t base) {
+  uint32_t dbase = 0;
+  int s0 = -1, s1 = -1, b0 = 0, b1 = 0;
+  for (int i = 0; i < op.k; i++) {
+    if (op.rs[i] != 0xFF) {
+      if (s0 < 0) {
+        s0 = op.rs[i];
+        b0 = i;
+      } else {
+        s1 = op.rs[i];
+        b1 = i;
+      }
+    } else if (op.pos[i] != 0xFF) {
+      dbase |= ((tb >> op.pos[i]) & 1u) << i;
+    } else {
+      dbase |= (uint32_t)((base >> op.gq[i]) & 1ull) << i;
+    }
+  }
+  const Cx<R> f0 = cf[dbase];
+  const Cx<R> f1 = s0 >= 0 ? cf[dbase | (1u << b0)] : f0;
+  const Cx<R> f2 = s1 >= 0 ? cf[dbase | (1u << b1)] : f0;
+  const Cx<R> f3 = s1 >= 0 ? cf[dbase | (1u << b0) | (1u << b1)] : f1;
+  const int sh0 = s0 >= 0 ? s0 : 0, sh1 = s1 >= 0 ? s1 : 0;
+  const uint32_t m0 = s0 >= 0 ? 1u : 0u, m1 = s1 >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if ((j & op.rmask) != op.rval) continue;
+    const uint32_t c0 = ((uint32_t)j >> sh0) & m0, c1 = ((uint32_t)j >> sh1) & m1;
+    const Cx<R> f = c1 ? (c0 ? f3 : f2) : (c0 ? f1 : f0);
+    v[j] = cmul(f, v[j]);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_reg(Cx<R> (&v)[NR], const DevOp& op, const Cx<R>* pool, uint32_t tb,
+                                          uint64_t base) {
+  if ((base & op.xmask) != op.xval) return;  // same for the whole block
+  if ((tb & op.tmask) != op.tval) return;    // same for the thread's 16 amplitudes
+  const Cx<R>* cf = pool + op.coef;
+  const uint32_t rm = op.rmask, rv = op.rval;
+  switch (op.kind) {
+    case OPK_DENSE:
+    case OPK_REAL:
+      if (op.k == 1) {
+        const bool real = op.kind == OPK_REAL;
+        switch (op.rs[0]) {
+          case 0: r_dense1<R, 0>(v, cf, rm, rv, real); break;
+          case 1: r_dense1<R, 1>(v, cf, rm, rv, real); break;
+          case 2: r_dense1<R, 2>(v, cf, rm, rv, real); break;
+          default: r_dense1<R, 3>(v, cf, rm, rv, real); break;
+        }
+      } else {
+        switch (op.rs[0] * 4 + op.rs[1]) {  // the host orders rs[0] < rs[1]
+          case 1: r_dense2<R, 0, 1>(v, cf, rm, rv); break;
+          case 2: r_dense2<R, 0, 2>(v, cf, rm, rv); break;
+          case 3: r_dense2<R, 0, 3>(v, cf, rm, rv); break;
+          case 6: r_dense2<R, 1, 2>(v, cf, rm, rv); break;
+          case 7: r_dense2<R, 1, 3>(v, cf, rm, rv); break;
+          default: r_dense2<R, 2, 3>(v, cf, rm, rv); break;
+        }
+      }
+      break;
+    case OPK_ANTIDIAG: {
+      const bool flip = op.pad != 0;  // pure bit flip (X, CNOT): no multiplies
+      switch (op.rs[0]) {
+        case 0: r_anti1<R, 0>(v, cf, rm, rv, flip); break;
+        case 1: r_anti1<R, 1>(v, cf, rm, rv, flip); break;
+        case 2: r_anti1<R, 2>(v, cf, rm, rv, flip); break;
+        default: r_anti1<R, 3>(v, cf, rm, rv, flip); break;
+      }
+      break;
+    }
+    case OPK_SWAP:
+      switch (op.rs[0] * 4 + op.rs[1]) {
+        case 1: r_swap<R, 0, 1>(v, rm, rv); break;
+        case 2: r_swap<R, 0, 2>(v, rm, rv); break;
+        case 3: r_swap<R, 0, 3>(v, rm, rv); break;
+        case 6: r_swap<R, 1, 2>(v, rm, rv); break;
+        case 7: r_swap<R, 1, 3>(v, rm, rv); break;
+        default: r_swap<R, 2, 3>(v, rm, rv); break;
+      }
+      break;
+    case OPK_DIAG: r_diag<R>(v, op, cf, tb, base); break;
+    case OPK_SIGN: r_sign<R>(v, rm, rv); break;
+    default: break;
+  }
+}
+
+// The local bits of register slot combination j (masks m[] = 1 << rp[]).
+__device__ __forceinline__ uint32_t reg_bits(int j, const uint32_t (&m)[kRegQ]) {
+  return ((j & 1) ? m[0] : 0u) | ((j & 2) ? m[1] : 0u) | ((j & 4) ? m[2] : 0u) | ((j & 8) ? m[3] : 0u);
+}
+
+template <typename R>
+__device__ __forceinline__ void reg_load(Cx<R> (&v)[NR], const Cx<R>* s, uint32_t tb, const uint32_t (&m)[kRegQ]) {
+  if (sizeof(Cx<R>) == 8 && m[0] == 1u) {  // pairs (j, j+1) share a 16-byte granule
+#pragma unroll
+    for (int j = 0; j < NR; j += 2) {
+      const float4 w = *reinterpret_cast<const float4*>(s + phys<R>(tb | reg_bits(j, m)));
+      v[j] = Cx<R>{(R)w.x, (R)w.y};
+      v[j + 1] = Cx<R>{(R)w.z, (R)w.w};
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; j++) v[j] = s[phys<R>(tb | reg_bits(j, m))];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void reg_store(const Cx<R> (&v)[NR], Cx<R>* s, uint32_t tb, const uint32_t (&m)[kRegQ]) {
+  if (sizeof(Cx<R>) == 8 && m[0] == 1u) {
+#pragma unroll
+    for (int j = 0; j < NR; j += 2)
+      *reinterpret_cast<float4*>(s + phys<R>(tb | reg_bits(j, m))) =
+          make_float4((float)v[j].re, (float)v[j].im, (float)v[j + 1].re, (float)v[j + 1].im);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; j++) s[phys<R>(tb | reg_bits(j, m))] = v[j];
+  }
+}
+
+// ---------------------------------------------------------------- shared-memory ops
 
 template <typename R, int K>
-__device__ __forceinline__ void op_denseK(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, bool real) {
+__device__ __forceinline__ void s_denseK(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf) {
   constexpr int D = 1 << K;
   uint32_t bit[K];
 #pragma unroll
@@ -126,52 +317,116 @@ __device__ __forceinline__ void op_denseK(Cx<R>* s, int tsz, const DevOp& op, co
 #pragma unroll
       for (int i = 0; i < K; i++)
         if ((j >> i) & 1) x |= bit[i];
-      v[j] = s[x];
+      v[j] = s[phys<R>(x)];
     }
 #pragma unroll 1
     for (int r = 0; r < D; r++) {
       Cx<R> acc = {R(0), R(0)};
       const Cx<R>* row = cf + r * D;
-      if (real) {
 #pragma unroll
-        for (int c = 0; c < D; c++) {
-          acc.re = fma(row[c].re, v[c].re, acc.re);
-          acc.im = fma(row[c].re, v[c].im, acc.im);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < D; c++) acc = cfma(row[c], v[c], acc);
-      }
+      for (int c = 0; c < D; c++) acc = cfma(row[c], v[c], acc);
       uint32_t x = b;
 #pragma unroll
       for (int i = 0; i < K; i++)
         if ((r >> i) & 1) x |= bit[i];
-      s[x] = acc;
+      s[phys<R>(x)] = acc;
     }
   }
 }
 
 template <typename R>
-__device__ __forceinline__ void op_diag(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, uint64_t base) {
-  // external matrix bits are fixed for the whole tile
+__device__ __forceinline__ void s_diag(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, uint64_t base) {
   uint32_t xi = 0;
   for (int i = 0; i < op.k; i++)
     if (op.pos[i] == 0xFF) xi |= (uint32_t)((base >> op.gq[i]) & 1ull) << i;
   for (uint32_t a = threadIdx.x; a < (uint32_t)tsz; a += blockDim.x) {
     if ((a & op.lmask) != op.lval) continue;
-    uint32_t di = xi;
-    for (int i = 0; i < op.k; i++)
-      if (op.pos[i] != 0xFF) di |= ((a >> op.pos[i]) & 1u) << i;
-    s[a] = cmul(cf[di], s[a]);
+    const uint32_t pa = phys<R>(a);
+    if (op.kind == OPK_SIGN) {
+      s[pa] = Cx<R>{-s[pa].re, -s[pa].im};
+    } else {
+      uint32_t di = xi;
+      for (int i = 0; i < op.k; i++)
+        if (op.pos[i] != 0xFF) di |= ((a >> op.pos[i]) & 1u) << i;
+      s[pa] = cmul(cf[di], s[pa]);
+    }
+  }
+}
+
+// Anti-diagonal and swap ops of a shared-memory phase (tiles too small for
+// register groups).
+template <typename R>
+__device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf) {
+  if (op.kind == OPK_ANTIDIAG) {
+    const int p = op.pos[0];
+    for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 1); g += blockDim.x) {
+      const uint32_t i0 = ins0(g, p);
+      if ((i0 & op.lmask) != op.lval) continue;
+      const uint32_t a = phys<R>(i0), b = phys<R>(i0 | (1u << p));
+      const Cx<R> x = s[a], y = s[b];
+      s[a] = cmul(cf[0], y);
+      s[b] = cmul(cf[1], x);
+    }
+  } else {
+    for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 2); g += blockDim.x) {
+      const uint32_t b = ins0(ins0(g, op.spos[0]), op.spos[1]);
+      if ((b & op.lmask) != op.lval) continue;
+      const uint32_t i01 = phys<R>(b | (1u << op.pos[0])), i10 = phys<R>(b | (1u << op.pos[1]));
+      const Cx<R> t = s[i01];
+      s[i01] = s[i10];
+      s[i10] = t;
+    }
   }
 }
 
 // ---------------------------------------------------------------- kernels
 
-// KMAX: widest dense operation the program holds (the host picks the variant,
-// so programs of one- and two-qubit gates do not pay the registers of k = 5).
+// Runs every phase of a program on a tile that is already in shared memory.
+// KMAX: widest dense operation the program runs in shared memory.
 template <typename R, int KMAX>
-__global__ void __launch_bounds__(256) k_sweep(Cx<R>* __restrict__ state, const __grid_constant__ SweepProgram<R> P) {
+__device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, int tsz, uint64_t base) {
+  const ProgramHeader& h = P.h;
+  for (int p = 0; p < h.nphases; p++) {
+    const Phase& ph = P.ph[p];
+    if (ph.kind == PH_REG) {
+      if (threadIdx.x < (1u << ph.ntpos)) {
+        uint32_t tb = 0;
+        for (int i = 0; i < ph.ntpos; i++)
+          if ((threadIdx.x >> i) & 1u) tb |= 1u << ph.tpos[i];
+        const uint32_t m[kRegQ] = {1u << ph.rp[0], 1u << ph.rp[1], 1u << ph.rp[2], 1u << ph.rp[3]};
+        Cx<R> v[NR];
+        reg_load<R>(v, s, tb, m);
+        for (int o = ph.first; o < ph.first + ph.nops; o++) apply_reg<R>(v, P.ops[o], P.coef, tb, base);
+        reg_store<R>(v, s, tb, m);
+      }
+    } else {
+      const DevOp& op = P.ops[ph.first];
+      if ((base & op.xmask) == op.xval) {
+        const Cx<R>* cf = P.coef + op.coef;
+        switch (op.kind) {
+          case OPK_DIAG:
+          case OPK_SIGN: s_diag<R>(s, tsz, op, cf, base); break;
+          case OPK_ANTIDIAG:
+          case OPK_SWAP: s_perm<R>(s, tsz, op, cf); break;
+          default:
+            switch (op.k) {
+              case 1: s_denseK<R, 1>(s, tsz, op, cf); break;
+              case 2: s_denseK<R, 2>(s, tsz, op, cf); break;
+              case 3: if constexpr (KMAX >= 3) s_denseK<R, 3>(s, tsz, op, cf); break;
+              case 4: if constexpr (KMAX >= 4) s_denseK<R, 4>(s, tsz, op, cf); break;
+              default: if constexpr (KMAX >= 5) s_denseK<R, 5>(s, tsz, op, cf); break;
+            }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One pass over the state: gather each tile, run the program, scatter back.
+template <typename R, int KMAX>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
+    k_sweep(Cx<R>* __restrict__ state, const __grid_constant__ SweepProgram<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
   const ProgramHeader& h = P.h;
@@ -179,44 +434,62 @@ __global__ void __launch_bounds__(256) k_sweep(Cx<R>* __restrict__ state, const 
   constexpr int A = 16 / sizeof(Cx<R>);  // amplitudes per 16-byte access
   const int nvec = tsz / A;
   const uint64_t ntiles = 1ull << (h.n - h.m);
-  uint4* s4 = reinterpret_cast<uint4*>(s);
+  // global offset of every run of 2^L contiguous amplitudes of a tile (the
+  // same for all tiles), kept after the tile in shared memory
+  uint64_t* hi_off = reinterpret_cast<uint64_t*>(s + tsz);
+  const int nhi = 1 << (h.m - h.L);
+  for (int c = threadIdx.x; c < nhi; c += blockDim.x) hi_off[c] = local_offset((uint32_t)c << h.L, h);
+  const uint32_t lowmask = (1u << h.L) - 1u;
+  __syncthreads();
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     uint64_t base = tile;
     for (int i = 0; i < h.m; i++) base = ins0_64(base, h.tq[i]);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-      uint64_t off = local_offset((uint32_t)(v * A), h);
-      s4[v] = *reinterpret_cast<const uint4*>(state + (base + off));
+      const uint32_t l = (uint32_t)(v * A);
+      *reinterpret_cast<uint4*>(s + phys<R>(l)) =
+          *reinterpret_cast<const uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask))));
     }
     __syncthreads();
-    for (int o = 0; o < h.nops; o++) {
-      const DevOp& op = P.ops[o];
-      if ((base & op.xmask) != op.xval) continue;  // same for the whole block
-      const Cx<R>* cf = P.coef + op.coef;
-      switch (op.kind) {
-        case OPK_DENSE:
-        case OPK_REAL: {
-          bool real = op.kind == OPK_REAL;
-          switch (op.k) {
-            case 1: op_dense1<R>(s, tsz, op, cf, real); break;
-            case 2: op_denseK<R, 2>(s, tsz, op, cf, real); break;
-            case 3: if constexpr (KMAX >= 3) op_denseK<R, 3>(s, tsz, op, cf, false); break;
-            case 4: if constexpr (KMAX >= 4) op_denseK<R, 4>(s, tsz, op, cf, false); break;
-            default: if constexpr (KMAX >= 5) op_denseK<R, 5>(s, tsz, op, cf, false); break;
-          }
-          break;
-        }
-        case OPK_DIAG: op_diag<R>(s, tsz, op, cf, base); break;
-        case OPK_ANTIDIAG: op_antidiag<R>(s, tsz, op, cf); break;
-        case OPK_SWAP: op_swap<R>(s, tsz, op); break;
-        default: break;
-      }
-      __syncthreads();
-    }
+    run_phases<R, KMAX>(P, s, tsz, base);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-      uint64_t off = local_offset((uint32_t)(v * A), h);
-      *reinterpret_cast<uint4*>(state + (base + off)) = s4[v];
+      const uint32_t l = (uint32_t)(v * A);
+      *reinterpret_cast<uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask)))) =
+          *reinterpret_cast<const uint4*>(s + phys<R>(l));
     }
     __syncthreads();
+  }
+}
+
+// Packed small states (serving): CTA b simulates request b entirely in shared
+// memory -- |0..0>, every program of the request, then sum_q <Z_q> =
+// sum_a |psi_a|^2 (n - 2 popcount(a)) -- and writes one double.  The state
+// never touches HBM.
+template <typename R>
+__global__ void __launch_bounds__(256) k_small_batch(const SweepProgram<R>* __restrict__ progs,
+                                                     const int* __restrict__ first_prog, const int* __restrict__ nq,
+                                                     double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
+  __shared__ double red[8];
+  const int b = blockIdx.x;
+  const int n = nq[b];
+  const int tsz = 1 << n;
+  for (int a = threadIdx.x; a < tsz; a += blockDim.x) s[phys<R>(a)] = Cx<R>{R(a == 0 ? 1 : 0), R(0)};
+  __syncthreads();
+  for (int p = first_prog[b]; p < first_prog[b + 1]; p++) run_phases<R, 2>(progs[p], s, tsz, 0ull);
+  double acc = 0.0;
+  for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
+    const Cx<R> x = s[phys<R>(a)];
+    acc += (double)(x.re * x.re + x.im * x.im) * (double)(n - 2 * __popc(a));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    out[b] = t;
   }
 }
 
@@ -237,9 +510,15 @@ int device_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+int sweep_threads(int m) {
+  // one thread per register group of 16 amplitudes; at least one warp
+  int t = m > kRegQ + 5 ? (1 << (m - kRegQ)) : 32;
+  return t > 256 ? 256 : t;
+}
+
 template <typename R, int KMAX>
 static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
-  const int smem = (int)sizeof(Cx<R>) << prog.h.m;
+  const int smem = ((int)sizeof(Cx<R>) << prog.h.m) + (8 << (prog.h.m - prog.h.L));
   // raise the dynamic shared-memory limit to what this launch needs (per device)
   static int configured_bytes[64] = {0};
   int dev = 0;
@@ -250,21 +529,24 @@ static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cud
     if (e != cudaSuccess) return e;
     configured_bytes[dev] = smem;
   }
+  const int threads = sweep_threads(prog.h.m);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX>, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX>, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
   uint64_t grid = (uint64_t)device_sm_count() * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_sweep<R, KMAX><<<(unsigned)grid, 256, smem, stream>>>(state, prog);
+  k_sweep<R, KMAX><<<(unsigned)grid, threads, smem, stream>>>(state, prog);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
   int kmax = 1;
-  for (int o = 0; o < prog.h.nops; o++) {
-    const DevOp& op = prog.ops[o];
+  for (int p = 0; p < prog.h.nphases; p++) {
+    const Phase& ph = prog.ph[p];
+    if (ph.kind != PH_SMEM) continue;
+    const DevOp& op = prog.ops[ph.first];
     if ((op.kind == OPK_DENSE || op.kind == OPK_REAL) && op.k > kmax) kmax = op.k;
   }
   if (kmax <= 2) return launch_sweep_k<R, 2>(state, prog, stream);
@@ -282,6 +564,27 @@ cudaError_t launch_init_basis(Cx<R>* state, int n, uint64_t index, cudaStream_t 
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_small_batch(const SweepProgram<R>* progs, const int* first_prog, const int* nq, int n_requests,
+                               int max_n, double* out, cudaStream_t stream) {
+  const int smem = (int)sizeof(Cx<R>) << max_n;
+  static int configured_bytes[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (smem > 48 * 1024 && smem > configured_bytes[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_small_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes[dev] = smem;
+  }
+  k_small_batch<R><<<n_requests, 256, smem, stream>>>(progs, first_prog, nq, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_small_batch<float>(const SweepProgram<float>*, const int*, const int*, int, int, double*,
+                                               cudaStream_t);
+template cudaError_t launch_small_batch<double>(const SweepProgram<double>*, const int*, const int*, int, int, double*,
+                                                cudaStream_t);
 template cudaError_t launch_sweep<float>(Cx<float>*, const SweepProgram<float>&, cudaStream_t);
 template cudaError_t launch_sweep<double>(Cx<double>*, const SweepProgram<double>&, cudaStream_t);
 template cudaError_t launch_init_basis<float>(Cx<float>*, int, uint64_t, cudaStream_t);

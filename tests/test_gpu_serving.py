@@ -1,0 +1,63 @@
+"""GPU tests of the serving rows: the packed small-state launch against the
+oracle, and the serving loop's results alone vs in the mix (complex64:
+1e-4 on sum_q <Z_q>)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_09733_gb300 import binding as B
+from workloads import random_circuit, serving_circuit, serving_stream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dt", [B.SV_C64, B.SV_C128])
+def test_packed_small_batch_matches_oracle(svlib, cuda_dev, dt):
+    ns = [1, 2, 3, 4, 5, 7, 8, 9, 10, 11, 12, 6, 12]
+    sets = [random_circuit(n, 40, seed=200 + i, max_controls=min(2, n - 1) if n > 1 else 0,
+                           max_unitary_k=min(4, n)) for i, n in enumerate(ns)]
+    got = B.sv_run_batch_small(ns, sets, dt)
+    tol = 1e-4 if dt == B.SV_C64 else 1e-10
+    for n, g, v in zip(ns, sets, got):
+        _, s = oracle.expect_z_all(oracle.run(n, g), n)
+        assert abs(v - s) < tol * max(1, n), (n, v, s)
+
+
+def test_packed_small_batch_result_independent_of_batch(svlib, cuda_dev):
+    ns = [8, 12, 10, 9]
+    sets = [serving_circuit(n, 7, seed=n) for n in ns]
+    mix = B.sv_run_batch_small(ns, sets)
+    for i in range(len(ns)):
+        alone = B.sv_run_batch_small([ns[i]], [sets[i]])
+        assert alone[0] == mix[i]
+
+
+def test_serving_loop_results_alone_equal_in_the_mix(svlib, cuda_dev):
+    import torch
+    from paper_2608_09733_gb300.serving import Server, request_gates, run_sequential
+    stream = serving_stream(rate=4000.0, duration=0.05, n_lo=8, n_hi=17, d_lo=2, d_hi=6, seed=3)
+    assert len(stream) > 50
+    srv = Server(B.SV_C64, budget_bytes=2e9, workers=4, max_small_batch=64)
+    stats, reqs = srv.run(stream)
+    assert stats.completed == len(stream) and stats.rejected == 0
+    assert stats.small > 0 and stats.large > 0
+    seq, sreqs = run_sequential(stream, B.SV_C64)
+    for r, q in zip(reqs, sreqs):
+        assert abs(r.result - q.result) < 1e-4, (r.n, r.result, q.result)
+    # a sample against the oracle
+    for r in reqs[:: max(1, len(reqs) // 8)]:
+        if r.n <= 14:
+            g = serving_circuit(r.n, r.depth, r.seed)
+            _, s = oracle.expect_z_all(oracle.run(r.n, g), r.n)
+            assert abs(r.result - s) < 1e-4 * r.n
+    torch.cuda.synchronize()
+
+
+def test_admission_rejects_states_beyond_the_budget(svlib, cuda_dev):
+    from paper_2608_09733_gb300.serving import Server
+    stream = [(0.0, 20, 2, 1), (0.0, 10, 2, 2)]
+    srv = Server(B.SV_C64, budget_bytes=(1 << 19) * 8, workers=1)
+    stats, reqs = srv.run(stream)
+    assert reqs[0].path == "rejected" and reqs[1].result is not None
+    assert stats.rejected == 1 and stats.completed == 1

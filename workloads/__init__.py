@@ -25,6 +25,7 @@ from .circuits import (  # noqa: F401
     hea_params,
     serving_stream,
     serving_circuit,
+    serving_angles,
     random_circuit,
     random_pauli_terms,
     haar_unitary,

@@ -194,13 +194,25 @@ def hea_params(batch: int, n_params: int, seed: int = 0) -> np.ndarray:
     return _rng(seed).random((batch, n_params)) * TWO_PI
 
 
-def serving_circuit(n: int, depth: int, rng: np.random.Generator) -> List[Gate]:
+def serving_angles(n: int, depth: int, seed: int) -> np.ndarray:
+    """(depth, n, 3) Haar-distributed U3 angles (theta, phi, lambda) of one
+    serving request, drawn at once from ``seed`` (see ``haar_u3_angles``)."""
+    u = _rng(seed).random((depth, n, 3))
+    ang = np.empty_like(u)
+    ang[..., 0] = np.arccos(1.0 - 2.0 * u[..., 0])
+    ang[..., 1] = u[..., 1] * TWO_PI
+    ang[..., 2] = u[..., 2] * TWO_PI
+    return ang
+
+
+def serving_circuit(n: int, depth: int, seed: int) -> List[Gate]:
     """One serving request: ``depth`` layers of Haar-angle U3 on all qubits
-    followed by the CNOT ladder i -> i+1."""
+    followed by the CNOT ladder i -> i+1; angles from ``serving_angles``."""
+    ang = serving_angles(n, depth, seed)
     gates: List[Gate] = []
-    for _ in range(depth):
+    for d in range(depth):
         for q in range(n):
-            gates.append(Gate("u3", [q], params=list(haar_u3_angles(rng))))
+            gates.append(Gate("u3", [q], params=[float(x) for x in ang[d, q]]))
         for q in range(n - 1):
             gates.append(Gate("x", [q + 1], controls=[q]))
     return gates
