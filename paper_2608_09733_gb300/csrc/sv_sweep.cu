@@ -173,6 +173,28 @@ __device__ __forceinline__ void r_sign(Cx<R> (&v)[NR], uint32_t rmask, uint32_t 
   }
 }
 
+// The register combinations j (bit j of the result) whose slots in rmask
+// hold rval: an AND of the per-slot patterns 0xAAAA, 0xCCCC, 0xF0F0, 0xFF00.
+__device__ __forceinline__ uint32_t sign_pattern(uint32_t rmask, uint32_t rval) {
+  uint32_t p = 0xFFFFu;
+  if (rmask & 1u) p &= (rval & 1u) ? 0xAAAAu : 0x5555u;
+  if (rmask & 2u) p &= (rval & 2u) ? 0xCCCCu : 0x3333u;
+  if (rmask & 4u) p &= (rval & 4u) ? 0xF0F0u : 0x0F0Fu;
+  if (rmask & 8u) p &= (rval & 8u) ? 0xFF00u : 0x00FFu;
+  return p;
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_neg(Cx<R> (&v)[NR], uint32_t neg) {
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if ((neg >> j) & 1u) {
+      v[j].re = -v[j].re;
+      v[j].im = -v[j].im;
+    }
+  }
+}
+
 // Diagonal op with k <= 2 matrix bits, each held by a register slot, by the
 // thread index, or fixed for the tile.
 template <typename R>
@@ -396,7 +418,22 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, i
         const uint32_t m[kRegQ] = {1u << ph.rp[0], 1u << ph.rp[1], 1u << ph.rp[2], 1u << ph.rp[3]};
         Cx<R> v[NR];
         reg_load<R>(v, s, tb, m);
-        for (int o = ph.first; o < ph.first + ph.nops; o++) apply_reg<R>(v, P.ops[o], P.coef, tb, base);
+        // Sign flips commute with each other: a run of them becomes one mask of
+        // the thread's amplitudes to negate, applied before the next other op.
+        uint32_t neg = 0;
+        for (int o = ph.first; o < ph.first + ph.nops; o++) {
+          const DevOp& op = P.ops[o];
+          if (op.kind == OPK_SIGN) {
+            if ((base & op.xmask) == op.xval && (tb & op.tmask) == op.tval) neg ^= sign_pattern(op.rmask, op.rval);
+            continue;
+          }
+          if (neg) {
+            apply_neg<R>(v, neg);
+            neg = 0;
+          }
+          apply_reg<R>(v, op, P.coef, tb, base);
+        }
+        if (neg) apply_neg<R>(v, neg);
         reg_store<R>(v, s, tb, m);
       }
     } else {
@@ -476,7 +513,7 @@ __global__ void __launch_bounds__(256) k_small_batch(const SweepProgram<R>* __re
   const int tsz = 1 << n;
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) s[phys<R>(a)] = Cx<R>{R(a == 0 ? 1 : 0), R(0)};
   __syncthreads();
-  for (int p = first_prog[b]; p < first_prog[b + 1]; p++) run_phases<R, 2>(progs[p], s, tsz, 0ull);
+  for (int p = first_prog[b]; p < first_prog[b + 1]; p++) run_phases<R, 5>(progs[p], s, tsz, 0ull);
   double acc = 0.0;
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
     const Cx<R> x = s[phys<R>(a)];

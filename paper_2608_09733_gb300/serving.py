@@ -46,12 +46,14 @@ class Request:
     done: Optional[float] = None
     result: Optional[float] = None
     path: str = ""
+    error: Optional[str] = None
 
 
 @dataclass
 class ServeStats:
     offered: int = 0
     completed: int = 0
+    failed: int = 0
     rejected: int = 0
     unfinished: int = 0
     wall_s: float = 0.0
@@ -137,6 +139,10 @@ class Server:
                     r.result = float(zout[r.n].item())
                     r.done = time.perf_counter() - t0
                     r.path = "large"
+                except Exception as e:  # reported per request; the worker keeps serving
+                    r.error = repr(e)
+                    r.path = "failed"
+                    r.done = time.perf_counter() - t0
                 finally:
                     with self._lock:
                         self._inflight -= need
@@ -146,7 +152,11 @@ class Server:
     def run(self, stream, time_limit: Optional[float] = None, realtime: bool = True) -> (ServeStats, List[Request]):
         """Serves ``stream`` = [(arrival_s, n, depth, seed), ...] (sorted).
         With ``realtime`` requests become visible at their arrival times; else
-        all are queued at t = 0 (saturation throughput)."""
+        all are queued at t = 0 (saturation throughput).  The run stops at
+        ``time_limit`` seconds (default: last arrival + 120 s); requests not
+        finished by then count as unfinished."""
+        if time_limit is None:
+            time_limit = (max((a for a, _, _, _ in stream), default=0.0) if realtime else 0.0) + 120.0
         torch = self.torch
         reqs = [Request(i, float(a) if realtime else 0.0, int(n), int(d), int(s))
                 for i, (a, n, d, s) in enumerate(stream)]
@@ -219,9 +229,10 @@ class Server:
             for t in threads:
                 t.join(timeout=30)
             torch.cuda.synchronize()
-        done = [r for r in reqs if r.done is not None]
+        stats.failed = sum(1 for r in reqs if r.path == "failed")
+        done = [r for r in reqs if r.done is not None and r.path != "failed"]
         stats.completed = len(done)
-        stats.unfinished = stats.offered - stats.completed - stats.rejected
+        stats.unfinished = stats.offered - stats.completed - stats.rejected - stats.failed
         stats.small = sum(1 for r in done if r.path == "small")
         stats.large = sum(1 for r in done if r.path == "large")
         stats.peak_inflight_bytes = int(self._peak)

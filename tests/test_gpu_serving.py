@@ -40,6 +40,7 @@ def test_serving_loop_results_alone_equal_in_the_mix(svlib, cuda_dev):
     assert len(stream) > 50
     srv = Server(B.SV_C64, budget_bytes=2e9, workers=4, max_small_batch=64)
     stats, reqs = srv.run(stream)
+    assert stats.failed == 0, [r.error for r in reqs if r.error]
     assert stats.completed == len(stream) and stats.rejected == 0
     assert stats.small > 0 and stats.large > 0
     seq, sreqs = run_sequential(stream, B.SV_C64)
