@@ -180,6 +180,24 @@ sv_status sv_expect(const void* state, int n_qubits, sv_dtype dtype, const sv_pa
 sv_status sv_expect_z_all(const void* state, int n_qubits, sv_dtype dtype, double* out, int out_on_device,
                           void* stream);
 
+/* sv_expect_z_all without any device allocation.  (The paper has no
+ * counterpart: this exists for callers that cannot let a library allocate
+ * device memory -- a process whose device memory all belongs to its own pool
+ * or allocator, or code that must not let a cudaMalloc/cudaFree synchronize
+ * the device under other streams.)
+ *   state  device, 2^n amplitudes of dtype, not modified
+ *   out    device, n_qubits + 1 doubles, as sv_expect_z_all; the call only
+ *          enqueues work on `stream`
+ * The per-block partial sums live in a fixed array inside the library (1024
+ * rows of 35 doubles, 280 KiB, held on every GPU that loads the library until
+ * the process exits) instead of allocated scratch.  n_qubits outside 1..34, or
+ * a GPU that would need more than 1024 partial rows, is SV_ERR_INVALID.  The
+ * first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and may return wrong
+ * values. */
+sv_status sv_expect_z_all_noalloc(const void* state, int n_qubits, sv_dtype dtype, double* out, void* stream);
+
 /* Planning summary of a circuit without running it (opts as in
  * sv_apply_circuit_ex, NULL = all zero): number of fused blocks (the paper's
  * fusion when 2 <= fuse_max_k <= 5, else the gate count), the number of

@@ -34,7 +34,8 @@ GATE_TYPES = {
 EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "sv_apply_circuit_ex", "sv_expect",
            "sv_expect_z_all",
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
-           "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small"]
+           "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
+           "sv_expect_z_all_noalloc"]
 
 
 class SvError(RuntimeError):
@@ -107,6 +108,7 @@ def load():
             "sv_profile_enable": ([ci], ci),
             "sv_adjoint_grad": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(SvPauliTerm), sz, ci, P(cd), P(cd), vp], ci),
             "sv_run_batch_small": ([ci, ci, P(ci), P(P(SvGate)), P(sz), vp, ci, vp], ci),
+            "sv_expect_z_all_noalloc": ([vp, ci, ci, vp, vp], ci),
             "sv_profile_read": ([P(SvProfileEntry), ci, P(ci), ci], ci),
         }
         for name, (args, res) in sig.items():
@@ -421,4 +423,12 @@ def sv_run_batch_small(n_qubits, gate_sets, dtype: int = SV_C64, out=None, strea
         _check(load().sv_run_batch_small(nreq, dtype, nq, ptrs, ng, host.ctypes.data_as(ctypes.c_void_p), 0, st))
         return host
     _check(load().sv_run_batch_small(nreq, dtype, nq, ptrs, ng, ctypes.c_void_p(out.data_ptr()), 1, st))
+    return out
+
+
+def sv_expect_z_all_noalloc(state, out, stream=None):
+    """sv_expect_z_all into the device float64 tensor ``out`` (n + 1) with the
+    library's fixed scratch array instead of allocated scratch (async)."""
+    _check(load().sv_expect_z_all_noalloc(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state),
+                                          ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
