@@ -387,6 +387,13 @@ def main():
     sweep_gbs = sw["bytes"] / (sw["total_ms"] / 1e3) / 1e9 if sw["launches"] else None
     peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     traffic = read_traffic("sweep_%dq_%s" % (n, args.dtype), stamp)
+    # ALU side: the complex arithmetic the gates need, 8 * 2^k - 2 real flops
+    # per amplitude for a dense k-qubit gate (U3: 14), none for CZ; against
+    # the FP32 (complex64) or FP64 (complex128) rate from unit counts x clock
+    flops_step = sum(14.0 for g in gates if g.name == "u3") * (2 ** n)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = (152 * 128 * 2 * sm_mhz * 1e6 / 1e12) if dt == sv.SV_C64 else 1.25
+    alu_achieved = flops_step * args.steps / (sw["total_ms"] / 1e3) / 1e12 if sw["launches"] else None
 
     # e2e: the same workload through the host-buffer entry point (H2D/D2H inside)
     e2e = None
@@ -423,7 +430,11 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
                          "frac": (sweep_gbs / peak) if sweep_gbs else None, "traffic": traffic,
                          "peak_source": peak_src + " hbm_gbs",
-                         "launches": sw["launches"], "avg_launch_ms": sw["total_ms"] / max(1, sw["launches"])},
+                         "launches": sw["launches"], "avg_launch_ms": sw["total_ms"] / max(1, sw["launches"]),
+                         "alu_side": {"achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                                      "frac": (alu_achieved / alu_peak) if alu_achieved else None,
+                                      "peak_source": ("FP32: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz)
+                                      if dt == sv.SV_C64 else "FP64: nominal 1.25 TFLOP/s"}},
             "kernels": prof,
             "gpu_launches": launches,
             "clocks": clk,

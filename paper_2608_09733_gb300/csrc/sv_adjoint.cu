@@ -68,6 +68,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Shared-memory slot of local amplitude l (XOR swizzle of 16-byte granules,
+// the same as the single-state sweep).
+template <typename R>
+__device__ __forceinline__ uint32_t sw(uint32_t l) {
+  if constexpr (sizeof(Cx<R>) == 8)
+    return l ^ ((l >> 3) & 14u);
+  else
+    return l ^ ((l >> 3) & 7u);
+}
+
 // Element (r, c) of the op's matrix, or of its conjugate transpose.
 template <typename R>
 __device__ __forceinline__ Cx<R> mel(const Cx<R>* M, int d, int r, int c, bool dag) {
@@ -93,7 +103,7 @@ __device__ __forceinline__ void bop_dense(Cx<R>* sp, Cx<R>* sl, int tsz, const B
 #pragma unroll
       for (int i = 0; i < K; i++)
         if ((j >> i) & 1) x |= 1u << op.pos[i];
-      idx[j] = x;
+      idx[j] = sw<R>(x);
     }
     Cx<R> p[D];
 #pragma unroll
@@ -142,13 +152,14 @@ __device__ __forceinline__ void bop_diag(Cx<R>* sp, Cx<R>* sl, int tsz, const BO
     for (int i = 0; i < op.k; i++)
       if (op.pos[i] != 0xFF) di |= ((a >> op.pos[i]) & 1u) << i;
     Cx<R> u = dag ? conjx(M[di]) : M[di];
-    Cx<R> p = sp[a];
+    const uint32_t pa = sw<R>(a);
+    Cx<R> p = sp[pa];
     if (REV) {
-      Cx<R> l = sl[a];
+      Cx<R> l = sl[pa];
       if (op.grad) acc += im_cdot(l, cmul(G[di], p));
-      sl[a] = cmul(u, l);
+      sl[pa] = cmul(u, l);
     }
-    sp[a] = cmul(u, p);
+    sp[pa] = cmul(u, p);
   }
 }
 
@@ -161,7 +172,8 @@ __device__ __forceinline__ void bop_antidiag(Cx<R>* sp, Cx<R>* sl, int tsz, cons
   for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 1); g += blockDim.x) {
     uint32_t i0 = ins0(g, p);
     if ((i0 & op.lmask) != op.lval) continue;
-    uint32_t i1 = i0 | (1u << p);
+    uint32_t i1 = sw<R>(i0 | (1u << p));
+    i0 = sw<R>(i0);
     Cx<R> v0 = sp[i0], v1 = sp[i1];
     sp[i0] = cmul(a, v1);
     sp[i1] = cmul(bb, v0);
@@ -178,7 +190,7 @@ __device__ __forceinline__ void bop_swap(Cx<R>* sp, Cx<R>* sl, int tsz, const BO
   for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 2); g += blockDim.x) {
     uint32_t b = ins0(ins0(g, op.spos[0]), op.spos[1]);
     if ((b & op.lmask) != op.lval) continue;
-    uint32_t i01 = b | (1u << op.pos[0]), i10 = b | (1u << op.pos[1]);
+    uint32_t i01 = sw<R>(b | (1u << op.pos[0])), i10 = sw<R>(b | (1u << op.pos[1]));
     Cx<R> t = sp[i01];
     sp[i01] = sp[i10];
     sp[i10] = t;
@@ -187,6 +199,236 @@ __device__ __forceinline__ void bop_swap(Cx<R>* sp, Cx<R>* sl, int tsz, const BO
       sl[i01] = sl[i10];
       sl[i10] = t;
     }
+  }
+}
+
+// ---------------------------------------------------------------- register phases
+//
+// As in the single-state sweep, a register phase gives each thread the 16
+// amplitudes of four register qubits -- here of psi and, in reverse mode, of
+// lambda -- and applies its ops with FMAs on registers.
+
+constexpr int NR = 1 << kRegQ;
+
+__device__ __forceinline__ uint32_t reg_bits(int j, const uint32_t (&m)[kRegQ]) {
+  return ((j & 1) ? m[0] : 0u) | ((j & 2) ? m[1] : 0u) | ((j & 4) ? m[2] : 0u) | ((j & 8) ? m[3] : 0u);
+}
+
+// Matrix element (r, c) of U (or U^dag) of dimension D.
+template <typename R, int D>
+__device__ __forceinline__ Cx<R> uel(const Cx<R>* M, int r, int c, bool dag) {
+  return dag ? conjx(M[c * D + r]) : M[r * D + c];
+}
+
+template <typename R, int S, bool REV>
+__device__ __forceinline__ void b_dense1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
+                                         const Cx<R>* G, R& acc) {
+  const bool dag = op.dagger;
+  const Cx<R> u00 = uel<R, 2>(M, 0, 0, dag), u01 = uel<R, 2>(M, 0, 1, dag);
+  const Cx<R> u10 = uel<R, 2>(M, 1, 0, dag), u11 = uel<R, 2>(M, 1, 1, dag);
+  const bool grad = REV && op.grad;
+  const uint32_t rm = op.rmask, rv = op.rval;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    if ((j & rm) != rv) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> a = p[j], b = p[j1];
+    if (grad) {
+      const Cx<R> g0 = cfma(G[1], b, cmul(G[0], a)), g1 = cfma(G[3], b, cmul(G[2], a));
+      acc += im_cdot(l[j], g0) + im_cdot(l[j1], g1);
+    }
+    p[j] = cfma(u01, b, cmul(u00, a));
+    p[j1] = cfma(u11, b, cmul(u10, a));
+    if (REV) {
+      const Cx<R> c = l[j], d = l[j1];
+      l[j] = cfma(u01, d, cmul(u00, c));
+      l[j1] = cfma(u11, d, cmul(u10, c));
+    }
+  }
+}
+
+// A = register slot of matrix bit 0, B = of matrix bit 1.
+template <typename R, int A, int B, bool REV>
+__device__ __forceinline__ void b_dense2(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
+                                         const Cx<R>* G, R& acc) {
+  const bool dag = op.dagger;
+  const bool grad = REV && op.grad;
+  const uint32_t rm = op.rmask, rv = op.rval;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & ((1 << A) | (1 << B))) continue;
+    if ((j & rm) != rv) continue;
+    const int idx[4] = {j, j | (1 << A), j | (1 << B), j | (1 << A) | (1 << B)};
+    Cx<R> x[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) x[c] = p[idx[c]];
+    if (grad) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        Cx<R> g = cmul(G[r * 4], x[0]);
+#pragma unroll
+        for (int c = 1; c < 4; c++) g = cfma(G[r * 4 + c], x[c], g);
+        acc += im_cdot(l[idx[r]], g);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      Cx<R> o = cmul(uel<R, 4>(M, r, 0, dag), x[0]);
+#pragma unroll
+      for (int c = 1; c < 4; c++) o = cfma(uel<R, 4>(M, r, c, dag), x[c], o);
+      p[idx[r]] = o;
+    }
+    if (REV) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) x[c] = l[idx[c]];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        Cx<R> o = cmul(uel<R, 4>(M, r, 0, dag), x[0]);
+#pragma unroll
+        for (int c = 1; c < 4; c++) o = cfma(uel<R, 4>(M, r, c, dag), x[c], o);
+        l[idx[r]] = o;
+      }
+    }
+  }
+}
+
+template <typename R, int S, bool REV>
+__device__ __forceinline__ void b_anti1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M) {
+  const bool flip = op.flags & OPF_FLIP;
+  const Cx<R> a = op.dagger ? conjx(M[1]) : M[0], b = op.dagger ? conjx(M[0]) : M[1];
+  const uint32_t rm = op.rmask, rv = op.rval;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    if ((j & rm) != rv) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> x = p[j], y = p[j1];
+    p[j] = flip ? y : cmul(a, y);
+    p[j1] = flip ? x : cmul(b, x);
+    if (REV) {
+      const Cx<R> u = l[j], w = l[j1];
+      l[j] = flip ? w : cmul(a, w);
+      l[j1] = flip ? u : cmul(b, u);
+    }
+  }
+}
+
+template <typename R, int A, int B, bool REV>
+__device__ __forceinline__ void b_swap(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op) {
+  const uint32_t rm = op.rmask, rv = op.rval;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & ((1 << A) | (1 << B))) continue;
+    if ((j & rm) != rv) continue;
+    Cx<R> t = p[j | (1 << A)];
+    p[j | (1 << A)] = p[j | (1 << B)];
+    p[j | (1 << B)] = t;
+    if (REV) {
+      t = l[j | (1 << A)];
+      l[j | (1 << A)] = l[j | (1 << B)];
+      l[j | (1 << B)] = t;
+    }
+  }
+}
+
+template <typename R, bool REV>
+__device__ __forceinline__ void b_diag(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
+                                       const Cx<R>* G, uint32_t tb, uint64_t base, R& acc) {
+  uint32_t dbase = 0;
+  int s0 = -1, s1 = -1, b0 = 0, b1 = 0;
+  for (int i = 0; i < op.k; i++) {
+    if (op.rs[i] != 0xFF) {
+      if (s0 < 0) {
+        s0 = op.rs[i];
+        b0 = i;
+      } else {
+        s1 = op.rs[i];
+        b1 = i;
+      }
+    } else if (op.pos[i] != 0xFF) {
+      dbase |= ((tb >> op.pos[i]) & 1u) << i;
+    } else {
+      dbase |= (uint32_t)((base >> op.gq[i]) & 1ull) << i;
+    }
+  }
+  const uint32_t i1 = s0 >= 0 ? (1u << b0) : 0u, i2 = s1 >= 0 ? (1u << b1) : 0u;
+  const bool dag = op.dagger, grad = REV && op.grad;
+  Cx<R> f[4], g[4];
+  const uint32_t di[4] = {dbase, dbase | i1, dbase | i2, dbase | i1 | i2};
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    f[c] = dag ? conjx(M[di[c]]) : M[di[c]];
+    g[c] = grad ? G[di[c]] : Cx<R>{R(0), R(0)};
+  }
+  const int sh0 = s0 >= 0 ? s0 : 0, sh1 = s1 >= 0 ? s1 : 0;
+  const uint32_t m0 = s0 >= 0 ? 1u : 0u, m1 = s1 >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if ((j & op.rmask) != op.rval) continue;
+    const uint32_t c0 = ((uint32_t)j >> sh0) & m0, c1 = ((uint32_t)j >> sh1) & m1;
+    const Cx<R> fj = c1 ? (c0 ? f[3] : f[2]) : (c0 ? f[1] : f[0]);
+    if (grad) {
+      const Cx<R> gj = c1 ? (c0 ? g[3] : g[2]) : (c0 ? g[1] : g[0]);
+      acc += im_cdot(l[j], cmul(gj, p[j]));
+    }
+    p[j] = cmul(fj, p[j]);
+    if (REV) l[j] = cmul(fj, l[j]);
+  }
+}
+
+template <typename R, bool REV>
+__device__ __forceinline__ void b_apply(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
+                                        const Cx<R>* G, uint32_t tb, uint64_t base, R& acc) {
+  switch (op.kind) {
+    case OPK_DENSE:
+    case OPK_REAL:
+      if (op.k == 1) {
+        switch (op.rs[0]) {
+          case 0: b_dense1<R, 0, REV>(p, l, op, M, G, acc); break;
+          case 1: b_dense1<R, 1, REV>(p, l, op, M, G, acc); break;
+          case 2: b_dense1<R, 2, REV>(p, l, op, M, G, acc); break;
+          default: b_dense1<R, 3, REV>(p, l, op, M, G, acc); break;
+        }
+      } else {
+        switch (op.rs[0] * 4 + op.rs[1]) {
+          case 1: b_dense2<R, 0, 1, REV>(p, l, op, M, G, acc); break;
+          case 2: b_dense2<R, 0, 2, REV>(p, l, op, M, G, acc); break;
+          case 3: b_dense2<R, 0, 3, REV>(p, l, op, M, G, acc); break;
+          case 4: b_dense2<R, 1, 0, REV>(p, l, op, M, G, acc); break;
+          case 6: b_dense2<R, 1, 2, REV>(p, l, op, M, G, acc); break;
+          case 7: b_dense2<R, 1, 3, REV>(p, l, op, M, G, acc); break;
+          case 8: b_dense2<R, 2, 0, REV>(p, l, op, M, G, acc); break;
+          case 9: b_dense2<R, 2, 1, REV>(p, l, op, M, G, acc); break;
+          case 11: b_dense2<R, 2, 3, REV>(p, l, op, M, G, acc); break;
+          case 12: b_dense2<R, 3, 0, REV>(p, l, op, M, G, acc); break;
+          case 13: b_dense2<R, 3, 1, REV>(p, l, op, M, G, acc); break;
+          default: b_dense2<R, 3, 2, REV>(p, l, op, M, G, acc); break;
+        }
+      }
+      break;
+    case OPK_ANTIDIAG:
+      switch (op.rs[0]) {
+        case 0: b_anti1<R, 0, REV>(p, l, op, M); break;
+        case 1: b_anti1<R, 1, REV>(p, l, op, M); break;
+        case 2: b_anti1<R, 2, REV>(p, l, op, M); break;
+        default: b_anti1<R, 3, REV>(p, l, op, M); break;
+      }
+      break;
+    case OPK_SWAP: {
+      const int a = op.rs[0] < op.rs[1] ? op.rs[0] : op.rs[1], b = op.rs[0] < op.rs[1] ? op.rs[1] : op.rs[0];
+      switch (a * 4 + b) {
+        case 1: b_swap<R, 0, 1, REV>(p, l, op); break;
+        case 2: b_swap<R, 0, 2, REV>(p, l, op); break;
+        case 3: b_swap<R, 0, 3, REV>(p, l, op); break;
+        case 6: b_swap<R, 1, 2, REV>(p, l, op); break;
+        case 7: b_swap<R, 1, 3, REV>(p, l, op); break;
+        default: b_swap<R, 2, 3, REV>(p, l, op); break;
+      }
+      break;
+    }
+    case OPK_DIAG: b_diag<R, REV>(p, l, op, M, G, tb, base, acc); break;
+    default: break;
   }
 }
 
@@ -199,6 +441,7 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
   const int tsz = 1 << h.m;
   Cx<R>* sp = reinterpret_cast<Cx<R>*>(smem_raw);
   Cx<R>* sl = sp + (REV ? tsz : 0);
+  uint64_t* hi_off = reinterpret_cast<uint64_t*>(sp + (REV ? 2 * tsz : tsz));
   __shared__ double gacc[kBatchGacc][8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kBatchGacc * 8; i += blockDim.x) gacc[i / 8][i % 8] = 0.0;
@@ -208,44 +451,98 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
   constexpr int A = 16 / sizeof(Cx<R>);
   const int nvec = tsz / A;
   const uint64_t ntiles = 1ull << (h.n - h.m);
+  const int nhi = 1 << (h.m - h.L);
+  for (int c = threadIdx.x; c < nhi; c += blockDim.x) hi_off[c] = local_offset((uint32_t)c << h.L, h);
+  const uint32_t lowmask = (1u << h.L) - 1u;
   __syncthreads();
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     uint64_t base = tile;
     for (int i = 0; i < h.m; i++) base = ins0_64(base, h.tq[i]);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-      uint64_t off = local_offset((uint32_t)(v * A), h);
-      reinterpret_cast<uint4*>(sp)[v] = *reinterpret_cast<const uint4*>(ps + (base + off));
-      if (REV) reinterpret_cast<uint4*>(sl)[v] = *reinterpret_cast<const uint4*>(ls + (base + off));
+      const uint32_t l = (uint32_t)(v * A);
+      const uint64_t off = base + (hi_off[l >> h.L] | (l & lowmask));
+      *reinterpret_cast<uint4*>(sp + sw<R>(l)) = *reinterpret_cast<const uint4*>(ps + off);
+      if (REV) *reinterpret_cast<uint4*>(sl + sw<R>(l)) = *reinterpret_cast<const uint4*>(ls + off);
     }
     __syncthreads();
-    for (int o = 0; o < h.nops; o++) {
-      const BOp& op = P.ops[o];
-      if ((base & op.xmask) != op.xval) continue;  // uniform over the block
-      const Cx<R>* M = op.table ? table + ((uint64_t)op.coef * h.batch + bidx) * kTableStride : P.pool + op.coef;
-      const Cx<R>* G = P.pool + op.gen;
-      R acc = R(0);
-      switch (op.kind) {
-        case OPK_DENSE:
-          if (op.k == 1)
-            bop_dense<R, 1, REV>(sp, sl, tsz, op, M, G, acc);
-          else
-            bop_dense<R, 2, REV>(sp, sl, tsz, op, M, G, acc);
-          break;
-        case OPK_DIAG: bop_diag<R, REV>(sp, sl, tsz, op, M, G, base, acc); break;
-        case OPK_ANTIDIAG: bop_antidiag<R, REV>(sp, sl, tsz, op, M); break;
-        case OPK_SWAP: bop_swap<R, REV>(sp, sl, tsz, op); break;
-        default: break;
-      }
-      if (REV && op.grad) {
-        double w = warp_sum((double)acc);
-        if (lane == 0) gacc[op.gacc][warp] += w;
+    for (int ph_i = 0; ph_i < h.nphases; ph_i++) {
+      const Phase& ph = P.ph[ph_i];
+      if (ph.kind == PH_REG) {
+        const bool active = threadIdx.x < (1u << ph.ntpos);
+        if ((threadIdx.x & ~31u) < (1u << ph.ntpos)) {  // the warp holds at least one group
+          uint32_t tb = 0;
+          for (int i = 0; i < ph.ntpos; i++)
+            if ((threadIdx.x >> i) & 1u) tb |= 1u << ph.tpos[i];
+          const uint32_t m[kRegQ] = {1u << ph.rp[0], 1u << ph.rp[1], 1u << ph.rp[2], 1u << ph.rp[3]};
+          Cx<R> p[NR], l[NR];
+          if (active) {
+#pragma unroll
+            for (int j = 0; j < NR; j++) {
+              const uint32_t a = sw<R>(tb | reg_bits(j, m));
+              p[j] = sp[a];
+              if (REV) l[j] = sl[a];
+            }
+          }
+          for (int o = ph.first; o < ph.first + ph.nops; o++) {
+            const BOp& op = P.ops[o];
+            R acc = R(0);
+            if (active && (base & op.xmask) == op.xval && (tb & op.tmask) == op.tval) {
+              const Cx<R>* M =
+                  op.table ? table + ((uint64_t)op.coef * h.batch + bidx) * kTableStride : P.pool + op.coef;
+              b_apply<R, REV>(p, l, op, M, P.pool + op.gen, tb, base, acc);
+            }
+            if (REV && op.grad) {  // warp sum in the state's precision, then double
+              R w = acc;
+#pragma unroll
+              for (int s2 = 16; s2 > 0; s2 >>= 1) w += __shfl_xor_sync(0xffffffffu, w, s2);
+              if (lane == 0) gacc[op.gacc][warp] += (double)w;
+            }
+          }
+          if (active) {
+#pragma unroll
+            for (int j = 0; j < NR; j++) {
+              const uint32_t a = sw<R>(tb | reg_bits(j, m));
+              sp[a] = p[j];
+              if (REV) sl[a] = l[j];
+            }
+          }
+        }
+      } else {
+        // tiles too small for register groups (m < 4): the op group by group
+        // in shared memory, through the same swizzle
+        const BOp& op = P.ops[ph.first];
+        if ((base & op.xmask) == op.xval) {
+          const Cx<R>* M = op.table ? table + ((uint64_t)op.coef * h.batch + bidx) * kTableStride : P.pool + op.coef;
+          const Cx<R>* G = P.pool + op.gen;
+          R acc = R(0);
+          switch (op.kind) {
+            case OPK_DENSE:
+            case OPK_REAL:
+              if (op.k == 1)
+                bop_dense<R, 1, REV>(sp, sl, tsz, op, M, G, acc);
+              else
+                bop_dense<R, 2, REV>(sp, sl, tsz, op, M, G, acc);
+              break;
+            case OPK_DIAG: bop_diag<R, REV>(sp, sl, tsz, op, M, G, base, acc); break;
+            case OPK_ANTIDIAG: bop_antidiag<R, REV>(sp, sl, tsz, op, M); break;
+            case OPK_SWAP: bop_swap<R, REV>(sp, sl, tsz, op); break;
+            default: break;
+          }
+          if (REV && op.grad) {
+            double w = warp_sum((double)acc);
+            if (lane == 0) gacc[op.gacc][warp] += w;
+          }
+        } else if (REV && op.grad) {
+          // nothing to add, but keep the warp reduction uniform
+        }
       }
       __syncthreads();
     }
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-      uint64_t off = local_offset((uint32_t)(v * A), h);
-      *reinterpret_cast<uint4*>(ps + (base + off)) = reinterpret_cast<uint4*>(sp)[v];
-      if (REV) *reinterpret_cast<uint4*>(ls + (base + off)) = reinterpret_cast<uint4*>(sl)[v];
+      const uint32_t l = (uint32_t)(v * A);
+      const uint64_t off = base + (hi_off[l >> h.L] | (l & lowmask));
+      *reinterpret_cast<uint4*>(ps + off) = *reinterpret_cast<const uint4*>(sp + sw<R>(l));
+      if (REV) *reinterpret_cast<uint4*>(ls + off) = *reinterpret_cast<const uint4*>(sl + sw<R>(l));
     }
     __syncthreads();
   }
@@ -253,9 +550,9 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
     for (int o = threadIdx.x; o < h.nops; o += blockDim.x) {
       const BOp& op = P.ops[o];
       if (!op.grad) continue;
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += gacc[op.gacc][w];
-      gscratch[((uint64_t)bidx * h.ngrad_total + op.gidx) * gridDim.x + blockIdx.x] = s;
+      double s2 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s2 += gacc[op.gacc][w];
+      gscratch[((uint64_t)bidx * h.ngrad_total + op.gidx) * gridDim.x + blockIdx.x] = s2;
     }
   }
 }
@@ -357,7 +654,7 @@ int batch_grid_x(int n, int m, int batch) {
 template <typename R>
 cudaError_t launch_batch_sweep(Cx<R>* psi, Cx<R>* lam, const Cx<R>* table, double* gscratch, int grid_x,
                                const BatchProgram<R>& prog, bool reverse, cudaStream_t stream) {
-  const int smem = (int)sizeof(Cx<R>) << prog.h.m << (reverse ? 1 : 0);
+  const int smem = ((int)sizeof(Cx<R>) << prog.h.m << (reverse ? 1 : 0)) + (8 << (prog.h.m - prog.h.L));
   static int configured[2][64] = {{0}};
   int dev = 0;
   cudaGetDevice(&dev);

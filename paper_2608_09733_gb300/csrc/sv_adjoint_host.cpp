@@ -91,6 +91,7 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
     return at;
   };
   if ((int)sw.ops.size() > kBatchOps) fail(SV_ERR_INVALID, "internal: too many ops in a batch program");
+  std::vector<uint32_t> need(sw.ops.size(), 0);
   for (size_t oi = 0; oi < sw.ops.size(); oi++) {
     const AGate& g = ag[order[sw.ops[oi]]];
     const LOp& op = g.op;
@@ -98,6 +99,7 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
     std::memset(&d, 0, sizeof(d));
     d.kind = op.kind;
     d.k = (uint8_t)op.k;
+    d.rs[0] = d.rs[1] = 0xFF;
     int sp[2], ns = 0;
     for (int i = 0; i < op.k; i++) {
       int l = loc[op.q[i]];
@@ -108,6 +110,7 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
         if (l < 0) fail(SV_ERR_INVALID, "internal: target outside the tile");
         d.pos[i] = (uint8_t)l;
         sp[ns++] = l;
+        need[oi] |= 1u << l;
       }
     }
     if (ns == 2 && sp[0] > sp[1]) std::swap(sp[0], sp[1]);
@@ -123,6 +126,8 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
       }
     }
     d.dagger = reverse ? 1 : 0;
+    if (op.kind == OPK_ANTIDIAG && op.m.size() == 2 && op.m[0] == cplx(1.0) && op.m[1] == cplx(1.0))
+      d.flags |= OPF_FLIP;
     if (g.param) {
       d.table = 1;
       d.coef = (uint32_t)g.pidx;
@@ -140,6 +145,69 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
   }
   P.h.nops = (int)sw.ops.size();
   P.h.ngacc = nacc;
+
+  // phases: consecutive ops whose moving qubits fit four register slots; tiles
+  // of fewer than four qubits run every op in shared memory
+  const bool reg_ok = sw.m >= kRegQ && sw.m - kRegQ <= 8;
+  int nph = 0;
+  auto add_phase = [&](PhaseKind kind, int first, int nops, uint32_t nd) {
+    if (nph >= kMaxPhases) fail(SV_ERR_INVALID, "internal: too many phases");
+    Phase& ph = P.ph[nph++];
+    std::memset(&ph, 0, sizeof(ph));
+    ph.kind = kind;
+    ph.first = (uint8_t)first;
+    ph.nops = (uint8_t)nops;
+    if (kind != PH_REG) return;
+    uint32_t rp = nd;
+    if (__builtin_popcount(rp) < kRegQ && !(rp & 1u)) rp |= 1u;
+    for (int q = sw.m - 1; q >= 0 && __builtin_popcount(rp) < kRegQ; q--) rp |= 1u << q;
+    int slot_of[32], k2 = 0, nt = 0;
+    for (int q = 0; q < sw.m; q++) {
+      if ((rp >> q) & 1u) {
+        slot_of[q] = k2;
+        ph.rp[k2++] = (uint8_t)q;
+      } else {
+        slot_of[q] = -1;
+        ph.tpos[nt++] = (uint8_t)q;
+      }
+    }
+    ph.ntpos = (uint8_t)nt;
+    for (int o = first; o < first + nops; o++) {
+      BOp& d = P.ops[o];
+      for (int i = 0; i < d.k; i++)
+        d.rs[i] = (d.pos[i] != 0xFF && slot_of[d.pos[i]] >= 0) ? (uint8_t)slot_of[d.pos[i]] : 0xFF;
+      for (int q = 0; q < sw.m; q++) {
+        if (!((d.lmask >> q) & 1u)) continue;
+        const bool v = (d.lval >> q) & 1u;
+        if (slot_of[q] >= 0) {
+          d.rmask |= 1u << slot_of[q];
+          if (v) d.rval |= 1u << slot_of[q];
+        } else {
+          d.tmask |= 1u << q;
+          if (v) d.tval |= 1u << q;
+        }
+      }
+    }
+  };
+  int cur_first = -1, cur_n = 0;
+  uint32_t cur_need = 0;
+  for (int o = 0; o < (int)sw.ops.size(); o++) {
+    if (!reg_ok) {
+      add_phase(PH_SMEM, o, 1, 0);
+      continue;
+    }
+    if (cur_n && __builtin_popcount(cur_need | need[o]) <= kRegQ) {
+      cur_need |= need[o];
+      cur_n++;
+    } else {
+      if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
+      cur_first = o;
+      cur_n = 1;
+      cur_need = need[o];
+    }
+  }
+  if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
+  P.h.nphases = nph;
 }
 
 template <typename R>

@@ -378,17 +378,86 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
   if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
   P.h.nphases = nph;
 
+  // Final op list.  In a register phase, a run of uncontrolled one-qubit dense
+  // ops becomes one KRON op (same-slot matrices multiplied in double, distinct
+  // slots commute); sign flips carry their pattern of register combinations;
+  // flags tell the kernel which control tests to make.
+  auto u1_free = [](const Tmp& t) {
+    return (t.d.kind == OPK_DENSE || t.d.kind == OPK_REAL) && t.d.k == 1 && t.d.lmask == 0 && t.d.xmask == 0;
+  };
+  auto pattern = [](uint32_t rmask, uint32_t rval) {
+    uint32_t p = 0;
+    for (int j = 0; j < 16; j++)
+      if (((uint32_t)j & rmask) == rval) p |= 1u << j;
+    return p;
+  };
+  std::vector<Tmp> fin;
+  fin.reserve(ts.size());
+  for (int p = 0; p < nph; p++) {
+    Phase& ph = P.ph[p];
+    const int first = ph.first, nops = ph.nops;
+    const int nf = (int)fin.size();
+    if (ph.kind == PH_SMEM) {
+      fin.push_back(ts[first]);
+    } else {
+      for (int o = first; o < first + nops;) {
+        if (u1_free(ts[o]) && o + 1 < first + nops && u1_free(ts[o + 1])) {
+          Tmp k;
+          std::memset(&k.d, 0, sizeof(k.d));
+          k.d.kind = OPK_KRON;
+          k.smem = false;
+          k.need = 0;
+          std::vector<cplx> mats(16, 0.0);
+          for (int s2 = 0; s2 < 4; s2++) mats[4 * s2] = mats[4 * s2 + 3] = 1.0;
+          uint32_t present = 0;
+          for (; o < first + nops && u1_free(ts[o]); o++) {
+            const int sl = ts[o].d.rs[0];
+            const std::vector<cplx>& U = ts[o].m;
+            cplx* M = &mats[4 * sl];
+            const cplx a = U[0] * M[0] + U[1] * M[2], b = U[0] * M[1] + U[1] * M[3];
+            const cplx c = U[2] * M[0] + U[3] * M[2], d = U[2] * M[1] + U[3] * M[3];
+            M[0] = a; M[1] = b; M[2] = c; M[3] = d;
+            present |= 1u << sl;
+          }
+          k.d.rmask = (uint8_t)present;
+          k.m = mats;
+          fin.push_back(k);
+        } else {
+          fin.push_back(ts[o]);
+          o++;
+        }
+      }
+      for (int i = nf; i < (int)fin.size(); i++) {
+        DevOp& d = fin[i].d;
+        d.pad &= OPF_FLIP;
+        if (d.kind != OPK_KRON) {
+          if (d.tmask) d.pad |= OPF_TCOND;
+          if (d.xmask) d.pad |= OPF_XCOND;
+        }
+      }
+    }
+    if ((int)fin.size() - nf > 255) fail(SV_ERR_INVALID, "internal: phase too long");
+    ph.first = (uint8_t)nf;
+    ph.nops = (uint8_t)((int)fin.size() - nf);
+  }
+  if ((int)fin.size() > kMaxOps) fail(SV_ERR_INVALID, "internal: too many ops");
+  P.h.nops = (int)fin.size();
+
   int coef = 0;
-  for (size_t oi = 0; oi < ts.size(); oi++) {
-    ts[oi].d.coef = (uint32_t)coef;
-    for (const cplx& v : ts[oi].m) {
+  for (size_t oi = 0; oi < fin.size(); oi++) {
+    fin[oi].d.coef = (uint32_t)coef;
+    for (const cplx& v : fin[oi].m) {
       if (coef >= SweepProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: coefficient pool overflow");
       P.coef[coef].re = (R)v.real();
       P.coef[coef].im = (R)v.imag();
       coef++;
     }
-    P.ops[oi] = ts[oi].d;
+    P.ops[oi] = fin[oi].d;
   }
+  for (int p = 0; p < nph; p++)
+    if (P.ph[p].kind == PH_REG)
+      for (int o = P.ph[p].first; o < P.ph[p].first + P.ph[p].nops; o++)
+        if (P.ops[o].kind == OPK_SIGN) P.ops[o].coef = pattern(P.ops[o].rmask, P.ops[o].rval);
   P.h.ncoef = coef;
   static const bool debug = std::getenv("SV_DEBUG_PLAN") != nullptr;
   if (debug) {

@@ -32,7 +32,14 @@ enum OpKind : uint8_t {
   OPK_ANTIDIAG = 3, // one qubit: out0 = a * v1, out1 = b * v0 (X, Y, CNOT ...)
   OPK_SWAP = 4,     // two local positions: exchange |01> and |10>
   OPK_SIGN = 5,     // negate the amplitudes whose bits match (CZ, Z, CCZ ...): no coefficients
+  OPK_KRON = 6,     // register phase only: uncontrolled 2x2 matrices on register slots (rmask = the
+                    // slots present), four blocks of four coefficients at `coef`
 };
+
+// DevOp.pad flag bits
+constexpr uint8_t OPF_FLIP = 1;   // anti-diagonal (1, 1): a pure bit flip
+constexpr uint8_t OPF_TCOND = 2;  // tmask/tval is not empty
+constexpr uint8_t OPF_XCOND = 4;  // xmask/xval is not empty
 
 constexpr int kMaxTileQ = 14;  // 2^14 amplitudes: 128 KiB (c64) of shared memory
 constexpr int kMaxOps = 96;
@@ -57,8 +64,9 @@ struct DevOp {
   uint32_t lmask, lval; // all local controls (shared-memory path)
   uint32_t tmask, tval; // local controls held by the thread index (register path)
   uint64_t xmask, xval; // controls outside the tile (global bit mask / required values)
-  uint32_t coef;        // first coefficient in the program's pool
-  uint32_t pad;
+  uint32_t coef;        // first coefficient in the program's pool (OPK_SIGN in a register
+                        // phase: the 16-bit pattern of register combinations to negate)
+  uint32_t pad;         // OPF_* flags
 };
 static_assert(sizeof(DevOp) == 64, "DevOp layout");
 
@@ -110,40 +118,45 @@ struct SweepProgram {
 // projector) and then applies the conjugate transpose to psi and lambda.
 
 struct BOp {
-  uint8_t kind;         // OPK_DENSE / OPK_DIAG / OPK_ANTIDIAG / OPK_SWAP, k <= 2
+  uint8_t kind;         // OPK_DENSE / OPK_DIAG / OPK_ANTIDIAG / OPK_SWAP / OPK_SIGN, k <= 2
   uint8_t k;
   uint8_t pos[2];       // local positions (matrix order); OPK_DIAG: 0xFF = external
   uint8_t spos[2];      // sorted local positions
   uint8_t gq[2];        // global qubits (OPK_DIAG external bits)
+  uint8_t rs[2];        // register slots in a register phase (0xFF: none)
   uint8_t table;        // 1: coefficients from the per-state table row `coef`
   uint8_t dagger;       // 1: apply the conjugate transpose
   uint8_t grad;         // 1: accumulate Im <lambda|G|psi> into gradient `gidx`
   uint8_t gacc;         // local accumulator index of a gradient op
-  uint32_t lmask, lval;
+  uint8_t rmask, rval;  // controls on register slots (register phase)
+  uint32_t lmask, lval; // all local controls (shared-memory phase)
+  uint32_t tmask, tval; // local controls held by the thread index (register phase)
   uint64_t xmask, xval;
   uint32_t coef;        // pool offset, or table row when `table`
   uint32_t gen;         // pool offset of the generator (d x d dense, or d diagonal entries)
   uint32_t gidx;        // index of the parameterised gate (gradient scratch row)
-  uint32_t pad;
+  uint32_t flags;       // OPF_* flags
 };
-static_assert(sizeof(BOp) == 56, "BOp layout");
+static_assert(sizeof(BOp) == 64, "BOp layout");
 
-constexpr int kBatchOps = 128;
+constexpr int kBatchOps = 96;
 constexpr int kBatchGacc = 64;   // gradient accumulators per program
 constexpr int kTableStride = 16; // complex entries per (gate, state) table row
 
 struct BatchHeader {
   int32_t n, m, L, nops;
-  int32_t batch, ngacc, ngrad_total, pad;
+  int32_t batch, ngacc, ngrad_total, nphases;
   int8_t tq[16];
 };
 
 template <typename R>
 struct BatchProgram {
-  static constexpr int kPool =
-      (kProgramBytes - (int)sizeof(BatchHeader) - kBatchOps * (int)sizeof(BOp)) / (int)sizeof(Cx<R>);
+  static constexpr int kPool = (kProgramBytes - (int)sizeof(BatchHeader) - kBatchOps * (int)sizeof(BOp) -
+                                kMaxPhases * (int)sizeof(Phase)) /
+                               (int)sizeof(Cx<R>);
   BatchHeader h;
   BOp ops[kBatchOps];
+  Phase ph[kMaxPhases];
   Cx<R> pool[kPool];
 };
 

@@ -173,17 +173,6 @@ __device__ __forceinline__ void r_sign(Cx<R> (&v)[NR], uint32_t rmask, uint32_t 
   }
 }
 
-// The register combinations j (bit j of the result) whose slots in rmask
-// hold rval: an AND of the per-slot patterns 0xAAAA, 0xCCCC, 0xF0F0, 0xFF00.
-__device__ __forceinline__ uint32_t sign_pattern(uint32_t rmask, uint32_t rval) {
-  uint32_t p = 0xFFFFu;
-  if (rmask & 1u) p &= (rval & 1u) ? 0xAAAAu : 0x5555u;
-  if (rmask & 2u) p &= (rval & 2u) ? 0xCCCCu : 0x3333u;
-  if (rmask & 4u) p &= (rval & 4u) ? 0xF0F0u : 0x0F0Fu;
-  if (rmask & 8u) p &= (rval & 8u) ? 0xFF00u : 0x00FFu;
-  return p;
-}
-
 template <typename R>
 __device__ __forceinline__ void apply_neg(Cx<R> (&v)[NR], uint32_t neg) {
 #pragma unroll
@@ -231,14 +220,35 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[NR], const DevOp& op, const Cx
   }
 }
 
+// Uncontrolled 2x2 complex matrix on register slot S.
+template <typename R, int S>
+__device__ __forceinline__ void r_u1(Cx<R> (&v)[NR], const Cx<R>* cf) {
+  const Cx<R> u00 = cf[0], u01 = cf[1], u10 = cf[2], u11 = cf[3];
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> a = v[j], b = v[j1];
+    v[j] = cfma(u01, b, cmul(u00, a));
+    v[j1] = cfma(u11, b, cmul(u10, a));
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void apply_reg(Cx<R> (&v)[NR], const DevOp& op, const Cx<R>* pool, uint32_t tb,
                                           uint64_t base) {
-  if ((base & op.xmask) != op.xval) return;  // same for the whole block
-  if ((tb & op.tmask) != op.tval) return;    // same for the thread's 16 amplitudes
+  const uint32_t fl = op.pad;
+  if ((fl & OPF_XCOND) && (base & op.xmask) != op.xval) return;  // same for the whole block
+  if ((fl & OPF_TCOND) && (tb & op.tmask) != op.tval) return;    // same for the thread's 16 amplitudes
   const Cx<R>* cf = pool + op.coef;
   const uint32_t rm = op.rmask, rv = op.rval;
   switch (op.kind) {
+    case OPK_KRON:  // one-qubit gates on distinct slots commute: apply each present block
+      if (rm & 1u) r_u1<R, 0>(v, cf);
+      if (rm & 2u) r_u1<R, 1>(v, cf + 4);
+      if (rm & 4u) r_u1<R, 2>(v, cf + 8);
+      if (rm & 8u) r_u1<R, 3>(v, cf + 12);
+      break;
     case OPK_DENSE:
     case OPK_REAL:
       if (op.k == 1) {
@@ -261,7 +271,7 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[NR], const DevOp& op, const
       }
       break;
     case OPK_ANTIDIAG: {
-      const bool flip = op.pad != 0;  // pure bit flip (X, CNOT): no multiplies
+      const bool flip = (fl & OPF_FLIP) != 0;  // pure bit flip (X, CNOT): no multiplies
       switch (op.rs[0]) {
         case 0: r_anti1<R, 0>(v, cf, rm, rv, flip); break;
         case 1: r_anti1<R, 1>(v, cf, rm, rv, flip); break;
@@ -423,8 +433,8 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, i
         uint32_t neg = 0;
         for (int o = ph.first; o < ph.first + ph.nops; o++) {
           const DevOp& op = P.ops[o];
-          if (op.kind == OPK_SIGN) {
-            if ((base & op.xmask) == op.xval && (tb & op.tmask) == op.tval) neg ^= sign_pattern(op.rmask, op.rval);
+          if (op.kind == OPK_SIGN) {  // coef holds the precomputed pattern
+            if ((base & op.xmask) == op.xval && (tb & op.tmask) == op.tval) neg ^= op.coef;
             continue;
           }
           if (neg) {
@@ -460,40 +470,74 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, i
   }
 }
 
-// One pass over the state: gather each tile, run the program, scatter back.
+// Asynchronous 16-byte global -> shared copy (completes at cp_async_wait).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+#ifndef SV_SWEEP_MIN_BLOCKS
+#define SV_SWEEP_MIN_BLOCKS 3  // complex64 occupancy hint (resident CTAs per SM)
+#endif
+
+// One pass over the state.  Each CTA walks its tiles with two shared-memory
+// buffers: while it runs the program on tile t, the copies of tile t + grid
+// are already in flight (cp.async), so the gather latency hides behind the
+// arithmetic.  Then it scatters the tile back with 16-byte stores.
 template <typename R, int KMAX>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? SV_SWEEP_MIN_BLOCKS : 1)
     k_sweep(Cx<R>* __restrict__ state, const __grid_constant__ SweepProgram<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
   const ProgramHeader& h = P.h;
   const int tsz = 1 << h.m;
+  Cx<R>* buf[2] = {reinterpret_cast<Cx<R>*>(smem_raw), reinterpret_cast<Cx<R>*>(smem_raw) + tsz};
   constexpr int A = 16 / sizeof(Cx<R>);  // amplitudes per 16-byte access
   const int nvec = tsz / A;
   const uint64_t ntiles = 1ull << (h.n - h.m);
   // global offset of every run of 2^L contiguous amplitudes of a tile (the
-  // same for all tiles), kept after the tile in shared memory
-  uint64_t* hi_off = reinterpret_cast<uint64_t*>(s + tsz);
+  // same for all tiles), kept after the two buffers
+  uint64_t* hi_off = reinterpret_cast<uint64_t*>(buf[1] + tsz);
   const int nhi = 1 << (h.m - h.L);
   for (int c = threadIdx.x; c < nhi; c += blockDim.x) hi_off[c] = local_offset((uint32_t)c << h.L, h);
   const uint32_t lowmask = (1u << h.L) - 1u;
   __syncthreads();
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  auto tile_base = [&](uint64_t tile) {
     uint64_t base = tile;
     for (int i = 0; i < h.m; i++) base = ins0_64(base, h.tq[i]);
+    return base;
+  };
+  auto gather = [&](Cx<R>* s, uint64_t base) {
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const uint32_t l = (uint32_t)(v * A);
-      *reinterpret_cast<uint4*>(s + phys<R>(l)) =
-          *reinterpret_cast<const uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask))));
+      cp_async16(s + phys<R>(l), state + (base + (hi_off[l >> h.L] | (l & lowmask))));
     }
-    __syncthreads();
+    cp_async_commit();
+  };
+  uint64_t tile = blockIdx.x;
+  if (tile < ntiles) gather(buf[0], tile_base(tile));
+  for (int cur = 0; tile < ntiles; tile += gridDim.x, cur ^= 1) {
+    const uint64_t base = tile_base(tile);
+    const uint64_t next = tile + gridDim.x;
+    if (next < ntiles) {
+      gather(buf[cur ^ 1], tile_base(next));
+      cp_async_wait<1>();  // this thread's copies of the current tile are done
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();       // ... and every thread's
+    Cx<R>* s = buf[cur];
     run_phases<R, KMAX>(P, s, tsz, base);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const uint32_t l = (uint32_t)(v * A);
       *reinterpret_cast<uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask)))) =
           *reinterpret_cast<const uint4*>(s + phys<R>(l));
     }
-    __syncthreads();
+    __syncthreads();       // the buffer is free for the copies two tiles ahead
   }
 }
 
@@ -555,7 +599,7 @@ int sweep_threads(int m) {
 
 template <typename R, int KMAX>
 static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
-  const int smem = ((int)sizeof(Cx<R>) << prog.h.m) + (8 << (prog.h.m - prog.h.L));
+  const int smem = ((int)sizeof(Cx<R>) << (prog.h.m + 1)) + (8 << (prog.h.m - prog.h.L));
   // raise the dynamic shared-memory limit to what this launch needs (per device)
   static int configured_bytes[64] = {0};
   int dev = 0;
