@@ -172,6 +172,7 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
       }
     }
     ph.ntpos = (uint8_t)nt;
+    ph.nrp = (uint8_t)k2;
     for (int o = first; o < first + nops; o++) {
       BOp& d = P.ops[o];
       for (int i = 0; i < d.k; i++)

@@ -213,11 +213,13 @@ namespace {
 // register slots form one register phase; dense k >= 3 blocks and wide
 // diagonals get a shared-memory phase of their own.
 template <typename R>
-void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
+void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq_override = 0) {
   std::memset(&P.h, 0, sizeof(P.h));
   P.h.n = plan.n;
   P.h.m = sw.m;
   P.h.L = sw.L;
+  const int rq = rq_override > 0 ? rq_override : reg_qubits_for(sw.m);
+  P.h.rq = rq;
   P.h.nops = (int)sw.ops.size();
   int loc[64];
   for (int q = 0; q < 64; q++) loc[q] = -1;
@@ -225,7 +227,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
     P.h.tq[i] = (int8_t)sw.tq[i];
     loc[sw.tq[i]] = i;
   }
-  const bool reg_ok = sw.m >= kRegQ && sw.m - kRegQ <= 8;
+  const bool reg_ok = sw.m >= rq && sw.m - rq <= 8;
   struct Tmp {
     DevOp d;
     std::vector<cplx> m;
@@ -308,8 +310,8 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
     // register slots: the needed positions, then local bit 0 (16-byte
     // shared-memory accesses), then the highest free positions
     uint32_t rp = need;
-    if (__builtin_popcount(rp) < kRegQ && !(rp & 1u)) rp |= 1u;
-    for (int q = sw.m - 1; q >= 0 && __builtin_popcount(rp) < kRegQ; q--) rp |= 1u << q;
+    if (__builtin_popcount(rp) < rq && !(rp & 1u)) rp |= 1u;
+    for (int q = sw.m - 1; q >= 0 && __builtin_popcount(rp) < rq; q--) rp |= 1u << q;
     int slot_of[32];
     int ns2 = 0, nt = 0;
     for (int q = 0; q < sw.m; q++) {
@@ -322,6 +324,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
       }
     }
     ph.ntpos = (uint8_t)nt;
+    ph.nrp = (uint8_t)ns2;
     for (int o = first; o < first + nops; o++) {
       Tmp& t = ts[o];
       DevOp& d = t.d;
@@ -365,7 +368,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
       add_phase(PH_SMEM, o, 1, 0);
       continue;
     }
-    if (cur_n && __builtin_popcount(cur_need | ts[o].need) <= kRegQ && cur_n < 255) {
+    if (cur_n && __builtin_popcount(cur_need | ts[o].need) <= rq && cur_n < 255) {
       cur_need |= ts[o].need;
       cur_n++;
     } else {
@@ -385,9 +388,9 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
   auto u1_free = [](const Tmp& t) {
     return (t.d.kind == OPK_DENSE || t.d.kind == OPK_REAL) && t.d.k == 1 && t.d.lmask == 0 && t.d.xmask == 0;
   };
-  auto pattern = [](uint32_t rmask, uint32_t rval) {
+  auto pattern = [rq](uint32_t rmask, uint32_t rval) {
     uint32_t p = 0;
-    for (int j = 0; j < 16; j++)
+    for (int j = 0; j < (1 << rq); j++)
       if (((uint32_t)j & rmask) == rval) p |= 1u << j;
     return p;
   };
@@ -407,8 +410,8 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P) {
           k.d.kind = OPK_KRON;
           k.smem = false;
           k.need = 0;
-          std::vector<cplx> mats(16, 0.0);
-          for (int s2 = 0; s2 < 4; s2++) mats[4 * s2] = mats[4 * s2 + 3] = 1.0;
+          std::vector<cplx> mats(4 * rq, 0.0);
+          for (int s2 = 0; s2 < rq; s2++) mats[4 * s2] = mats[4 * s2 + 3] = 1.0;
           uint32_t present = 0;
           for (; o < first + nops && u1_free(ts[o]); o++) {
             const int sl = ts[o].d.rs[0];
@@ -805,7 +808,7 @@ void run_batch_small(int nreq, sv_dtype dtype, const int* nq, const sv_gate* con
   for (int b = 0; b < nreq; b++) {
     hfirst[b] = (int)k;
     hnq[b] = nq[b];
-    for (const Sweep& sw : plans[b].sweeps) build_program<R>(plans[b], sw, hp[k++]);
+    for (const Sweep& sw : plans[b].sweeps) build_program<R>(plans[b], sw, hp[k++], kRegQ);
   }
   hfirst[nreq] = (int)k;
   char* dbuf = (char*)scratch_buffer(stream, "small_batch_programs", total);

@@ -44,7 +44,8 @@ constexpr uint8_t OPF_XCOND = 4;  // xmask/xval is not empty
 constexpr int kMaxTileQ = 14;  // 2^14 amplitudes: 128 KiB (c64) of shared memory
 constexpr int kMaxOps = 96;
 constexpr int kMaxPhases = 96;
-constexpr int kRegQ = 4;        // register qubits of a phase: 16 amplitudes per thread
+constexpr int kRegQ = 4;        // register qubits of a phase (default: 16 amplitudes per thread)
+constexpr int kMaxRegQ = 5;     // at most 32 amplitudes per thread
 constexpr int kProgramBytes = 32000;  // kernel parameter space is 32764 bytes
 
 // An op as the kernel sees it.  Positions are local tile bits (indices into
@@ -78,10 +79,9 @@ enum PhaseKind : uint8_t { PH_REG = 0, PH_SMEM = 1 };
 // applied group by group straight in shared memory (dense k >= 3 and wide
 // diagonals).
 struct Phase {
-  uint8_t kind, first, nops, ntpos;
-  uint8_t rp[kRegQ];
+  uint8_t kind, first, nops, ntpos, nrp;
+  uint8_t rp[kMaxRegQ];
   uint8_t tpos[kMaxTileQ];
-  uint8_t pad[2];
 };
 static_assert(sizeof(Phase) == 24, "Phase layout");
 
@@ -93,6 +93,7 @@ struct Cx {
 struct ProgramHeader {
   int32_t n, m, L, nops;
   int32_t ncoef, nphases;
+  int32_t rq, pad;  // register qubits of the register phases (4 or 5)
   int8_t tq[16];
 };
 
@@ -240,6 +241,7 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
 double op_cost(const LOp& op);
 int tile_qubits_for(sv_dtype dtype);
 int low_qubits_for(sv_dtype dtype);
+int reg_qubits_for(int m);  // register qubits of a tile of m qubits (4, or 5 for m >= 13)
 
 // ----------------------------------------------------------------- launches
 // (sv_sweep.cu / sv_reduce.cu).  All return cudaError_t of the launch.

@@ -37,7 +37,11 @@ int popc(uint64_t x) { return __builtin_popcountll(x); }
 
 }  // namespace
 
-int tile_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? 12 : 11; }  // 32 KiB tiles
+#ifndef SV_C64_TILE_Q
+#define SV_C64_TILE_Q 13  // 64 KiB tiles, five register qubits per phase
+#endif
+int tile_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? SV_C64_TILE_Q : 11; }
+int reg_qubits_for(int m) { return m >= 13 ? 5 : kRegQ; }
 int low_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? 5 : 4; }     // 256-byte runs
 
 void validate_gates(int n, const sv_gate* gates, size_t n_gates, size_t n_param_values) {

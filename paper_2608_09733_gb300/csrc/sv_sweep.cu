@@ -73,23 +73,17 @@ __device__ __forceinline__ uint64_t local_offset(uint32_t l, const ProgramHeader
 }
 
 // ---------------------------------------------------------------- register ops
+//
+// A register phase gives each thread NR = 2^RQ amplitudes that differ only on
+// the phase's RQ register tile qubits (RQ = 4 or 5).  Every op below is fully
+// unrolled over the NR registers; its register slots are template arguments
+// picked by a switch, so every register index is a compile-time constant.
 
-constexpr int NR = 1 << kRegQ;  // amplitudes per thread in a register phase
-
-template <typename R, int S>
-__device__ __forceinline__ void r_dense1(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_t rmask, uint32_t rval, bool real) {
+template <typename R, int RQ, int S>
+__device__ __forceinline__ void r_dense1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval,
+                                         bool real) {
+  constexpr int NR = 1 << RQ;
   const Cx<R> u00 = cf[0], u01 = cf[1], u10 = cf[2], u11 = cf[3];
-  if (rmask == 0 && !real) {  // the common case: no control among the register slots
-#pragma unroll
-    for (int j = 0; j < NR; j++) {
-      if (j & (1 << S)) continue;
-      const int j1 = j | (1 << S);
-      const Cx<R> a = v[j], b = v[j1];
-      v[j] = cfma(u01, b, cmul(u00, a));
-      v[j1] = cfma(u11, b, cmul(u10, a));
-    }
-    return;
-  }
   if (real) {
 #pragma unroll
     for (int j = 0; j < NR; j++) {
@@ -113,8 +107,25 @@ __device__ __forceinline__ void r_dense1(Cx<R> (&v)[NR], const Cx<R>* cf, uint32
   }
 }
 
-template <typename R, int S>
-__device__ __forceinline__ void r_anti1(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_t rmask, uint32_t rval, bool flip) {
+// Uncontrolled 2x2 complex matrix on register slot S.
+template <typename R, int RQ, int S>
+__device__ __forceinline__ void r_u1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf) {
+  constexpr int NR = 1 << RQ;
+  const Cx<R> u00 = cf[0], u01 = cf[1], u10 = cf[2], u11 = cf[3];
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> a = v[j], b = v[j1];
+    v[j] = cfma(u01, b, cmul(u00, a));
+    v[j1] = cfma(u11, b, cmul(u10, a));
+  }
+}
+
+template <typename R, int RQ, int S>
+__device__ __forceinline__ void r_anti1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval,
+                                        bool flip) {
+  constexpr int NR = 1 << RQ;
   const Cx<R> a01 = cf[0], a10 = cf[1];
 #pragma unroll
   for (int j = 0; j < NR; j++) {
@@ -132,8 +143,9 @@ __device__ __forceinline__ void r_anti1(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_
   }
 }
 
-template <typename R, int A, int B>
-__device__ __forceinline__ void r_dense2(Cx<R> (&v)[NR], const Cx<R>* cf, uint32_t rmask, uint32_t rval) {
+template <typename R, int RQ, int A, int B>
+__device__ __forceinline__ void r_dense2(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval) {
+  constexpr int NR = 1 << RQ;
 #pragma unroll
   for (int j = 0; j < NR; j++) {
     if (j & ((1 << A) | (1 << B))) continue;
@@ -151,8 +163,9 @@ __device__ __forceinline__ void r_dense2(Cx<R> (&v)[NR], const Cx<R>* cf, uint32
   }
 }
 
-template <typename R, int A, int B>
-__device__ __forceinline__ void r_swap(Cx<R> (&v)[NR], uint32_t rmask, uint32_t rval) {
+template <typename R, int RQ, int A, int B>
+__device__ __forceinline__ void r_swap(Cx<R> (&v)[1 << RQ], uint32_t rmask, uint32_t rval) {
+  constexpr int NR = 1 << RQ;
 #pragma unroll
   for (int j = 0; j < NR; j++) {
     if (j & ((1 << A) | (1 << B))) continue;
@@ -163,20 +176,10 @@ __device__ __forceinline__ void r_swap(Cx<R> (&v)[NR], uint32_t rmask, uint32_t 
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void r_sign(Cx<R> (&v)[NR], uint32_t rmask, uint32_t rval) {
+template <typename R, int RQ>
+__device__ __forceinline__ void apply_neg(Cx<R> (&v)[1 << RQ], uint32_t neg) {
 #pragma unroll
-  for (int j = 0; j < NR; j++) {
-    if ((j & rmask) != rval) continue;
-    v[j].re = -v[j].re;
-    v[j].im = -v[j].im;
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ void apply_neg(Cx<R> (&v)[NR], uint32_t neg) {
-#pragma unroll
-  for (int j = 0; j < NR; j++) {
+  for (int j = 0; j < (1 << RQ); j++) {
     if ((neg >> j) & 1u) {
       v[j].re = -v[j].re;
       v[j].im = -v[j].im;
@@ -186,8 +189,9 @@ __device__ __forceinline__ void apply_neg(Cx<R> (&v)[NR], uint32_t neg) {
 
 // Diagonal op with k <= 2 matrix bits, each held by a register slot, by the
 // thread index, or fixed for the tile.
-template <typename R>
-__device__ __forceinline__ void r_diag(Cx<R> (&v)[NR], const DevOp& op, const Cx<R>* cf, uint32_t tb, uint64_t base) {
+template <typename R, int RQ>
+__device__ __forceinline__ void r_diag(Cx<R> (&v)[1 << RQ], const DevOp& op, const Cx<R>* cf, uint32_t tb,
+                                       uint64_t base) {
   uint32_t dbase = 0;
   int s0 = -1, s1 = -1, b0 = 0, b1 = 0;
   for (int i = 0; i < op.k; i++) {
@@ -212,7 +216,7 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[NR], const DevOp& op, const Cx
   const int sh0 = s0 >= 0 ? s0 : 0, sh1 = s1 >= 0 ? s1 : 0;
   const uint32_t m0 = s0 >= 0 ? 1u : 0u, m1 = s1 >= 0 ? 1u : 0u;
 #pragma unroll
-  for (int j = 0; j < NR; j++) {
+  for (int j = 0; j < (1 << RQ); j++) {
     if ((j & op.rmask) != op.rval) continue;
     const uint32_t c0 = ((uint32_t)j >> sh0) & m0, c1 = ((uint32_t)j >> sh1) & m1;
     const Cx<R> f = c1 ? (c0 ? f3 : f2) : (c0 ? f1 : f0);
@@ -220,112 +224,104 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[NR], const DevOp& op, const Cx
   }
 }
 
-// Uncontrolled 2x2 complex matrix on register slot S.
-template <typename R, int S>
-__device__ __forceinline__ void r_u1(Cx<R> (&v)[NR], const Cx<R>* cf) {
-  const Cx<R> u00 = cf[0], u01 = cf[1], u10 = cf[2], u11 = cf[3];
-#pragma unroll
-  for (int j = 0; j < NR; j++) {
-    if (j & (1 << S)) continue;
-    const int j1 = j | (1 << S);
-    const Cx<R> a = v[j], b = v[j1];
-    v[j] = cfma(u01, b, cmul(u00, a));
-    v[j1] = cfma(u11, b, cmul(u10, a));
+#define SV_SLOT_CASES(F, ...)            \
+  switch (op.rs[0]) {                    \
+    case 0: F<R, RQ, 0>(__VA_ARGS__); break; \
+    case 1: F<R, RQ, 1>(__VA_ARGS__); break; \
+    case 2: F<R, RQ, 2>(__VA_ARGS__); break; \
+    case 3: F<R, RQ, 3>(__VA_ARGS__); break; \
+    default:                             \
+      if constexpr (RQ > 4) F<R, RQ, 4>(__VA_ARGS__); \
+      break;                             \
   }
-}
 
-template <typename R>
-__device__ __forceinline__ void apply_reg(Cx<R> (&v)[NR], const DevOp& op, const Cx<R>* pool, uint32_t tb,
+#define SV_PAIR_CASES(F, ...)                            \
+  switch (op.rs[0] * 8 + op.rs[1]) { /* rs[0] < rs[1] */ \
+    case 1: F<R, RQ, 0, 1>(__VA_ARGS__); break;          \
+    case 2: F<R, RQ, 0, 2>(__VA_ARGS__); break;          \
+    case 3: F<R, RQ, 0, 3>(__VA_ARGS__); break;          \
+    case 10: F<R, RQ, 1, 2>(__VA_ARGS__); break;         \
+    case 11: F<R, RQ, 1, 3>(__VA_ARGS__); break;         \
+    case 19: F<R, RQ, 2, 3>(__VA_ARGS__); break;         \
+    case 4: if constexpr (RQ > 4) F<R, RQ, 0, 4>(__VA_ARGS__); break;  \
+    case 12: if constexpr (RQ > 4) F<R, RQ, 1, 4>(__VA_ARGS__); break; \
+    case 20: if constexpr (RQ > 4) F<R, RQ, 2, 4>(__VA_ARGS__); break; \
+    default: if constexpr (RQ > 4) F<R, RQ, 3, 4>(__VA_ARGS__); break; \
+  }
+
+template <typename R, int RQ>
+__device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, const Cx<R>* pool, uint32_t tb,
                                           uint64_t base) {
   const uint32_t fl = op.pad;
   if ((fl & OPF_XCOND) && (base & op.xmask) != op.xval) return;  // same for the whole block
-  if ((fl & OPF_TCOND) && (tb & op.tmask) != op.tval) return;    // same for the thread's 16 amplitudes
+  if ((fl & OPF_TCOND) && (tb & op.tmask) != op.tval) return;    // same for the thread's amplitudes
   const Cx<R>* cf = pool + op.coef;
   const uint32_t rm = op.rmask, rv = op.rval;
   switch (op.kind) {
     case OPK_KRON:  // one-qubit gates on distinct slots commute: apply each present block
-      if (rm & 1u) r_u1<R, 0>(v, cf);
-      if (rm & 2u) r_u1<R, 1>(v, cf + 4);
-      if (rm & 4u) r_u1<R, 2>(v, cf + 8);
-      if (rm & 8u) r_u1<R, 3>(v, cf + 12);
+      if (rm & 1u) r_u1<R, RQ, 0>(v, cf);
+      if (rm & 2u) r_u1<R, RQ, 1>(v, cf + 4);
+      if (rm & 4u) r_u1<R, RQ, 2>(v, cf + 8);
+      if (rm & 8u) r_u1<R, RQ, 3>(v, cf + 12);
+      if constexpr (RQ > 4)
+        if (rm & 16u) r_u1<R, RQ, 4>(v, cf + 16);
       break;
     case OPK_DENSE:
     case OPK_REAL:
       if (op.k == 1) {
         const bool real = op.kind == OPK_REAL;
-        switch (op.rs[0]) {
-          case 0: r_dense1<R, 0>(v, cf, rm, rv, real); break;
-          case 1: r_dense1<R, 1>(v, cf, rm, rv, real); break;
-          case 2: r_dense1<R, 2>(v, cf, rm, rv, real); break;
-          default: r_dense1<R, 3>(v, cf, rm, rv, real); break;
-        }
+        SV_SLOT_CASES(r_dense1, v, cf, rm, rv, real)
       } else {
-        switch (op.rs[0] * 4 + op.rs[1]) {  // the host orders rs[0] < rs[1]
-          case 1: r_dense2<R, 0, 1>(v, cf, rm, rv); break;
-          case 2: r_dense2<R, 0, 2>(v, cf, rm, rv); break;
-          case 3: r_dense2<R, 0, 3>(v, cf, rm, rv); break;
-          case 6: r_dense2<R, 1, 2>(v, cf, rm, rv); break;
-          case 7: r_dense2<R, 1, 3>(v, cf, rm, rv); break;
-          default: r_dense2<R, 2, 3>(v, cf, rm, rv); break;
-        }
+        SV_PAIR_CASES(r_dense2, v, cf, rm, rv)
       }
       break;
     case OPK_ANTIDIAG: {
       const bool flip = (fl & OPF_FLIP) != 0;  // pure bit flip (X, CNOT): no multiplies
-      switch (op.rs[0]) {
-        case 0: r_anti1<R, 0>(v, cf, rm, rv, flip); break;
-        case 1: r_anti1<R, 1>(v, cf, rm, rv, flip); break;
-        case 2: r_anti1<R, 2>(v, cf, rm, rv, flip); break;
-        default: r_anti1<R, 3>(v, cf, rm, rv, flip); break;
-      }
+      SV_SLOT_CASES(r_anti1, v, cf, rm, rv, flip)
       break;
     }
-    case OPK_SWAP:
-      switch (op.rs[0] * 4 + op.rs[1]) {
-        case 1: r_swap<R, 0, 1>(v, rm, rv); break;
-        case 2: r_swap<R, 0, 2>(v, rm, rv); break;
-        case 3: r_swap<R, 0, 3>(v, rm, rv); break;
-        case 6: r_swap<R, 1, 2>(v, rm, rv); break;
-        case 7: r_swap<R, 1, 3>(v, rm, rv); break;
-        default: r_swap<R, 2, 3>(v, rm, rv); break;
-      }
-      break;
-    case OPK_DIAG: r_diag<R>(v, op, cf, tb, base); break;
-    case OPK_SIGN: r_sign<R>(v, rm, rv); break;
+    case OPK_SWAP: SV_PAIR_CASES(r_swap, v, rm, rv) break;
+    case OPK_DIAG: r_diag<R, RQ>(v, op, cf, tb, base); break;
     default: break;
   }
 }
 
 // The local bits of register slot combination j (masks m[] = 1 << rp[]).
-__device__ __forceinline__ uint32_t reg_bits(int j, const uint32_t (&m)[kRegQ]) {
-  return ((j & 1) ? m[0] : 0u) | ((j & 2) ? m[1] : 0u) | ((j & 4) ? m[2] : 0u) | ((j & 8) ? m[3] : 0u);
+template <int RQ>
+__device__ __forceinline__ uint32_t reg_bits(int j, const uint32_t (&m)[RQ]) {
+  uint32_t b = 0;
+#pragma unroll
+  for (int i = 0; i < RQ; i++)
+    if ((j >> i) & 1) b |= m[i];
+  return b;
 }
 
-template <typename R>
-__device__ __forceinline__ void reg_load(Cx<R> (&v)[NR], const Cx<R>* s, uint32_t tb, const uint32_t (&m)[kRegQ]) {
+template <typename R, int RQ>
+__device__ __forceinline__ void reg_load(Cx<R> (&v)[1 << RQ], const Cx<R>* s, uint32_t tb, const uint32_t (&m)[RQ]) {
   if (sizeof(Cx<R>) == 8 && m[0] == 1u) {  // pairs (j, j+1) share a 16-byte granule
 #pragma unroll
-    for (int j = 0; j < NR; j += 2) {
-      const float4 w = *reinterpret_cast<const float4*>(s + phys<R>(tb | reg_bits(j, m)));
+    for (int j = 0; j < (1 << RQ); j += 2) {
+      const float4 w = *reinterpret_cast<const float4*>(s + phys<R>(tb | reg_bits<RQ>(j, m)));
       v[j] = Cx<R>{(R)w.x, (R)w.y};
       v[j + 1] = Cx<R>{(R)w.z, (R)w.w};
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < NR; j++) v[j] = s[phys<R>(tb | reg_bits(j, m))];
+    for (int j = 0; j < (1 << RQ); j++) v[j] = s[phys<R>(tb | reg_bits<RQ>(j, m))];
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void reg_store(const Cx<R> (&v)[NR], Cx<R>* s, uint32_t tb, const uint32_t (&m)[kRegQ]) {
+template <typename R, int RQ>
+__device__ __forceinline__ void reg_store(const Cx<R> (&v)[1 << RQ], Cx<R>* s, uint32_t tb,
+                                          const uint32_t (&m)[RQ]) {
   if (sizeof(Cx<R>) == 8 && m[0] == 1u) {
 #pragma unroll
-    for (int j = 0; j < NR; j += 2)
-      *reinterpret_cast<float4*>(s + phys<R>(tb | reg_bits(j, m))) =
+    for (int j = 0; j < (1 << RQ); j += 2)
+      *reinterpret_cast<float4*>(s + phys<R>(tb | reg_bits<RQ>(j, m))) =
           make_float4((float)v[j].re, (float)v[j].im, (float)v[j + 1].re, (float)v[j + 1].im);
   } else {
 #pragma unroll
-    for (int j = 0; j < NR; j++) s[phys<R>(tb | reg_bits(j, m))] = v[j];
+    for (int j = 0; j < (1 << RQ); j++) s[phys<R>(tb | reg_bits<RQ>(j, m))] = v[j];
   }
 }
 
@@ -414,8 +410,9 @@ __device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const
 // ---------------------------------------------------------------- kernels
 
 // Runs every phase of a program on a tile that is already in shared memory.
-// KMAX: widest dense operation the program runs in shared memory.
-template <typename R, int KMAX>
+// KMAX: widest dense operation the program runs in shared memory; RQ: the
+// register qubits of its register phases.
+template <typename R, int KMAX, int RQ>
 __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, int tsz, uint64_t base) {
   const ProgramHeader& h = P.h;
   for (int p = 0; p < h.nphases; p++) {
@@ -425,9 +422,11 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, i
         uint32_t tb = 0;
         for (int i = 0; i < ph.ntpos; i++)
           if ((threadIdx.x >> i) & 1u) tb |= 1u << ph.tpos[i];
-        const uint32_t m[kRegQ] = {1u << ph.rp[0], 1u << ph.rp[1], 1u << ph.rp[2], 1u << ph.rp[3]};
-        Cx<R> v[NR];
-        reg_load<R>(v, s, tb, m);
+        uint32_t m[RQ];
+#pragma unroll
+        for (int i = 0; i < RQ; i++) m[i] = 1u << ph.rp[i];
+        Cx<R> v[1 << RQ];
+        reg_load<R, RQ>(v, s, tb, m);
         // Sign flips commute with each other: a run of them becomes one mask of
         // the thread's amplitudes to negate, applied before the next other op.
         uint32_t neg = 0;
@@ -438,13 +437,13 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, Cx<R>* s, i
             continue;
           }
           if (neg) {
-            apply_neg<R>(v, neg);
+            apply_neg<R, RQ>(v, neg);
             neg = 0;
           }
-          apply_reg<R>(v, op, P.coef, tb, base);
+          apply_reg<R, RQ>(v, op, P.coef, tb, base);
         }
-        if (neg) apply_neg<R>(v, neg);
-        reg_store<R>(v, s, tb, m);
+        if (neg) apply_neg<R, RQ>(v, neg);
+        reg_store<R, RQ>(v, s, tb, m);
       }
     } else {
       const DevOp& op = P.ops[ph.first];
@@ -485,22 +484,24 @@ __device__ __forceinline__ void cp_async_wait() {
 #define SV_SWEEP_MIN_BLOCKS 3  // complex64 occupancy hint (resident CTAs per SM)
 #endif
 
-// One pass over the state.  Each CTA walks its tiles with two shared-memory
-// buffers: while it runs the program on tile t, the copies of tile t + grid
-// are already in flight (cp.async), so the gather latency hides behind the
-// arithmetic.  Then it scatters the tile back with 16-byte stores.
-template <typename R, int KMAX>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? SV_SWEEP_MIN_BLOCKS : 1)
+// One pass over the state.  With DBUF each CTA walks its tiles with two
+// shared-memory buffers: while it runs the program on tile t, the copies of
+// tile t + grid are already in flight (cp.async), so the gather latency hides
+// behind the arithmetic.  Without DBUF (tiles too large for two buffers) the
+// copies of a tile are waited for before it runs.  Each tile is scattered back
+// with 16-byte stores.
+template <typename R, int KMAX, int RQ, bool DBUF>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (DBUF ? SV_SWEEP_MIN_BLOCKS : 2) : 1)
     k_sweep(Cx<R>* __restrict__ state, const __grid_constant__ SweepProgram<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ProgramHeader& h = P.h;
   const int tsz = 1 << h.m;
-  Cx<R>* buf[2] = {reinterpret_cast<Cx<R>*>(smem_raw), reinterpret_cast<Cx<R>*>(smem_raw) + tsz};
+  Cx<R>* buf[2] = {reinterpret_cast<Cx<R>*>(smem_raw), reinterpret_cast<Cx<R>*>(smem_raw) + (DBUF ? tsz : 0)};
   constexpr int A = 16 / sizeof(Cx<R>);  // amplitudes per 16-byte access
   const int nvec = tsz / A;
   const uint64_t ntiles = 1ull << (h.n - h.m);
   // global offset of every run of 2^L contiguous amplitudes of a tile (the
-  // same for all tiles), kept after the two buffers
+  // same for all tiles), kept after the buffers
   uint64_t* hi_off = reinterpret_cast<uint64_t*>(buf[1] + tsz);
   const int nhi = 1 << (h.m - h.L);
   for (int c = threadIdx.x; c < nhi; c += blockDim.x) hi_off[c] = local_offset((uint32_t)c << h.L, h);
@@ -519,25 +520,30 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? SV_SWEEP_MIN_BLOCKS : 1)
     cp_async_commit();
   };
   uint64_t tile = blockIdx.x;
-  if (tile < ntiles) gather(buf[0], tile_base(tile));
-  for (int cur = 0; tile < ntiles; tile += gridDim.x, cur ^= 1) {
+  if (DBUF && tile < ntiles) gather(buf[0], tile_base(tile));
+  for (int cur = 0; tile < ntiles; tile += gridDim.x, cur ^= (DBUF ? 1 : 0)) {
     const uint64_t base = tile_base(tile);
-    const uint64_t next = tile + gridDim.x;
-    if (next < ntiles) {
-      gather(buf[cur ^ 1], tile_base(next));
-      cp_async_wait<1>();  // this thread's copies of the current tile are done
+    if constexpr (DBUF) {
+      const uint64_t next = tile + gridDim.x;
+      if (next < ntiles) {
+        gather(buf[cur ^ 1], tile_base(next));
+        cp_async_wait<1>();  // this thread's copies of the current tile are done
+      } else {
+        cp_async_wait<0>();
+      }
     } else {
+      gather(buf[0], base);
       cp_async_wait<0>();
     }
-    __syncthreads();       // ... and every thread's
+    __syncthreads();  // ... and every thread's
     Cx<R>* s = buf[cur];
-    run_phases<R, KMAX>(P, s, tsz, base);
+    run_phases<R, KMAX, RQ>(P, s, tsz, base);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const uint32_t l = (uint32_t)(v * A);
       *reinterpret_cast<uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask)))) =
           *reinterpret_cast<const uint4*>(s + phys<R>(l));
     }
-    __syncthreads();       // the buffer is free for the copies two tiles ahead
+    __syncthreads();  // the buffer is free for the next copies
   }
 }
 
@@ -557,7 +563,7 @@ __global__ void __launch_bounds__(256) k_small_batch(const SweepProgram<R>* __re
   const int tsz = 1 << n;
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) s[phys<R>(a)] = Cx<R>{R(a == 0 ? 1 : 0), R(0)};
   __syncthreads();
-  for (int p = first_prog[b]; p < first_prog[b + 1]; p++) run_phases<R, 5>(progs[p], s, tsz, 0ull);
+  for (int p = first_prog[b]; p < first_prog[b + 1]; p++) run_phases<R, 5, kRegQ>(progs[p], s, tsz, 0ull);
   double acc = 0.0;
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
     const Cx<R> x = s[phys<R>(a)];
@@ -591,38 +597,39 @@ int device_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-int sweep_threads(int m) {
-  // one thread per register group of 16 amplitudes; at least one warp
-  int t = m > kRegQ + 5 ? (1 << (m - kRegQ)) : 32;
+int sweep_threads(int m, int rq) {
+  // one thread per register group of 2^rq amplitudes; at least one warp
+  int t = m - rq >= 5 ? (1 << (m - rq)) : 32;
   return t > 256 ? 256 : t;
 }
 
-template <typename R, int KMAX>
+template <typename R, int KMAX, int RQ, bool DBUF>
 static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
-  const int smem = ((int)sizeof(Cx<R>) << (prog.h.m + 1)) + (8 << (prog.h.m - prog.h.L));
+  const int smem = ((int)sizeof(Cx<R>) << (prog.h.m + (DBUF ? 1 : 0))) + (8 << (prog.h.m - prog.h.L));
   // raise the dynamic shared-memory limit to what this launch needs (per device)
   static int configured_bytes[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (smem > 48 * 1024 && smem > configured_bytes[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_sweep<R, KMAX, RQ, DBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured_bytes[dev] = smem;
   }
-  const int threads = sweep_threads(prog.h.m);
+  const int threads = sweep_threads(prog.h.m, RQ);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX>, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX, RQ, DBUF>, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
   uint64_t grid = (uint64_t)device_sm_count() * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_sweep<R, KMAX><<<(unsigned)grid, threads, smem, stream>>>(state, prog);
+  k_sweep<R, KMAX, RQ, DBUF><<<(unsigned)grid, threads, smem, stream>>>(state, prog);
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
+template <typename R, int RQ, bool DBUF>
+static cudaError_t launch_sweep_rq(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
   int kmax = 1;
   for (int p = 0; p < prog.h.nphases; p++) {
     const Phase& ph = prog.ph[p];
@@ -630,9 +637,16 @@ cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t
     const DevOp& op = prog.ops[ph.first];
     if ((op.kind == OPK_DENSE || op.kind == OPK_REAL) && op.k > kmax) kmax = op.k;
   }
-  if (kmax <= 2) return launch_sweep_k<R, 2>(state, prog, stream);
-  if (kmax == 3) return launch_sweep_k<R, 3>(state, prog, stream);
-  return launch_sweep_k<R, 5>(state, prog, stream);
+  if (kmax <= 2) return launch_sweep_k<R, 2, RQ, DBUF>(state, prog, stream);
+  if (kmax == 3) return launch_sweep_k<R, 3, RQ, DBUF>(state, prog, stream);
+  return launch_sweep_k<R, 5, RQ, DBUF>(state, prog, stream);
+}
+
+template <typename R>
+cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
+  // four register qubits with two tile buffers, or five with one (large tiles)
+  if (prog.h.rq == 5) return launch_sweep_rq<R, 5, false>(state, prog, stream);
+  return launch_sweep_rq<R, 4, true>(state, prog, stream);
 }
 
 template <typename R>
