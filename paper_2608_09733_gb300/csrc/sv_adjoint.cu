@@ -442,6 +442,9 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
   Cx<R>* sp = reinterpret_cast<Cx<R>*>(smem_raw);
   Cx<R>* sl = sp + (REV ? tsz : 0);
   uint64_t* hi_off = reinterpret_cast<uint64_t*>(sp + (REV ? 2 * tsz : tsz));
+  // this state's coefficients (table rows and constant matrices) and the
+  // generators, copied once per CTA
+  Cx<R>* scoef = reinterpret_cast<Cx<R>*>(hi_off + (1 << (h.m - h.L)));
   __shared__ double gacc[kBatchGacc][8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kBatchGacc * 8; i += blockDim.x) gacc[i / 8][i % 8] = 0.0;
@@ -453,6 +456,14 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
   const uint64_t ntiles = 1ull << (h.n - h.m);
   const int nhi = 1 << (h.m - h.L);
   for (int c = threadIdx.x; c < nhi; c += blockDim.x) hi_off[c] = local_offset((uint32_t)c << h.L, h);
+  for (int o = warp; o < h.nops; o += (int)(blockDim.x >> 5)) {
+    const BOp& op = P.ops[o];
+    const int dd = 1 << op.k;
+    const int mc = op.kind == OPK_DIAG ? dd : op.kind == OPK_ANTIDIAG ? 2 : op.kind == OPK_SWAP ? 0 : dd * dd;
+    const int gc = op.grad ? (op.kind == OPK_DIAG ? dd : dd * dd) : 0;
+    const Cx<R>* src = op.table ? table + ((uint64_t)op.coef * h.batch + bidx) * kTableStride : P.pool + op.coef;
+    for (int e = lane; e < mc + gc; e += 32) scoef[op.soff + e] = e < mc ? src[e] : P.pool[op.gen + (e - mc)];
+  }
   const uint32_t lowmask = (1u << h.L) - 1u;
   __syncthreads();
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -487,9 +498,10 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
             const BOp& op = P.ops[o];
             R acc = R(0);
             if (active && (base & op.xmask) == op.xval && (tb & op.tmask) == op.tval) {
-              const Cx<R>* M =
-                  op.table ? table + ((uint64_t)op.coef * h.batch + bidx) * kTableStride : P.pool + op.coef;
-              b_apply<R, REV>(p, l, op, M, P.pool + op.gen, tb, base, acc);
+              const Cx<R>* M = scoef + op.soff;
+              const int dd = 1 << op.k;
+              const Cx<R>* G = M + (op.kind == OPK_DIAG ? dd : dd * dd);
+              b_apply<R, REV>(p, l, op, M, G, tb, base, acc);
             }
             if (REV && op.grad) {  // warp sum in the state's precision, then double
               R w = acc;
@@ -512,8 +524,9 @@ __global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx
         // in shared memory, through the same swizzle
         const BOp& op = P.ops[ph.first];
         if ((base & op.xmask) == op.xval) {
-          const Cx<R>* M = op.table ? table + ((uint64_t)op.coef * h.batch + bidx) * kTableStride : P.pool + op.coef;
-          const Cx<R>* G = P.pool + op.gen;
+          const Cx<R>* M = scoef + op.soff;
+          const int dd = 1 << op.k;
+          const Cx<R>* G = M + (op.kind == OPK_DIAG ? dd : dd * dd);
           R acc = R(0);
           switch (op.kind) {
             case OPK_DENSE:
@@ -654,7 +667,8 @@ int batch_grid_x(int n, int m, int batch) {
 template <typename R>
 cudaError_t launch_batch_sweep(Cx<R>* psi, Cx<R>* lam, const Cx<R>* table, double* gscratch, int grid_x,
                                const BatchProgram<R>& prog, bool reverse, cudaStream_t stream) {
-  const int smem = ((int)sizeof(Cx<R>) << prog.h.m << (reverse ? 1 : 0)) + (8 << (prog.h.m - prog.h.L));
+  const int smem = ((int)sizeof(Cx<R>) << prog.h.m << (reverse ? 1 : 0)) + (8 << (prog.h.m - prog.h.L)) +
+                   (int)sizeof(Cx<R>) * prog.h.scoef;
   static int configured[2][64] = {{0}};
   int dev = 0;
   cudaGetDevice(&dev);

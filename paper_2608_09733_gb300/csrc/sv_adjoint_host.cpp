@@ -145,6 +145,17 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
   }
   P.h.nops = (int)sw.ops.size();
   P.h.ngacc = nacc;
+  // offsets of each op's matrix and generator in the CTA's shared copy
+  int soff = 0;
+  for (int o = 0; o < P.h.nops; o++) {
+    BOp& d = P.ops[o];
+    const int dd = 1 << d.k;
+    const int mc = d.kind == OPK_DIAG ? dd : d.kind == OPK_ANTIDIAG ? 2 : d.kind == OPK_SWAP ? 0 : dd * dd;
+    const int gc = d.grad ? (d.kind == OPK_DIAG ? dd : dd * dd) : 0;
+    d.soff = (uint16_t)soff;
+    soff += mc + gc;
+  }
+  P.h.scoef = soff;
 
   // phases: consecutive ops whose moving qubits fit four register slots; tiles
   // of fewer than four qubits run every op in shared memory
@@ -279,7 +290,10 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   // ---- device buffers (library-owned, per stream, grow-only)
   const int c = ckpt > 0 ? ckpt : (int)ng + 1;
   const int nck = ng > 0 ? (int)((ng - 1) / c) : 0;  // stored states after c, 2c, ... gates
-  const int tile_q = tile_qubits_for(dtype), low_q = low_qubits_for(dtype);
+  // 2^12 (complex64) or 2^11 (complex128) amplitudes per tile: psi and lambda
+  // tiles fit shared memory twice over, and the register phases hold 16
+  // amplitudes per thread with 256 threads
+  const int tile_q = dtype == SV_C64 ? 12 : 11, low_q = low_qubits_for(dtype);
   const int m = std::min(n, tile_q);
   const int grid_x = batch_grid_x(n, m, batch);
   Cx<R>* psi = (Cx<R>*)scratch_buffer(stream, "adj_psi", sbytes);

@@ -136,7 +136,8 @@ struct BOp {
   uint32_t coef;        // pool offset, or table row when `table`
   uint32_t gen;         // pool offset of the generator (d x d dense, or d diagonal entries)
   uint32_t gidx;        // index of the parameterised gate (gradient scratch row)
-  uint32_t flags;       // OPF_* flags
+  uint16_t flags;       // OPF_* flags
+  uint16_t soff;        // offset of the op's matrix (then its generator) in the CTA's shared copy
 };
 static_assert(sizeof(BOp) == 64, "BOp layout");
 
@@ -147,6 +148,7 @@ constexpr int kTableStride = 16; // complex entries per (gate, state) table row
 struct BatchHeader {
   int32_t n, m, L, nops;
   int32_t batch, ngacc, ngrad_total, nphases;
+  int32_t scoef, pad;  // complex entries of the shared coefficient copy
   int8_t tq[16];
 };
 

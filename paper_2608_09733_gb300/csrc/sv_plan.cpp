@@ -41,7 +41,10 @@ int popc(uint64_t x) { return __builtin_popcountll(x); }
 #define SV_C64_TILE_Q 13  // 64 KiB tiles, five register qubits per phase
 #endif
 int tile_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? SV_C64_TILE_Q : 11; }
-int reg_qubits_for(int m) { return m >= 13 ? 5 : kRegQ; }
+#ifndef SV_RQ5_MIN_M
+#define SV_RQ5_MIN_M 13  // tiles of at least this many qubits use five register qubits
+#endif
+int reg_qubits_for(int m) { return m >= SV_RQ5_MIN_M ? 5 : kRegQ; }
 int low_qubits_for(sv_dtype dtype) { return dtype == SV_C64 ? 5 : 4; }     // 256-byte runs
 
 void validate_gates(int n, const sv_gate* gates, size_t n_gates, size_t n_param_values) {

@@ -481,7 +481,18 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 #ifndef SV_SWEEP_MIN_BLOCKS
-#define SV_SWEEP_MIN_BLOCKS 3  // complex64 occupancy hint (resident CTAs per SM)
+#define SV_SWEEP_MIN_BLOCKS 3  // complex64, four register qubits: resident CTAs per SM
+#endif
+// Launch shape of the five-register-qubit (32 amplitudes per thread) passes:
+// largest block, resident CTAs per SM hint, and whether tiles are double-buffered.
+#ifndef SV_RQ5_MAXT
+#define SV_RQ5_MAXT 256
+#endif
+#ifndef SV_RQ5_MINB
+#define SV_RQ5_MINB 2
+#endif
+#ifndef SV_RQ5_DBUF
+#define SV_RQ5_DBUF false
 #endif
 
 // One pass over the state.  With DBUF each CTA walks its tiles with two
@@ -491,7 +502,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // copies of a tile are waited for before it runs.  Each tile is scattered back
 // with 16-byte stores.
 template <typename R, int KMAX, int RQ, bool DBUF>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (DBUF ? SV_SWEEP_MIN_BLOCKS : 2) : 1)
+__global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
+                                  sizeof(R) == 4 ? (RQ == 5 ? SV_RQ5_MINB : SV_SWEEP_MIN_BLOCKS) : 1)
     k_sweep(Cx<R>* __restrict__ state, const __grid_constant__ SweepProgram<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ProgramHeader& h = P.h;
@@ -645,7 +657,7 @@ static cudaError_t launch_sweep_rq(Cx<R>* state, const SweepProgram<R>& prog, cu
 template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
   // four register qubits with two tile buffers, or five with one (large tiles)
-  if (prog.h.rq == 5) return launch_sweep_rq<R, 5, false>(state, prog, stream);
+  if (prog.h.rq == 5) return launch_sweep_rq<R, 5, SV_RQ5_DBUF>(state, prog, stream);
   return launch_sweep_rq<R, 4, true>(state, prog, stream);
 }
 
