@@ -79,31 +79,28 @@ __device__ __forceinline__ uint64_t local_offset(uint32_t l, const ProgramHeader
 // unrolled over the NR registers; its register slots are template arguments
 // picked by a switch, so every register index is a compile-time constant.
 
-template <typename R, int RQ, int S>
-__device__ __forceinline__ void r_dense1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval,
-                                         bool real) {
+// Controlled (or real) 2x2 matrix on register slot S; the register-slot part
+// of the controls is a per-pair predicate applied with selects.
+template <typename R, int RQ, int S, bool REAL>
+__device__ __forceinline__ void r_dense1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval) {
   constexpr int NR = 1 << RQ;
   const Cx<R> u00 = cf[0], u01 = cf[1], u10 = cf[2], u11 = cf[3];
-  if (real) {
 #pragma unroll
-    for (int j = 0; j < NR; j++) {
-      if (j & (1 << S)) continue;
-      if ((j & rmask) != rval) continue;
-      const int j1 = j | (1 << S);
-      const Cx<R> a = v[j], b = v[j1];
-      v[j] = {fma(u00.re, a.re, u01.re * b.re), fma(u00.re, a.im, u01.re * b.im)};
-      v[j1] = {fma(u10.re, a.re, u11.re * b.re), fma(u10.re, a.im, u11.re * b.im)};
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    const int j1 = j | (1 << S);
+    const bool on = (j & rmask) == rval;
+    const Cx<R> a = v[j], b = v[j1];
+    Cx<R> o0, o1;
+    if (REAL) {
+      o0 = {fma(u00.re, a.re, u01.re * b.re), fma(u00.re, a.im, u01.re * b.im)};
+      o1 = {fma(u10.re, a.re, u11.re * b.re), fma(u10.re, a.im, u11.re * b.im)};
+    } else {
+      o0 = cfma(u01, b, cmul(u00, a));
+      o1 = cfma(u11, b, cmul(u10, a));
     }
-  } else {
-#pragma unroll
-    for (int j = 0; j < NR; j++) {
-      if (j & (1 << S)) continue;
-      if ((j & rmask) != rval) continue;
-      const int j1 = j | (1 << S);
-      const Cx<R> a = v[j], b = v[j1];
-      v[j] = cfma(u01, b, cmul(u00, a));
-      v[j1] = cfma(u11, b, cmul(u10, a));
-    }
+    v[j] = on ? o0 : a;
+    v[j1] = on ? o1 : b;
   }
 }
 
@@ -122,24 +119,25 @@ __device__ __forceinline__ void r_u1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf) {
   }
 }
 
-template <typename R, int RQ, int S>
-__device__ __forceinline__ void r_anti1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval,
-                                        bool flip) {
+// Anti-diagonal 2x2 on register slot S: a pure bit flip (X, CNOT) when FLIP,
+// else out0 = a01 v1, out1 = a10 v0 (Y ...); register-slot controls by select.
+template <typename R, int RQ, int S, bool FLIP>
+__device__ __forceinline__ void r_anti1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t rmask, uint32_t rval) {
   constexpr int NR = 1 << RQ;
-  const Cx<R> a01 = cf[0], a10 = cf[1];
+  Cx<R> a01 = {R(1), R(0)}, a10 = {R(1), R(0)};
+  if (!FLIP) {
+    a01 = cf[0];
+    a10 = cf[1];
+  }
 #pragma unroll
   for (int j = 0; j < NR; j++) {
     if (j & (1 << S)) continue;
-    if ((j & rmask) != rval) continue;
     const int j1 = j | (1 << S);
+    const bool on = (j & rmask) == rval;
     const Cx<R> a = v[j], b = v[j1];
-    if (flip) {
-      v[j] = b;
-      v[j1] = a;
-    } else {
-      v[j] = cmul(a01, b);
-      v[j1] = cmul(a10, a);
-    }
+    const Cx<R> o0 = FLIP ? b : cmul(a01, b), o1 = FLIP ? a : cmul(a10, a);
+    v[j] = on ? o0 : a;
+    v[j1] = on ? o1 : b;
   }
 }
 
@@ -224,15 +222,15 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[1 << RQ], const DevOp& op, con
   }
 }
 
-#define SV_SLOT_CASES(F, ...)            \
-  switch (op.rs[0]) {                    \
-    case 0: F<R, RQ, 0>(__VA_ARGS__); break; \
-    case 1: F<R, RQ, 1>(__VA_ARGS__); break; \
-    case 2: F<R, RQ, 2>(__VA_ARGS__); break; \
-    case 3: F<R, RQ, 3>(__VA_ARGS__); break; \
-    default:                             \
-      if constexpr (RQ > 4) F<R, RQ, 4>(__VA_ARGS__); \
-      break;                             \
+#define SV_SLOT_CASES(F, FL, ...)                        \
+  switch (op.rs[0]) {                                    \
+    case 0: F<R, RQ, 0, FL>(__VA_ARGS__); break;         \
+    case 1: F<R, RQ, 1, FL>(__VA_ARGS__); break;         \
+    case 2: F<R, RQ, 2, FL>(__VA_ARGS__); break;         \
+    case 3: F<R, RQ, 3, FL>(__VA_ARGS__); break;         \
+    default:                                             \
+      if constexpr (RQ > 4) F<R, RQ, 4, FL>(__VA_ARGS__); \
+      break;                                             \
   }
 
 #define SV_PAIR_CASES(F, ...)                            \
@@ -249,6 +247,15 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[1 << RQ], const DevOp& op, con
     default: if constexpr (RQ > 4) F<R, RQ, 3, 4>(__VA_ARGS__); break; \
   }
 
+#ifndef SV_KRON_FENCE_ON
+#define SV_KRON_FENCE_ON 1
+#endif
+#if SV_KRON_FENCE_ON
+#define SV_KRON_FENCE() asm volatile("" ::: "memory")
+#else
+#define SV_KRON_FENCE() ((void)0)
+#endif
+
 template <typename R, int RQ>
 __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, const Cx<R>* pool, uint32_t tb,
                                           uint64_t base) {
@@ -259,27 +266,38 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
   const uint32_t rm = op.rmask, rv = op.rval;
   switch (op.kind) {
     case OPK_KRON:  // one-qubit gates on distinct slots commute: apply each present block
+      // (the fences keep one block's coefficients live at a time)
       if (rm & 1u) r_u1<R, RQ, 0>(v, cf);
+      SV_KRON_FENCE();
       if (rm & 2u) r_u1<R, RQ, 1>(v, cf + 4);
+      SV_KRON_FENCE();
       if (rm & 4u) r_u1<R, RQ, 2>(v, cf + 8);
+      SV_KRON_FENCE();
       if (rm & 8u) r_u1<R, RQ, 3>(v, cf + 12);
-      if constexpr (RQ > 4)
+      if constexpr (RQ > 4) {
+        SV_KRON_FENCE();
         if (rm & 16u) r_u1<R, RQ, 4>(v, cf + 16);
+      }
       break;
     case OPK_DENSE:
     case OPK_REAL:
       if (op.k == 1) {
-        const bool real = op.kind == OPK_REAL;
-        SV_SLOT_CASES(r_dense1, v, cf, rm, rv, real)
+        if (op.kind == OPK_REAL) {
+          SV_SLOT_CASES(r_dense1, true, v, cf, rm, rv)
+        } else {
+          SV_SLOT_CASES(r_dense1, false, v, cf, rm, rv)
+        }
       } else {
         SV_PAIR_CASES(r_dense2, v, cf, rm, rv)
       }
       break;
-    case OPK_ANTIDIAG: {
-      const bool flip = (fl & OPF_FLIP) != 0;  // pure bit flip (X, CNOT): no multiplies
-      SV_SLOT_CASES(r_anti1, v, cf, rm, rv, flip)
+    case OPK_ANTIDIAG:
+      if (fl & OPF_FLIP) {  // pure bit flip (X, CNOT): no multiplies
+        SV_SLOT_CASES(r_anti1, true, v, cf, rm, rv)
+      } else {
+        SV_SLOT_CASES(r_anti1, false, v, cf, rm, rv)
+      }
       break;
-    }
     case OPK_SWAP: SV_PAIR_CASES(r_swap, v, rm, rv) break;
     case OPK_DIAG: r_diag<R, RQ>(v, op, cf, tb, base); break;
     default: break;
