@@ -208,6 +208,52 @@ namespace {
 
 // ----------------------------------------------------------- programs
 
+#ifndef SV_ROT_SPLIT
+#define SV_ROT_SPLIT 1
+#endif
+constexpr bool g_rot_split = SV_ROT_SPLIT != 0;  // register phases in rotation + phase-table form
+
+// A 2x2 unitary U written as g * diag(1, ephi) * [[C, -S], [S, C]] * diag(1, elam)
+// with C = |U00| and S = |U10| (C^2 + S^2 = 1, |g| = |ephi| = |elam| = 1): the
+// Z-Y-Z Euler form of a one-qubit gate.  The rotation is kept as t and a scale:
+// with C >= S it is C * [[1, -t], [t, 1]], t = S/C (cot = false); otherwise
+// S * [[t, -1], [1, t]], t = C/S (cot = true), so |t| <= 1 either way.
+struct RotSplit {
+  cplx g = 1.0, ephi = 1.0, elam = 1.0;
+  double t = 0.0, scale = 1.0;
+  bool cot = false;
+};
+
+bool rot_split(const cplx* U, double tol, RotSplit& r) {
+  double C = std::abs(U[0]), S = std::abs(U[2]);
+  const double nrm = std::hypot(C, S);
+  if (!(nrm > 0.5 && nrm < 2.0)) return false;
+  C /= nrm;
+  S /= nrm;
+  constexpr double tiny = 1e-150;
+  const cplx g = std::abs(U[0]) > tiny ? U[0] / std::abs(U[0])
+                 : std::abs(U[1]) > tiny ? -U[1] / std::abs(U[1])
+                                          : cplx(1.0);
+  cplx ephi = 1.0, elam = 1.0;
+  if (std::abs(U[2]) > tiny && std::abs(U[1]) > tiny) {
+    ephi = (U[2] / std::abs(U[2])) / g;
+    elam = -(U[1] / std::abs(U[1])) / g;
+  } else if (std::abs(U[3]) > tiny) {  // diagonal
+    ephi = (U[3] / std::abs(U[3])) / g;
+  }
+  // reconstruct and compare
+  const cplx M[4] = {g * C, -g * S * elam, g * ephi * S, g * ephi * elam * C};
+  for (int i = 0; i < 4; i++)
+    if (!(std::abs(M[i] - U[i]) <= tol)) return false;
+  r.g = g;
+  r.ephi = ephi;
+  r.elam = elam;
+  r.cot = S > C;
+  r.t = r.cot ? C / S : S / C;
+  r.scale = r.cot ? S : C;
+  return true;
+}
+
 // Converts one sweep of the plan into the kernel's program: each op gets local
 // positions and control masks; consecutive ops whose moving qubits fit four
 // register slots form one register phase; dense k >= 3 blocks and wide
@@ -381,10 +427,22 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
   if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
   P.h.nphases = nph;
 
-  // Final op list.  In a register phase, a run of uncontrolled one-qubit dense
-  // ops becomes one KRON op (same-slot matrices multiplied in double, distinct
-  // slots commute); sign flips carry their pattern of register combinations;
-  // flags tell the kernel which control tests to make.
+  // Final op list.  In a register phase, a run of uncontrolled one-qubit
+  // gates is merged per slot (same-slot matrices multiplied in double; distinct
+  // slots commute).  Each merged 2x2 unitary is split as
+  //   g * diag(1, e^{i phi}) * [[C, -S], [S, C]] * diag(1, e^{i lambda})
+  // and the rotation runs as one KROT op scaled by 1/max(C, S), so each output
+  // component costs one FMA.  The diagonal factors, the scales and global
+  // phases, and every diagonal op on register slots only (Z/CZ sign flips,
+  // phase gates) are collected in a table of 2^rq phases over the register
+  // combinations.  The table is applied (OPK_PHASE) only when a
+  // non-diagonal op needs it: when the table varies along one of the op's
+  // target slots (a diagonal commutes with an op whose targets it does not
+  // depend on, controls included), and at the end of the phase.  A unitary
+  // that does not split within the precision's tolerance falls back to the
+  // dense KRON form.  Sign flips involving thread or outside-tile bits carry
+  // their pattern of register combinations; flags tell the kernel which
+  // control tests to make.
   auto u1_free = [](const Tmp& t) {
     return (t.d.kind == OPK_DENSE || t.d.kind == OPK_REAL) && t.d.k == 1 && t.d.lmask == 0 && t.d.xmask == 0;
   };
@@ -394,56 +452,187 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
       if (((uint32_t)j & rmask) == rval) p |= 1u << j;
     return p;
   };
+  const double split_tol = sizeof(R) == 4 ? 1e-9 : 1e-13;
+  std::vector<std::pair<int, int>> span(nph);
+  for (int p = 0; p < nph; p++) span[p] = {P.ph[p].first, P.ph[p].nops};
   std::vector<Tmp> fin;
-  fin.reserve(ts.size());
-  for (int p = 0; p < nph; p++) {
-    Phase& ph = P.ph[p];
-    const int first = ph.first, nops = ph.nops;
-    const int nf = (int)fin.size();
-    if (ph.kind == PH_SMEM) {
-      fin.push_back(ts[first]);
-    } else {
-      for (int o = first; o < first + nops;) {
-        if (u1_free(ts[o]) && o + 1 < first + nops && u1_free(ts[o + 1])) {
-          Tmp k;
-          std::memset(&k.d, 0, sizeof(k.d));
-          k.d.kind = OPK_KRON;
-          k.smem = false;
-          k.need = 0;
-          std::vector<cplx> mats(4 * rq, 0.0);
-          for (int s2 = 0; s2 < rq; s2++) mats[4 * s2] = mats[4 * s2 + 3] = 1.0;
-          uint32_t present = 0;
-          for (; o < first + nops && u1_free(ts[o]); o++) {
-            const int sl = ts[o].d.rs[0];
-            const std::vector<cplx>& U = ts[o].m;
-            cplx* M = &mats[4 * sl];
-            const cplx a = U[0] * M[0] + U[1] * M[2], b = U[0] * M[1] + U[1] * M[3];
-            const cplx c = U[2] * M[0] + U[3] * M[2], d = U[2] * M[1] + U[3] * M[3];
-            M[0] = a; M[1] = b; M[2] = c; M[3] = d;
-            present |= 1u << sl;
-          }
-          k.d.rmask = (uint8_t)present;
-          k.m = mats;
-          fin.push_back(k);
-        } else {
-          fin.push_back(ts[o]);
-          o++;
-        }
-      }
-      for (int i = nf; i < (int)fin.size(); i++) {
-        DevOp& d = fin[i].d;
-        d.pad &= OPF_FLIP;
-        if (d.kind != OPK_KRON) {
-          if (d.tmask) d.pad |= OPF_TCOND;
-          if (d.xmask) d.pad |= OPF_XCOND;
-        }
+  fin.reserve(2 * ts.size() + 2 * nph);
+  auto blank = [](OpKind kind) {
+    Tmp t;
+    std::memset(&t.d, 0, sizeof(t.d));
+    t.d.kind = kind;
+    for (int i = 0; i < 5; i++) t.d.rs[i] = 0xFF;
+    t.smem = false;
+    t.need = 0;
+    return t;
+  };
+  // Per-slot products of a run of uncontrolled one-qubit gates [o, end).
+  auto merge_run = [&](int o, int end, std::vector<cplx>& mats) {
+    mats.assign(4 * rq, 0.0);
+    for (int s2 = 0; s2 < rq; s2++) mats[4 * s2] = mats[4 * s2 + 3] = 1.0;
+    uint32_t present = 0;
+    for (; o < end; o++) {
+      const int sl = ts[o].d.rs[0];
+      const std::vector<cplx>& U = ts[o].m;
+      cplx* M = &mats[4 * sl];
+      const cplx a = U[0] * M[0] + U[1] * M[2], b = U[0] * M[1] + U[1] * M[3];
+      const cplx c = U[2] * M[0] + U[3] * M[2], d = U[2] * M[1] + U[3] * M[3];
+      M[0] = a; M[1] = b; M[2] = c; M[3] = d;
+      present |= 1u << sl;
+    }
+    return present;
+  };
+  auto kron_op = [&](uint32_t present, const std::vector<cplx>& mats) {
+    Tmp k = blank(OPK_KRON);
+    k.d.rmask = (uint8_t)present;
+    k.m = mats;
+    return k;
+  };
+  auto emit_phase_plain = [&](int first, int nops) {
+    for (int o = first; o < first + nops;) {
+      if (u1_free(ts[o]) && o + 1 < first + nops && u1_free(ts[o + 1])) {
+        int end = o;
+        while (end < first + nops && u1_free(ts[end])) end++;
+        std::vector<cplx> mats;
+        const uint32_t present = merge_run(o, end, mats);
+        fin.push_back(kron_op(present, mats));
+        o = end;
+      } else {
+        fin.push_back(ts[o]);
+        o++;
       }
     }
-    if ((int)fin.size() - nf > 255) fail(SV_ERR_INVALID, "internal: phase too long");
-    ph.first = (uint8_t)nf;
-    ph.nops = (uint8_t)((int)fin.size() - nf);
-  }
-  if ((int)fin.size() > kMaxOps) fail(SV_ERR_INVALID, "internal: too many ops");
+  };
+  auto emit_phase_rot = [&](int first, int nops) {
+    const int NT = 1 << rq;
+    std::vector<cplx> tab(NT, 1.0);
+    cplx sc = 1.0;
+    auto tab_dep = [&](uint32_t slots) {
+      for (int j = 0; j < NT; j++)
+        for (int s2 = 0; s2 < rq; s2++)
+          if (((slots >> s2) & 1u) && tab[j] != tab[j ^ (1 << s2)]) return true;
+      return false;
+    };
+    auto flush = [&]() {
+      bool id = sc == cplx(1.0);
+      for (const cplx& x : tab)
+        if (x != cplx(1.0)) id = false;
+      if (id) return;
+      Tmp t = blank(OPK_PHASE);
+      t.m.resize(NT);
+      for (int j = 0; j < NT; j++) t.m[j] = tab[j] * sc;
+      fin.push_back(t);
+      tab.assign(NT, 1.0);
+      sc = 1.0;
+    };
+    for (int o = first; o < first + nops;) {
+      const Tmp& t = ts[o];
+      const DevOp& d = t.d;
+      if (u1_free(t)) {
+        int end = o;
+        while (end < first + nops && u1_free(ts[end])) end++;
+        std::vector<cplx> mats;
+        const uint32_t present = merge_run(o, end, mats);
+        o = end;
+        RotSplit sp[kMaxRegQ];
+        bool ok = true;
+        for (int s2 = 0; s2 < rq; s2++)
+          if ((present >> s2) & 1u) ok = ok && rot_split(&mats[4 * s2], split_tol, sp[s2]);
+        if (!ok) {
+          if (tab_dep(present)) flush();
+          fin.push_back(kron_op(present, mats));
+          continue;
+        }
+        for (int s2 = 0; s2 < rq; s2++) {
+          if (!((present >> s2) & 1u)) continue;
+          for (int j = 0; j < NT; j++)
+            if ((j >> s2) & 1) tab[j] *= sp[s2].elam;
+          sc *= sp[s2].g * sp[s2].scale;
+        }
+        if (tab_dep(present)) flush();
+        Tmp k = blank(OPK_KROT);
+        k.d.rmask = (uint8_t)present;
+        k.m.assign(rq, 0.0);
+        for (int s2 = 0; s2 < rq; s2++) {
+          if (!((present >> s2) & 1u)) continue;
+          k.m[s2] = sp[s2].t;
+          if (sp[s2].cot) k.d.rval |= (uint8_t)(1u << s2);
+        }
+        fin.push_back(k);
+        for (int s2 = 0; s2 < rq; s2++) {
+          if (!((present >> s2) & 1u)) continue;
+          for (int j = 0; j < NT; j++)
+            if ((j >> s2) & 1) tab[j] *= sp[s2].ephi;
+        }
+        // the unapplied scale bounds how far the amplitudes have grown
+        if (std::abs(sc) < 1e-9) flush();
+        continue;
+      }
+      if (d.kind == OPK_SIGN && d.tmask == 0 && d.xmask == 0) {  // on register slots only
+        for (int j = 0; j < NT; j++)
+          if (((uint32_t)j & d.rmask) == d.rval) tab[j] = -tab[j];
+        o++;
+        continue;
+      }
+      if (d.kind == OPK_DIAG && d.tmask == 0 && d.xmask == 0) {
+        bool regs = true;
+        for (int i = 0; i < d.k; i++)
+          if (d.rs[i] == 0xFF) regs = false;
+        if (regs) {
+          for (int j = 0; j < NT; j++) {
+            if (((uint32_t)j & d.rmask) != d.rval) continue;
+            int idx = 0;
+            for (int i = 0; i < d.k; i++) idx |= ((j >> d.rs[i]) & 1) << i;
+            tab[j] *= t.m[idx];
+          }
+          o++;
+          continue;
+        }
+      }
+      if (d.kind != OPK_SIGN && d.kind != OPK_DIAG) {
+        uint32_t tg = 0;
+        for (int i = 0; i < d.k; i++)
+          if (d.rs[i] != 0xFF) tg |= 1u << d.rs[i];
+        if (tab_dep(tg)) flush();
+      }
+      fin.push_back(t);
+      o++;
+    }
+    flush();
+  };
+  // Builds the whole list; false if it does not fit the program (the table
+  // form can need more ops and coefficients than the plain one).
+  auto make_fin = [&](bool rot) {
+    fin.clear();
+    size_t ncoef = 0;
+    for (int p = 0; p < nph; p++) {
+      Phase& ph = P.ph[p];
+      const int first = span[p].first, nops = span[p].second;
+      const int nf = (int)fin.size();
+      if (ph.kind == PH_SMEM) {
+        fin.push_back(ts[first]);
+      } else {
+        if (rot)
+          emit_phase_rot(first, nops);
+        else
+          emit_phase_plain(first, nops);
+        for (int i = nf; i < (int)fin.size(); i++) {
+          DevOp& d = fin[i].d;
+          d.pad &= OPF_FLIP;
+          if (d.kind != OPK_KRON && d.kind != OPK_KROT && d.kind != OPK_PHASE) {
+            if (d.tmask) d.pad |= OPF_TCOND;
+            if (d.xmask) d.pad |= OPF_XCOND;
+          }
+        }
+      }
+      if ((int)fin.size() - nf > 255) return false;
+      ph.first = (uint8_t)nf;
+      ph.nops = (uint8_t)((int)fin.size() - nf);
+    }
+    for (const Tmp& t : fin) ncoef += t.m.size();
+    return (int)fin.size() <= kMaxOps && ncoef <= (size_t)SweepProgram<R>::kPool;
+  };
+  if (!make_fin(g_rot_split) && !make_fin(false)) fail(SV_ERR_INVALID, "internal: program too long");
   P.h.nops = (int)fin.size();
 
   int coef = 0;

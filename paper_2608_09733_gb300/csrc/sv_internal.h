@@ -34,6 +34,10 @@ enum OpKind : uint8_t {
   OPK_SIGN = 5,     // negate the amplitudes whose bits match (CZ, Z, CCZ ...): no coefficients
   OPK_KRON = 6,     // register phase only: uncontrolled 2x2 matrices on register slots (rmask = the
                     // slots present), four blocks of four coefficients at `coef`
+  OPK_KROT = 7,     // register phase only: scaled real rotations on register slots (rmask = the slots
+                    // present).  Slot s has t = coef[s].re and, with bit s of rval clear,
+                    // (a, b) -> (a - t b, b + t a); with it set, (a, b) -> (t a - b, a + t b)
+  OPK_PHASE = 8,    // register phase only: amplitude j of the thread's 2^RQ is multiplied by coef[j]
 };
 
 // DevOp.pad flag bits

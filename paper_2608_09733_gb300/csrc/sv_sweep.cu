@@ -119,6 +119,35 @@ __device__ __forceinline__ void r_u1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf) {
   }
 }
 
+// Scaled real rotation on register slot S (the scale is carried by a later
+// phase table): (a, b) -> (a - t b, b + t a), or with COT (a, b) -> (t a - b, a + t b).
+// One FMA per output component.
+template <typename R, int RQ, int S, bool COT>
+__device__ __forceinline__ void r_rot(Cx<R> (&v)[1 << RQ], R t) {
+  constexpr int NR = 1 << RQ;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> a = v[j], b = v[j1];
+    if (COT) {
+      v[j] = {fma(t, a.re, -b.re), fma(t, a.im, -b.im)};
+      v[j1] = {fma(t, b.re, a.re), fma(t, b.im, a.im)};
+    } else {
+      v[j] = {fma(-t, b.re, a.re), fma(-t, b.im, a.im)};
+      v[j1] = {fma(t, a.re, b.re), fma(t, a.im, b.im)};
+    }
+  }
+}
+
+template <typename R, int RQ, int S>
+__device__ __forceinline__ void r_rot_slot(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t cot) {
+  if ((cot >> S) & 1u)
+    r_rot<R, RQ, S, true>(v, cf[S].re);
+  else
+    r_rot<R, RQ, S, false>(v, cf[S].re);
+}
+
 // Anti-diagonal 2x2 on register slot S: a pure bit flip (X, CNOT) when FLIP,
 // else out0 = a01 v1, out1 = a10 v0 (Y ...); register-slot controls by select.
 template <typename R, int RQ, int S, bool FLIP>
@@ -279,6 +308,23 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
         if (rm & 16u) r_u1<R, RQ, 4>(v, cf + 16);
       }
       break;
+    case OPK_KROT:  // rotations on distinct slots commute
+      if (rm & 1u) r_rot_slot<R, RQ, 0>(v, cf, rv);
+      SV_KRON_FENCE();
+      if (rm & 2u) r_rot_slot<R, RQ, 1>(v, cf, rv);
+      SV_KRON_FENCE();
+      if (rm & 4u) r_rot_slot<R, RQ, 2>(v, cf, rv);
+      SV_KRON_FENCE();
+      if (rm & 8u) r_rot_slot<R, RQ, 3>(v, cf, rv);
+      if constexpr (RQ > 4) {
+        SV_KRON_FENCE();
+        if (rm & 16u) r_rot_slot<R, RQ, 4>(v, cf, rv);
+      }
+      break;
+    case OPK_PHASE:
+#pragma unroll
+      for (int j = 0; j < (1 << RQ); j++) v[j] = cmul(cf[j], v[j]);
+      break;
     case OPK_DENSE:
     case OPK_REAL:
       if (op.k == 1) {
@@ -304,28 +350,38 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
   }
 }
 
-// The local bits of register slot combination j (masks m[] = 1 << rp[]).
-template <int RQ>
-__device__ __forceinline__ uint32_t reg_bits(int j, const uint32_t (&m)[RQ]) {
-  uint32_t b = 0;
+// Shared-memory slots of a thread's register combinations.  The swizzle is
+// linear over XOR and the thread bits tb are disjoint from the register bits,
+// so phys(tb | bits(j)) = phys(tb) ^ (XOR of phys(m[i]) over the set bits i of
+// j): each slot is one XOR away from a slot computed before it.  With STEP = 2
+// only even j are formed (pairs sharing a 16-byte granule).
+template <typename R, int RQ, int STEP>
+__device__ __forceinline__ void reg_slots(uint32_t (&off)[(1 << RQ) / STEP], uint32_t tb, const uint32_t (&m)[RQ]) {
+  off[0] = phys<R>(tb);
 #pragma unroll
-  for (int i = 0; i < RQ; i++)
-    if ((j >> i) & 1) b |= m[i];
-  return b;
+  for (int j = STEP; j < (1 << RQ); j += STEP) {
+    const int low = j & -j;  // lowest set bit of j
+    const int i = low == 1 ? 0 : low == 2 ? 1 : low == 4 ? 2 : low == 8 ? 3 : 4;
+    off[j / STEP] = off[(j ^ low) / STEP] ^ phys<R>(m[i]);
+  }
 }
 
 template <typename R, int RQ>
 __device__ __forceinline__ void reg_load(Cx<R> (&v)[1 << RQ], const Cx<R>* s, uint32_t tb, const uint32_t (&m)[RQ]) {
   if (sizeof(Cx<R>) == 8 && m[0] == 1u) {  // pairs (j, j+1) share a 16-byte granule
+    uint32_t off[(1 << RQ) / 2];
+    reg_slots<R, RQ, 2>(off, tb, m);
 #pragma unroll
     for (int j = 0; j < (1 << RQ); j += 2) {
-      const float4 w = *reinterpret_cast<const float4*>(s + phys<R>(tb | reg_bits<RQ>(j, m)));
+      const float4 w = *reinterpret_cast<const float4*>(s + off[j / 2]);
       v[j] = Cx<R>{(R)w.x, (R)w.y};
       v[j + 1] = Cx<R>{(R)w.z, (R)w.w};
     }
   } else {
+    uint32_t off[1 << RQ];
+    reg_slots<R, RQ, 1>(off, tb, m);
 #pragma unroll
-    for (int j = 0; j < (1 << RQ); j++) v[j] = s[phys<R>(tb | reg_bits<RQ>(j, m))];
+    for (int j = 0; j < (1 << RQ); j++) v[j] = s[off[j]];
   }
 }
 
@@ -333,13 +389,17 @@ template <typename R, int RQ>
 __device__ __forceinline__ void reg_store(const Cx<R> (&v)[1 << RQ], Cx<R>* s, uint32_t tb,
                                           const uint32_t (&m)[RQ]) {
   if (sizeof(Cx<R>) == 8 && m[0] == 1u) {
+    uint32_t off[(1 << RQ) / 2];
+    reg_slots<R, RQ, 2>(off, tb, m);
 #pragma unroll
     for (int j = 0; j < (1 << RQ); j += 2)
-      *reinterpret_cast<float4*>(s + phys<R>(tb | reg_bits<RQ>(j, m))) =
+      *reinterpret_cast<float4*>(s + off[j / 2]) =
           make_float4((float)v[j].re, (float)v[j].im, (float)v[j + 1].re, (float)v[j + 1].im);
   } else {
+    uint32_t off[1 << RQ];
+    reg_slots<R, RQ, 1>(off, tb, m);
 #pragma unroll
-    for (int j = 0; j < (1 << RQ); j++) s[phys<R>(tb | reg_bits<RQ>(j, m))] = v[j];
+    for (int j = 0; j < (1 << RQ); j++) s[off[j]] = v[j];
   }
 }
 
