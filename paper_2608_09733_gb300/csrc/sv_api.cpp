@@ -55,6 +55,14 @@ AddrRangeFn addr_range_fn() {
 
 void set_last_error(const std::string& m) { g_last_error = m; }
 
+// Waits for the stream; a pass kernel that gave up on its tile copies is
+// reported here as well.
+void sync_stream(cudaStream_t s) {
+  cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (sweep_timed_out())
+    fail(SV_ERR_TIMEOUT, "a pass gave up waiting (2 s) for its tile copies; the state is not valid");
+}
+
 void check_device_buffer(const void* p, size_t bytes, const char* what) {
   if (!p) fail(SV_ERR_INVALID, std::string(what) + " is NULL");
   if ((uintptr_t)p % 16) fail(SV_ERR_INVALID, std::string(what) + " is not 16-byte aligned");
@@ -99,7 +107,7 @@ std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 void grow(void** p, size_t* cap, size_t want, cudaStream_t stream, const char* what) {
   if (*cap >= want) return;
   if (*p) {
-    cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    sync_stream(stream);
     cudaFree(*p);
     *p = nullptr;
     *cap = 0;
@@ -215,13 +223,12 @@ constexpr bool g_rot_split = SV_ROT_SPLIT != 0;  // register phases in rotation 
 
 // A 2x2 unitary U written as g * diag(1, ephi) * [[C, -S], [S, C]] * diag(1, elam)
 // with C = |U00| and S = |U10| (C^2 + S^2 = 1, |g| = |ephi| = |elam| = 1): the
-// Z-Y-Z Euler form of a one-qubit gate.  The rotation is kept as t and a scale:
-// with C >= S it is C * [[1, -t], [t, 1]], t = S/C (cot = false); otherwise
-// S * [[t, -1], [1, t]], t = C/S (cot = true), so |t| <= 1 either way.
+// Z-Y-Z Euler form of a one-qubit gate.  With C = cos(alpha), S = sin(alpha),
+// alpha in [0, pi/2], the rotation is kept as the shear pair
+// (tan(alpha/2), sin(alpha)) = (S / (1 + C), S), both in [0, 1].
 struct RotSplit {
   cplx g = 1.0, ephi = 1.0, elam = 1.0;
-  double t = 0.0, scale = 1.0;
-  bool cot = false;
+  double t = 0.0, s = 0.0;
 };
 
 bool rot_split(const cplx* U, double tol, RotSplit& r) {
@@ -248,9 +255,8 @@ bool rot_split(const cplx* U, double tol, RotSplit& r) {
   r.g = g;
   r.ephi = ephi;
   r.elam = elam;
-  r.cot = S > C;
-  r.t = r.cot ? C / S : S / C;
-  r.scale = r.cot ? S : C;
+  r.t = S / (1.0 + C);
+  r.s = S;
   return true;
 }
 
@@ -431,9 +437,9 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
   // gates is merged per slot (same-slot matrices multiplied in double; distinct
   // slots commute).  Each merged 2x2 unitary is split as
   //   g * diag(1, e^{i phi}) * [[C, -S], [S, C]] * diag(1, e^{i lambda})
-  // and the rotation runs as one KROT op scaled by 1/max(C, S), so each output
-  // component costs one FMA.  The diagonal factors, the scales and global
-  // phases, and every diagonal op on register slots only (Z/CZ sign flips,
+  // and the rotations of the run become one KROT op (three in-place shears
+  // per slot).  The diagonal factors, the global phases, and every diagonal
+  // op on register slots only (Z/CZ sign flips,
   // phase gates) are collected in a table of 2^rq phases over the register
   // combinations.  The table is applied (OPK_PHASE) only when a
   // non-diagonal op needs it: when the table varies along one of the op's
@@ -547,25 +553,20 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
           if (!((present >> s2) & 1u)) continue;
           for (int j = 0; j < NT; j++)
             if ((j >> s2) & 1) tab[j] *= sp[s2].elam;
-          sc *= sp[s2].g * sp[s2].scale;
+          sc *= sp[s2].g;
         }
         if (tab_dep(present)) flush();
         Tmp k = blank(OPK_KROT);
         k.d.rmask = (uint8_t)present;
         k.m.assign(rq, 0.0);
-        for (int s2 = 0; s2 < rq; s2++) {
-          if (!((present >> s2) & 1u)) continue;
-          k.m[s2] = sp[s2].t;
-          if (sp[s2].cot) k.d.rval |= (uint8_t)(1u << s2);
-        }
+        for (int s2 = 0; s2 < rq; s2++)
+          if ((present >> s2) & 1u) k.m[s2] = cplx(sp[s2].t, sp[s2].s);
         fin.push_back(k);
         for (int s2 = 0; s2 < rq; s2++) {
           if (!((present >> s2) & 1u)) continue;
           for (int j = 0; j < NT; j++)
             if ((j >> s2) & 1) tab[j] *= sp[s2].ephi;
         }
-        // the unapplied scale bounds how far the amplitudes have grown
-        if (std::abs(sc) < 1e-9) flush();
         continue;
       }
       if (d.kind == OPK_SIGN && d.tmask == 0 && d.xmask == 0) {  // on register slots only
@@ -653,7 +654,9 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
   P.h.ncoef = coef;
   static const bool debug = std::getenv("SV_DEBUG_PLAN") != nullptr;
   if (debug) {
-    std::fprintf(stderr, "[sv plan] sweep m=%d L=%d ops=%d phases=%d:", sw.m, sw.L, P.h.nops, nph);
+    std::fprintf(stderr, "[sv plan] sweep m=%d L=%d tq=", sw.m, sw.L);
+    for (int i = 0; i < sw.m; i++) std::fprintf(stderr, "%s%d", i ? "," : "", sw.tq[i]);
+    std::fprintf(stderr, " ops=%d phases=%d:", P.h.nops, nph);
     for (int p = 0; p < nph; p++) {
       std::fprintf(stderr, " %s(", P.ph[p].kind == PH_REG ? "R" : "S");
       for (int o = P.ph[p].first; o < P.ph[p].first + P.ph[p].nops; o++)
@@ -666,6 +669,8 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
 
 template <typename R>
 void run_plan(void* state, const Plan& plan, cudaStream_t stream) {
+  if (sweep_timed_out())
+    fail(SV_ERR_TIMEOUT, "an earlier pass gave up waiting (2 s) for its tile copies; its state is not valid");
   static thread_local std::unique_ptr<SweepProgram<R>> prog;
   if (!prog) prog.reset(new SweepProgram<R>());
   const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << plan.n);  // read + write the state
@@ -795,7 +800,7 @@ sv_status sv_expect(const void* state, int n_qubits, sv_dtype dtype, const sv_pa
     pr.done();
     if (!out_on_device) {
       cuda_check(cudaMemcpyAsync(out, w.out, n_terms * sizeof(double), cudaMemcpyDeviceToHost, s), "result copy");
-      cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+      sync_stream(s);
     }
   });
 }
@@ -815,7 +820,7 @@ sv_status sv_expect_z_all(const void* state, int n_qubits, sv_dtype dtype, doubl
       expect_z_all_dev(state, n_qubits, dtype, w.out, s);
       cuda_check(cudaMemcpyAsync(out, w.out, (n_qubits + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
                  "result copy");
-      cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+      sync_stream(s);
     }
   });
 }
@@ -863,7 +868,7 @@ sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const 
                "result copy");
     if (state_out)
       cuda_check(cudaMemcpyAsync(state_out, w.state, bytes, cudaMemcpyDeviceToHost, s), "state download");
-    cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    sync_stream(s);
   });
 }
 
@@ -907,7 +912,7 @@ sv_status sv_set_state(sv_handle h, const void* src, int src_is_device) {
     cuda_check(cudaMemcpyAsync(h->ptr, src, h->bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                h->stream),
                "state copy");
-    cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    sync_stream(h->stream);
   });
 }
 
@@ -918,7 +923,7 @@ sv_status sv_get_state(sv_handle h, void* dst, int dst_is_device) {
     cuda_check(cudaMemcpyAsync(dst, h->ptr, h->bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                h->stream),
                "state copy");
-    cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    sync_stream(h->stream);
   });
 }
 
@@ -1012,7 +1017,7 @@ void run_batch_small(int nreq, sv_dtype dtype, const int* nq, const sv_gate* con
   pr.done();
   if (!out_on_device) {
     cuda_check(cudaMemcpyAsync(out, dout, sizeof(double) * nreq, cudaMemcpyDeviceToHost, stream), "result copy");
-    cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    sync_stream(stream);
   }
 }
 }  // namespace

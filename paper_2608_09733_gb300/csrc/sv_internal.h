@@ -34,9 +34,8 @@ enum OpKind : uint8_t {
   OPK_SIGN = 5,     // negate the amplitudes whose bits match (CZ, Z, CCZ ...): no coefficients
   OPK_KRON = 6,     // register phase only: uncontrolled 2x2 matrices on register slots (rmask = the
                     // slots present), four blocks of four coefficients at `coef`
-  OPK_KROT = 7,     // register phase only: scaled real rotations on register slots (rmask = the slots
-                    // present).  Slot s has t = coef[s].re and, with bit s of rval clear,
-                    // (a, b) -> (a - t b, b + t a); with it set, (a, b) -> (t a - b, a + t b)
+  OPK_KROT = 7,     // register phase only: real rotations [[C, -S], [S, C]] on register slots (rmask =
+                    // the slots present) as three shears; slot s has coef[s] = (tan(alpha/2), sin(alpha))
   OPK_PHASE = 8,    // register phase only: amplitude j of the thread's 2^RQ is multiplied by coef[j]
 };
 
@@ -254,6 +253,8 @@ int reg_qubits_for(int m);  // register qubits of a tile of m qubits (4, or 5 fo
 
 template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream);
+// True (once) if a pass kernel gave up waiting for its tile copies since the last call.
+bool sweep_timed_out();
 template <typename R>
 cudaError_t launch_init_basis(Cx<R>* state, int n, uint64_t index, cudaStream_t stream);
 // One CTA per small request (whole state in shared memory): request b runs
