@@ -208,6 +208,18 @@ sv_status sv_plan_info(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_
                        const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
                        int* out_blocks, int* out_sweeps, int* block_starts);
 
+/* Host execution of the pass kernel's programs: builds the plan of `gates`
+ * exactly as sv_apply_circuit_ex would for `dtype` (fusion, tiles, register
+ * phases, rotations, phase tables), then runs every program on the host in
+ * double precision.  The paper has no counterpart: this validates the
+ * program builder (the transformation of Sec. 5.3 / 9.2 gate lists into pass
+ * programs) without a GPU, and says nothing about the kernel's arithmetic.
+ *   state   host, 2^n complex128 (re, im interleaved), updated in place
+ * 1 <= n_qubits <= 20; errors as sv_apply_circuit_ex.  Slow (seconds). */
+sv_status sv_emulate_apply(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                           const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
+                           double* state);
+
 /* Gradients of f_b(theta) = <0|U^dag(theta_b) H U(theta_b)|0> (Sec. 4.2) for a
  * batch of parameter vectors of one circuit template, by the adjoint method:
  * one forward pass storing the state every `checkpoint_every` gates, then

@@ -20,6 +20,7 @@ from .binding import (  # noqa: F401
     SV_BLOCK_AUTO,
     SV_BLOCK_DENSE,
     sv_expect,
+    sv_emulate_apply,
     sv_expect_z_all,
     sv_init_basis,
     sv_plan_info,

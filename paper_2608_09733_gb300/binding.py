@@ -35,7 +35,7 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_expect_z_all",
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
-           "sv_expect_z_all_noalloc"]
+           "sv_expect_z_all_noalloc", "sv_emulate_apply"]
 
 
 class SvError(RuntimeError):
@@ -98,6 +98,7 @@ def load():
             "sv_expect_z_all": ([vp, ci, ci, vp, ci, vp], ci),
             "sv_apply_circuit_ex": ([vp, ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), vp], ci),
             "sv_plan_info": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), P(ci), P(ci), P(ci)], ci),
+            "sv_emulate_apply": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), vp], ci),
             "sv_run_host": ([ci, ci, vp, P(SvGate), sz, P(cd), sz, ci, P(cd), vp, vp], ci),
             "sv_alloc": ([ci, ci, vp, P(vp)], ci),
             "sv_free": ([vp], ci),
@@ -320,6 +321,19 @@ def sv_plan_info(n: int, dtype: int, gates, param_values=None, fuse_max_k: int =
     _check(load().sv_plan_info(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), ctypes.byref(nb), ctypes.byref(ns),
                                starts))
     return nb.value, ns.value, [starts[i] for i in range(nb.value + 1)]
+
+
+def sv_emulate_apply(state: np.ndarray, n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0,
+                     block_mode: int = 0, ops_per_pass: int = 0) -> np.ndarray:
+    """Runs the kernel programs the plan of `gates` builds for `dtype` on the
+    host, in double precision, on a complex128 numpy state (in place)."""
+    assert state.dtype == np.complex128 and state.size == 1 << n and state.flags.c_contiguous
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    pp, npv, _keep = _params(param_values)
+    o = _opts(fuse_max_k, block_mode, ops_per_pass)
+    _check(load().sv_emulate_apply(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o),
+                                   ctypes.c_void_p(state.ctypes.data)))
+    return state
 
 
 def sv_run_host(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, state_in=None,

@@ -214,459 +214,6 @@ void Prof::done() {
 
 namespace {
 
-// ----------------------------------------------------------- programs
-
-#ifndef SV_ROT_SPLIT
-#define SV_ROT_SPLIT 1
-#endif
-constexpr bool g_rot_split = SV_ROT_SPLIT != 0;  // register phases in rotation + phase-table form
-
-// A 2x2 unitary U written as g * diag(1, ephi) * [[C, -S], [S, C]] * diag(1, elam)
-// with C = |U00| and S = |U10| (C^2 + S^2 = 1, |g| = |ephi| = |elam| = 1): the
-// Z-Y-Z Euler form of a one-qubit gate.  With C = cos(alpha), S = sin(alpha),
-// alpha in [0, pi/2], the rotation is kept as the shear pair
-// (tan(alpha/2), sin(alpha)) = (S / (1 + C), S), both in [0, 1].
-struct RotSplit {
-  cplx g = 1.0, ephi = 1.0, elam = 1.0;
-  double t = 0.0, s = 0.0;
-};
-
-bool rot_split(const cplx* U, double tol, RotSplit& r) {
-  double C = std::abs(U[0]), S = std::abs(U[2]);
-  const double nrm = std::hypot(C, S);
-  if (!(nrm > 0.5 && nrm < 2.0)) return false;
-  C /= nrm;
-  S /= nrm;
-  constexpr double tiny = 1e-150;
-  const cplx g = std::abs(U[0]) > tiny ? U[0] / std::abs(U[0])
-                 : std::abs(U[1]) > tiny ? -U[1] / std::abs(U[1])
-                                          : cplx(1.0);
-  cplx ephi = 1.0, elam = 1.0;
-  if (std::abs(U[2]) > tiny && std::abs(U[1]) > tiny) {
-    ephi = (U[2] / std::abs(U[2])) / g;
-    elam = -(U[1] / std::abs(U[1])) / g;
-  } else if (std::abs(U[3]) > tiny) {  // diagonal
-    ephi = (U[3] / std::abs(U[3])) / g;
-  }
-  // reconstruct and compare
-  const cplx M[4] = {g * C, -g * S * elam, g * ephi * S, g * ephi * elam * C};
-  for (int i = 0; i < 4; i++)
-    if (!(std::abs(M[i] - U[i]) <= tol)) return false;
-  r.g = g;
-  r.ephi = ephi;
-  r.elam = elam;
-  r.t = S / (1.0 + C);
-  r.s = S;
-  return true;
-}
-
-// Converts one sweep of the plan into the kernel's program: each op gets local
-// positions and control masks; consecutive ops whose moving qubits fit four
-// register slots form one register phase; dense k >= 3 blocks and wide
-// diagonals get a shared-memory phase of their own.
-template <typename R>
-void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq_override = 0) {
-  std::memset(&P.h, 0, sizeof(P.h));
-  P.h.n = plan.n;
-  P.h.m = sw.m;
-  P.h.L = sw.L;
-  const int rq = rq_override > 0 ? rq_override : reg_qubits_for(sw.m);
-  P.h.rq = rq;
-  P.h.nops = (int)sw.ops.size();
-  int loc[64];
-  for (int q = 0; q < 64; q++) loc[q] = -1;
-  for (int i = 0; i < sw.m; i++) {
-    P.h.tq[i] = (int8_t)sw.tq[i];
-    loc[sw.tq[i]] = i;
-  }
-  const bool reg_ok = sw.m >= rq && sw.m - rq <= 8;
-  struct Tmp {
-    DevOp d;
-    std::vector<cplx> m;
-    bool smem;
-    uint32_t need;  // local positions that must be register slots
-  };
-  std::vector<Tmp> ts(sw.ops.size());
-  for (size_t oi = 0; oi < sw.ops.size(); oi++) {
-    const LOp& op = plan.ops[sw.ops[oi]];
-    Tmp& t = ts[oi];
-    DevOp& d = t.d;
-    std::memset(&d, 0, sizeof(d));
-    d.kind = op.kind;
-    d.k = (uint8_t)op.k;
-    t.m = op.m;
-    t.need = 0;
-    for (int i = 0; i < 5; i++) d.rs[i] = 0xFF;
-    int sp[5], ns = 0;
-    const bool diag = op.kind == OPK_DIAG;
-    for (int i = 0; i < op.k; i++) {
-      int l = loc[op.q[i]];
-      d.gq[i] = (uint8_t)op.q[i];
-      if (diag) {
-        d.pos[i] = l < 0 ? 0xFF : (uint8_t)l;
-      } else {
-        if (l < 0) fail(SV_ERR_INVALID, "internal: target outside the tile");
-        d.pos[i] = (uint8_t)l;
-        sp[ns++] = l;
-        t.need |= 1u << l;
-      }
-    }
-    for (int i = 1; i < ns; i++)
-      for (int j = i; j > 0 && sp[j - 1] > sp[j]; j--) std::swap(sp[j], sp[j - 1]);
-    for (int i = 0; i < ns; i++) d.spos[i] = (uint8_t)sp[i];
-    for (int i = 0; i < op.nc; i++) {
-      int l = loc[op.c[i]];
-      if (l >= 0) {
-        d.lmask |= 1u << l;
-        if (op.cs[i]) d.lval |= 1u << l;
-      } else {
-        d.xmask |= 1ull << op.c[i];
-        if (op.cs[i]) d.xval |= 1ull << op.c[i];
-      }
-    }
-    if (diag) {
-      // diag(1, .., 1, -1): a sign flip where every matrix bit is 1 (Z, CZ, CCZ)
-      const int dd = 1 << op.k;
-      bool sign = true;
-      for (int r = 0; r < dd; r++)
-        if (op.m[r] != (r == dd - 1 ? cplx(-1.0) : cplx(1.0))) sign = false;
-      if (sign) {
-        d.kind = OPK_SIGN;
-        t.m.clear();
-        for (int i = 0; i < op.k; i++) {
-          if (d.pos[i] != 0xFF) {
-            d.lmask |= 1u << d.pos[i];
-            d.lval |= 1u << d.pos[i];
-          } else {
-            d.xmask |= 1ull << op.q[i];
-            d.xval |= 1ull << op.q[i];
-          }
-        }
-      }
-    }
-    if (op.kind == OPK_ANTIDIAG && op.m.size() == 2 && op.m[0] == cplx(1.0) && op.m[1] == cplx(1.0)) d.pad = 1;
-    const bool wide = (op.kind == OPK_DENSE || op.kind == OPK_REAL) ? op.k >= 3 : (diag && d.kind == OPK_DIAG && op.k >= 3);
-    t.smem = !reg_ok || wide;
-  }
-
-  // phases
-  int nph = 0;
-  auto add_phase = [&](PhaseKind kind, int first, int nops, uint32_t need) {
-    if (nph >= kMaxPhases) fail(SV_ERR_INVALID, "internal: too many phases");
-    Phase& ph = P.ph[nph++];
-    std::memset(&ph, 0, sizeof(ph));
-    ph.kind = kind;
-    ph.first = (uint8_t)first;
-    ph.nops = (uint8_t)nops;
-    if (kind != PH_REG) return;
-    // register slots: the needed positions, then local bit 0 (16-byte
-    // shared-memory accesses), then the highest free positions
-    uint32_t rp = need;
-    if (__builtin_popcount(rp) < rq && !(rp & 1u)) rp |= 1u;
-    for (int q = sw.m - 1; q >= 0 && __builtin_popcount(rp) < rq; q--) rp |= 1u << q;
-    int slot_of[32];
-    int ns2 = 0, nt = 0;
-    for (int q = 0; q < sw.m; q++) {
-      if ((rp >> q) & 1u) {
-        slot_of[q] = ns2;
-        ph.rp[ns2++] = (uint8_t)q;
-      } else {
-        slot_of[q] = -1;
-        ph.tpos[nt++] = (uint8_t)q;
-      }
-    }
-    ph.ntpos = (uint8_t)nt;
-    ph.nrp = (uint8_t)ns2;
-    for (int o = first; o < first + nops; o++) {
-      Tmp& t = ts[o];
-      DevOp& d = t.d;
-      for (int i = 0; i < d.k; i++)
-        d.rs[i] = (d.pos[i] != 0xFF && slot_of[d.pos[i]] >= 0) ? (uint8_t)slot_of[d.pos[i]] : 0xFF;
-      d.rmask = d.rval = 0;
-      d.tmask = d.tval = 0;
-      for (int q = 0; q < sw.m; q++) {
-        if (!((d.lmask >> q) & 1u)) continue;
-        const bool v = (d.lval >> q) & 1u;
-        if (slot_of[q] >= 0) {
-          d.rmask |= 1u << slot_of[q];
-          if (v) d.rval |= 1u << slot_of[q];
-        } else {
-          d.tmask |= 1u << q;
-          if (v) d.tval |= 1u << q;
-        }
-      }
-      // two-qubit register ops want rs[0] < rs[1]: swap the matrix qubit order
-      if (d.k == 2 && d.kind != OPK_DIAG && d.kind != OPK_SIGN && d.rs[0] > d.rs[1]) {
-        std::swap(d.rs[0], d.rs[1]);
-        std::swap(d.pos[0], d.pos[1]);
-        std::swap(d.gq[0], d.gq[1]);
-        if (t.m.size() == 16) {
-          std::vector<cplx> mt(16);
-          auto sw2 = [](int x) { return ((x & 1) << 1) | ((x >> 1) & 1); };
-          for (int r = 0; r < 4; r++)
-            for (int c = 0; c < 4; c++) mt[r * 4 + c] = t.m[sw2(r) * 4 + sw2(c)];
-          t.m = mt;
-        }
-      }
-    }
-  };
-  int cur_first = -1, cur_n = 0;
-  uint32_t cur_need = 0;
-  for (int o = 0; o < (int)ts.size(); o++) {
-    if (ts[o].smem) {
-      if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
-      cur_n = 0;
-      cur_need = 0;
-      add_phase(PH_SMEM, o, 1, 0);
-      continue;
-    }
-    if (cur_n && __builtin_popcount(cur_need | ts[o].need) <= rq && cur_n < 255) {
-      cur_need |= ts[o].need;
-      cur_n++;
-    } else {
-      if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
-      cur_first = o;
-      cur_n = 1;
-      cur_need = ts[o].need;
-    }
-  }
-  if (cur_n) add_phase(PH_REG, cur_first, cur_n, cur_need);
-  P.h.nphases = nph;
-
-  // Final op list.  In a register phase, a run of uncontrolled one-qubit
-  // gates is merged per slot (same-slot matrices multiplied in double; distinct
-  // slots commute).  Each merged 2x2 unitary is split as
-  //   g * diag(1, e^{i phi}) * [[C, -S], [S, C]] * diag(1, e^{i lambda})
-  // and the rotations of the run become one KROT op (three in-place shears
-  // per slot).  The diagonal factors, the global phases, and every diagonal
-  // op on register slots only (Z/CZ sign flips,
-  // phase gates) are collected in a table of 2^rq phases over the register
-  // combinations.  The table is applied (OPK_PHASE) only when a
-  // non-diagonal op needs it: when the table varies along one of the op's
-  // target slots (a diagonal commutes with an op whose targets it does not
-  // depend on, controls included), and at the end of the phase.  A unitary
-  // that does not split within the precision's tolerance falls back to the
-  // dense KRON form.  Sign flips involving thread or outside-tile bits carry
-  // their pattern of register combinations; flags tell the kernel which
-  // control tests to make.
-  auto u1_free = [](const Tmp& t) {
-    return (t.d.kind == OPK_DENSE || t.d.kind == OPK_REAL) && t.d.k == 1 && t.d.lmask == 0 && t.d.xmask == 0;
-  };
-  auto pattern = [rq](uint32_t rmask, uint32_t rval) {
-    uint32_t p = 0;
-    for (int j = 0; j < (1 << rq); j++)
-      if (((uint32_t)j & rmask) == rval) p |= 1u << j;
-    return p;
-  };
-  const double split_tol = sizeof(R) == 4 ? 1e-9 : 1e-13;
-  std::vector<std::pair<int, int>> span(nph);
-  for (int p = 0; p < nph; p++) span[p] = {P.ph[p].first, P.ph[p].nops};
-  std::vector<Tmp> fin;
-  fin.reserve(2 * ts.size() + 2 * nph);
-  auto blank = [](OpKind kind) {
-    Tmp t;
-    std::memset(&t.d, 0, sizeof(t.d));
-    t.d.kind = kind;
-    for (int i = 0; i < 5; i++) t.d.rs[i] = 0xFF;
-    t.smem = false;
-    t.need = 0;
-    return t;
-  };
-  // Per-slot products of a run of uncontrolled one-qubit gates [o, end).
-  auto merge_run = [&](int o, int end, std::vector<cplx>& mats) {
-    mats.assign(4 * rq, 0.0);
-    for (int s2 = 0; s2 < rq; s2++) mats[4 * s2] = mats[4 * s2 + 3] = 1.0;
-    uint32_t present = 0;
-    for (; o < end; o++) {
-      const int sl = ts[o].d.rs[0];
-      const std::vector<cplx>& U = ts[o].m;
-      cplx* M = &mats[4 * sl];
-      const cplx a = U[0] * M[0] + U[1] * M[2], b = U[0] * M[1] + U[1] * M[3];
-      const cplx c = U[2] * M[0] + U[3] * M[2], d = U[2] * M[1] + U[3] * M[3];
-      M[0] = a; M[1] = b; M[2] = c; M[3] = d;
-      present |= 1u << sl;
-    }
-    return present;
-  };
-  auto kron_op = [&](uint32_t present, const std::vector<cplx>& mats) {
-    Tmp k = blank(OPK_KRON);
-    k.d.rmask = (uint8_t)present;
-    k.m = mats;
-    return k;
-  };
-  auto emit_phase_plain = [&](int first, int nops) {
-    for (int o = first; o < first + nops;) {
-      if (u1_free(ts[o]) && o + 1 < first + nops && u1_free(ts[o + 1])) {
-        int end = o;
-        while (end < first + nops && u1_free(ts[end])) end++;
-        std::vector<cplx> mats;
-        const uint32_t present = merge_run(o, end, mats);
-        fin.push_back(kron_op(present, mats));
-        o = end;
-      } else {
-        fin.push_back(ts[o]);
-        o++;
-      }
-    }
-  };
-  auto emit_phase_rot = [&](int first, int nops) {
-    const int NT = 1 << rq;
-    std::vector<cplx> tab(NT, 1.0);
-    cplx sc = 1.0;
-    auto tab_dep = [&](uint32_t slots) {
-      for (int j = 0; j < NT; j++)
-        for (int s2 = 0; s2 < rq; s2++)
-          if (((slots >> s2) & 1u) && tab[j] != tab[j ^ (1 << s2)]) return true;
-      return false;
-    };
-    auto flush = [&]() {
-      bool id = sc == cplx(1.0);
-      for (const cplx& x : tab)
-        if (x != cplx(1.0)) id = false;
-      if (id) return;
-      Tmp t = blank(OPK_PHASE);
-      t.m.resize(NT);
-      for (int j = 0; j < NT; j++) t.m[j] = tab[j] * sc;
-      fin.push_back(t);
-      tab.assign(NT, 1.0);
-      sc = 1.0;
-    };
-    for (int o = first; o < first + nops;) {
-      const Tmp& t = ts[o];
-      const DevOp& d = t.d;
-      if (u1_free(t)) {
-        int end = o;
-        while (end < first + nops && u1_free(ts[end])) end++;
-        std::vector<cplx> mats;
-        const uint32_t present = merge_run(o, end, mats);
-        o = end;
-        RotSplit sp[kMaxRegQ];
-        bool ok = true;
-        for (int s2 = 0; s2 < rq; s2++)
-          if ((present >> s2) & 1u) ok = ok && rot_split(&mats[4 * s2], split_tol, sp[s2]);
-        if (!ok) {
-          if (tab_dep(present)) flush();
-          fin.push_back(kron_op(present, mats));
-          continue;
-        }
-        for (int s2 = 0; s2 < rq; s2++) {
-          if (!((present >> s2) & 1u)) continue;
-          for (int j = 0; j < NT; j++)
-            if ((j >> s2) & 1) tab[j] *= sp[s2].elam;
-          sc *= sp[s2].g;
-        }
-        if (tab_dep(present)) flush();
-        Tmp k = blank(OPK_KROT);
-        k.d.rmask = (uint8_t)present;
-        k.m.assign(rq, 0.0);
-        for (int s2 = 0; s2 < rq; s2++)
-          if ((present >> s2) & 1u) k.m[s2] = cplx(sp[s2].t, sp[s2].s);
-        fin.push_back(k);
-        for (int s2 = 0; s2 < rq; s2++) {
-          if (!((present >> s2) & 1u)) continue;
-          for (int j = 0; j < NT; j++)
-            if ((j >> s2) & 1) tab[j] *= sp[s2].ephi;
-        }
-        continue;
-      }
-      if (d.kind == OPK_SIGN && d.tmask == 0 && d.xmask == 0) {  // on register slots only
-        for (int j = 0; j < NT; j++)
-          if (((uint32_t)j & d.rmask) == d.rval) tab[j] = -tab[j];
-        o++;
-        continue;
-      }
-      if (d.kind == OPK_DIAG && d.tmask == 0 && d.xmask == 0) {
-        bool regs = true;
-        for (int i = 0; i < d.k; i++)
-          if (d.rs[i] == 0xFF) regs = false;
-        if (regs) {
-          for (int j = 0; j < NT; j++) {
-            if (((uint32_t)j & d.rmask) != d.rval) continue;
-            int idx = 0;
-            for (int i = 0; i < d.k; i++) idx |= ((j >> d.rs[i]) & 1) << i;
-            tab[j] *= t.m[idx];
-          }
-          o++;
-          continue;
-        }
-      }
-      if (d.kind != OPK_SIGN && d.kind != OPK_DIAG) {
-        uint32_t tg = 0;
-        for (int i = 0; i < d.k; i++)
-          if (d.rs[i] != 0xFF) tg |= 1u << d.rs[i];
-        if (tab_dep(tg)) flush();
-      }
-      fin.push_back(t);
-      o++;
-    }
-    flush();
-  };
-  // Builds the whole list; false if it does not fit the program (the table
-  // form can need more ops and coefficients than the plain one).
-  auto make_fin = [&](bool rot) {
-    fin.clear();
-    size_t ncoef = 0;
-    for (int p = 0; p < nph; p++) {
-      Phase& ph = P.ph[p];
-      const int first = span[p].first, nops = span[p].second;
-      const int nf = (int)fin.size();
-      if (ph.kind == PH_SMEM) {
-        fin.push_back(ts[first]);
-      } else {
-        if (rot)
-          emit_phase_rot(first, nops);
-        else
-          emit_phase_plain(first, nops);
-        for (int i = nf; i < (int)fin.size(); i++) {
-          DevOp& d = fin[i].d;
-          d.pad &= OPF_FLIP;
-          if (d.kind != OPK_KRON && d.kind != OPK_KROT && d.kind != OPK_PHASE) {
-            if (d.tmask) d.pad |= OPF_TCOND;
-            if (d.xmask) d.pad |= OPF_XCOND;
-          }
-        }
-      }
-      if ((int)fin.size() - nf > 255) return false;
-      ph.first = (uint8_t)nf;
-      ph.nops = (uint8_t)((int)fin.size() - nf);
-    }
-    for (const Tmp& t : fin) ncoef += t.m.size();
-    return (int)fin.size() <= kMaxOps && ncoef <= (size_t)SweepProgram<R>::kPool;
-  };
-  if (!make_fin(g_rot_split) && !make_fin(false)) fail(SV_ERR_INVALID, "internal: program too long");
-  P.h.nops = (int)fin.size();
-
-  int coef = 0;
-  for (size_t oi = 0; oi < fin.size(); oi++) {
-    fin[oi].d.coef = (uint32_t)coef;
-    for (const cplx& v : fin[oi].m) {
-      if (coef >= SweepProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: coefficient pool overflow");
-      P.coef[coef].re = (R)v.real();
-      P.coef[coef].im = (R)v.imag();
-      coef++;
-    }
-    P.ops[oi] = fin[oi].d;
-  }
-  for (int p = 0; p < nph; p++)
-    if (P.ph[p].kind == PH_REG)
-      for (int o = P.ph[p].first; o < P.ph[p].first + P.ph[p].nops; o++)
-        if (P.ops[o].kind == OPK_SIGN) P.ops[o].coef = pattern(P.ops[o].rmask, P.ops[o].rval);
-  P.h.ncoef = coef;
-  static const bool debug = std::getenv("SV_DEBUG_PLAN") != nullptr;
-  if (debug) {
-    std::fprintf(stderr, "[sv plan] sweep m=%d L=%d tq=", sw.m, sw.L);
-    for (int i = 0; i < sw.m; i++) std::fprintf(stderr, "%s%d", i ? "," : "", sw.tq[i]);
-    std::fprintf(stderr, " ops=%d phases=%d:", P.h.nops, nph);
-    for (int p = 0; p < nph; p++) {
-      std::fprintf(stderr, " %s(", P.ph[p].kind == PH_REG ? "R" : "S");
-      for (int o = P.ph[p].first; o < P.ph[p].first + P.ph[p].nops; o++)
-        std::fprintf(stderr, "%s%d%s", o > P.ph[p].first ? "," : "", (int)P.ops[o].kind, P.ops[o].k > 1 ? "w" : "");
-      std::fprintf(stderr, ")");
-    }
-    std::fprintf(stderr, "\n");
-  }
-}
-
 template <typename R>
 void run_plan(void* state, const Plan& plan, cudaStream_t stream) {
   if (sweep_timed_out())

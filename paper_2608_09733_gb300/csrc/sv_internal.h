@@ -35,14 +35,25 @@ enum OpKind : uint8_t {
   OPK_KRON = 6,     // register phase only: uncontrolled 2x2 matrices on register slots (rmask = the
                     // slots present), four blocks of four coefficients at `coef`
   OPK_KROT = 7,     // register phase only: real rotations [[C, -S], [S, C]] on register slots (rmask =
-                    // the slots present) as three shears; slot s has coef[s] = (tan(alpha/2), sin(alpha))
-  OPK_PHASE = 8,    // register phase only: amplitude j of the thread's 2^RQ is multiplied by coef[j]
+                    // the slots present).  complex64: three shears, coef[s] = (tan(alpha/2), sin(alpha));
+                    // complex128: scaled form, coef[s].re = S/C (bit s of rval clear) or C/S (set)
+  OPK_PHASE = 8,    // register phase only: amplitude j of the thread's 2^RQ is multiplied by
+                    // coef[var * (2^RQ + 1) + j]; var collects k selector bits, selector i being bit
+                    // gq[i] of the thread's local bits (gq[i] < 64) or global bit gq[i] - 64 of the tile
 };
 
 // DevOp.pad flag bits
 constexpr uint8_t OPF_FLIP = 1;   // anti-diagonal (1, 1): a pure bit flip
 constexpr uint8_t OPF_TCOND = 2;  // tmask/tval is not empty
 constexpr uint8_t OPF_XCOND = 4;  // xmask/xval is not empty
+
+// In a register phase DevOp.pad holds the op's dispatch word, so one load
+// decides what to do: kind | flags << 4 | rmask << 7 | rval << 12 | coef << 17
+// (OPK_SIGN: the pattern stays in DevOp.coef and the coef field is 0).
+constexpr uint32_t op_code(uint32_t kind, uint32_t flags, uint32_t rmask, uint32_t rval, uint32_t coef) {
+  return kind | (flags << 4) | (rmask << 7) | (rval << 12) | (coef << 17);
+}
+constexpr int kCodeCoefMax = 1 << 15;
 
 constexpr int kMaxTileQ = 14;  // 2^14 amplitudes: 128 KiB (c64) of shared memory
 constexpr int kMaxOps = 96;
@@ -247,6 +258,11 @@ double op_cost(const LOp& op);
 int tile_qubits_for(sv_dtype dtype);
 int low_qubits_for(sv_dtype dtype);
 int reg_qubits_for(int m);  // register qubits of a tile of m qubits (4, or 5 for m >= 13)
+
+// The kernel program of one sweep (sv_program.cpp); rq_override > 0 forces the
+// register qubits of the register phases.
+template <typename R>
+void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq_override = 0);
 
 // ----------------------------------------------------------------- launches
 // (sv_sweep.cu / sv_reduce.cu).  All return cudaError_t of the launch.

@@ -123,10 +123,14 @@ __device__ __forceinline__ void r_u1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf) {
   }
 }
 
-// Real rotation [[C, -S], [S, C]] on register slot S as three shears
-// (a -= t b; b += s a; a -= t b with t = tan(alpha/2), s = sin(alpha)): every
-// step updates one register in place, so no temporaries are needed.
-template <typename R, int RQ, int S>
+// Real rotation [[C, -S], [S, C]] on register slot S.
+//  - float (issue-bound): three in-place shears a -= t b; b += s a; a -= t b
+//    with coef = (t, s) = (tan(alpha/2), sin(alpha)); no temporaries.
+//  - double (FP64-pipe-bound): two FMAs per component in scaled form, the
+//    scale carried by a later phase table: coef.re = t and, with COT clear,
+//    (a, b) -> (a - t b, b + t a) (scale C, t = S/C); with COT set,
+//    (a, b) -> (t a - b, a + t b) (scale S, t = C/S).
+template <typename R, int RQ, int S, bool COT>
 __device__ __forceinline__ void r_rot(Cx<R> (&v)[1 << RQ], Cx<R> ts) {
   constexpr int NR = 1 << RQ;
   const R t = ts.re, sn = ts.im;
@@ -134,13 +138,32 @@ __device__ __forceinline__ void r_rot(Cx<R> (&v)[1 << RQ], Cx<R> ts) {
   for (int j = 0; j < NR; j++) {
     if (j & (1 << S)) continue;
     const int j1 = j | (1 << S);
-    v[j].re = fma(-t, v[j1].re, v[j].re);
-    v[j].im = fma(-t, v[j1].im, v[j].im);
-    v[j1].re = fma(sn, v[j].re, v[j1].re);
-    v[j1].im = fma(sn, v[j].im, v[j1].im);
-    v[j].re = fma(-t, v[j1].re, v[j].re);
-    v[j].im = fma(-t, v[j1].im, v[j].im);
+    if constexpr (sizeof(R) == 4) {
+      v[j].re = fma(-t, v[j1].re, v[j].re);
+      v[j].im = fma(-t, v[j1].im, v[j].im);
+      v[j1].re = fma(sn, v[j].re, v[j1].re);
+      v[j1].im = fma(sn, v[j].im, v[j1].im);
+      v[j].re = fma(-t, v[j1].re, v[j].re);
+      v[j].im = fma(-t, v[j1].im, v[j].im);
+    } else {
+      const Cx<R> a = v[j], b = v[j1];
+      if (COT) {
+        v[j] = {fma(t, a.re, -b.re), fma(t, a.im, -b.im)};
+        v[j1] = {fma(t, b.re, a.re), fma(t, b.im, a.im)};
+      } else {
+        v[j] = {fma(-t, b.re, a.re), fma(-t, b.im, a.im)};
+        v[j1] = {fma(t, a.re, b.re), fma(t, a.im, b.im)};
+      }
+    }
   }
+}
+
+template <typename R, int RQ, int S>
+__device__ __forceinline__ void r_rot_slot(Cx<R> (&v)[1 << RQ], const Cx<R>* cf, uint32_t cot) {
+  if (sizeof(R) == 8 && ((cot >> S) & 1u))
+    r_rot<R, RQ, S, true>(v, cf[S]);
+  else
+    r_rot<R, RQ, S, false>(v, cf[S]);
 }
 
 // Anti-diagonal 2x2 on register slot S: a pure bit flip (X, CNOT) when FLIP,
@@ -281,14 +304,14 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[1 << RQ], const DevOp& op, con
 #endif
 
 template <typename R, int RQ>
-__device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, const Cx<R>* pool, uint32_t tb,
-                                          uint64_t base) {
-  const uint32_t fl = op.pad;
+__device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, uint32_t code, const Cx<R>* pool,
+                                          uint32_t tb, uint64_t base) {
+  const uint32_t fl = (code >> 4) & 7u;
   if ((fl & OPF_XCOND) && (base & op.xmask) != op.xval) return;  // same for the whole block
   if ((fl & OPF_TCOND) && (tb & op.tmask) != op.tval) return;    // same for the thread's amplitudes
-  const Cx<R>* cf = pool + op.coef;
-  const uint32_t rm = op.rmask, rv = op.rval;
-  switch (op.kind) {
+  const Cx<R>* cf = pool + (code >> 17);
+  const uint32_t rm = (code >> 7) & 31u, rv = (code >> 12) & 31u;
+  switch (code & 15u) {
     case OPK_KRON:  // one-qubit gates on distinct slots commute: apply each present block
       // (the fences keep one block's coefficients live at a time)
       if (rm & 1u) r_u1<R, RQ, 0>(v, cf);
@@ -304,31 +327,41 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
       }
       break;
     case OPK_KROT:  // rotations on distinct slots commute
-      if (rm & 1u) r_rot<R, RQ, 0>(v, cf[0]);
+      if (rm & 1u) r_rot_slot<R, RQ, 0>(v, cf, rv);
       SV_KRON_FENCE();
-      if (rm & 2u) r_rot<R, RQ, 1>(v, cf[1]);
+      if (rm & 2u) r_rot_slot<R, RQ, 1>(v, cf, rv);
       SV_KRON_FENCE();
-      if (rm & 4u) r_rot<R, RQ, 2>(v, cf[2]);
+      if (rm & 4u) r_rot_slot<R, RQ, 2>(v, cf, rv);
       SV_KRON_FENCE();
-      if (rm & 8u) r_rot<R, RQ, 3>(v, cf[3]);
+      if (rm & 8u) r_rot_slot<R, RQ, 3>(v, cf, rv);
       if constexpr (RQ > 4) {
         SV_KRON_FENCE();
-        if (rm & 16u) r_rot<R, RQ, 4>(v, cf[4]);
+        if (rm & 16u) r_rot_slot<R, RQ, 4>(v, cf, rv);
       }
       break;
-    case OPK_PHASE:
+    case OPK_PHASE: {
+      // variant of the table picked by the selector bits (thread bits, or
+      // bits outside the tile); variants are 2^RQ + 1 entries apart
+      uint32_t var = 0;
+      for (int i = 0; i < op.k; i++) {
+        const uint32_t c = op.gq[i];
+        const uint32_t b = c < 64 ? (tb >> c) & 1u : (uint32_t)(base >> (c - 64)) & 1u;
+        var |= b << i;
+      }
+      const Cx<R>* T0 = cf + var * ((1u << RQ) + 1u);
 #pragma unroll
       for (int j = 0; j < (1 << RQ); j++) {  // v *= T with one temporary: everything else in place
-        const Cx<R> T = cf[j];
+        const Cx<R> T = T0[j];
         const R t = v[j].im * T.im;
         v[j].im = fma(v[j].re, T.im, v[j].im * T.re);
         v[j].re = fma(v[j].re, T.re, -t);
       }
       break;
+    }
     case OPK_DENSE:
     case OPK_REAL:
       if (op.k == 1) {
-        if (op.kind == OPK_REAL) {
+        if ((code & 15u) == OPK_REAL) {
           SV_SLOT_CASES(r_dense1, true, v, cf, rm, rv)
         } else {
           SV_SLOT_CASES(r_dense1, false, v, cf, rm, rv)
@@ -512,17 +545,26 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, const Cx<R>
         // Sign flips commute with each other: a run of them becomes one mask of
         // the thread's amplitudes to negate, applied before the next other op.
         uint32_t neg = 0;
-        for (int o = ph.first; o < ph.first + ph.nops; o++) {
-          const DevOp& op = P.ops[o];
-          if (op.kind == OPK_SIGN) {  // coef holds the precomputed pattern
-            if ((base & op.xmask) == op.xval && (tb & op.tmask) == op.tval) neg ^= op.coef;
+        // each op's dispatch word is loaded one op ahead, off the critical path
+        const DevOp* ops = P.ops + ph.first;
+        const int nops = ph.nops;
+        uint32_t code_next = nops ? ops[0].pad : 0u;
+        for (int i = 0; i < nops; i++) {
+          const uint32_t code = code_next;
+          if (i + 1 < nops) code_next = ops[i + 1].pad;
+          const DevOp& op = ops[i];
+          if ((code & 15u) == OPK_SIGN) {  // op.coef holds the precomputed pattern
+            bool on = true;
+            if (code & (OPF_XCOND << 4)) on = (base & op.xmask) == op.xval;
+            if (code & (OPF_TCOND << 4)) on = on && (tb & op.tmask) == op.tval;
+            if (on) neg ^= op.coef;
             continue;
           }
           if (neg) {
             apply_neg<R, RQ>(v, neg);
             neg = 0;
           }
-          apply_reg<R, RQ>(v, op, coef, tb, base);
+          apply_reg<R, RQ>(v, op, code, coef, tb, base);
         }
         if (neg) apply_neg<R, RQ>(v, neg);
         reg_store<R, RQ>(v, s, tb, m);
