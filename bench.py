@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--seq-duration", type=float, default=10.0)
+    ap.add_argument("--sweep-rates", type=str, default="25,50,100,200",
+                    help="serving: extra sub-saturation rates (req/s), each run for --sweep-duration s")
+    ap.add_argument("--sweep-duration", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -279,10 +282,37 @@ def bench_adjoint(args):
         "kernels": prof}), flush=True)
 
 
+def serving_cpu_baseline(stream, served, budget_s=15.0):
+    """The oracle on the host cores, one request after another, over the
+    leading requests of the same stream (up to ~budget_s of CPU work, n <= 18
+    so each fits the oracle quickly); also reports how far the served results
+    of those requests are from the oracle's."""
+    import numpy as np
+    import oracle
+    from workloads import serving_circuit
+    done = {r.rid: r for r in served if r.result is not None}
+    t0 = time.perf_counter()
+    n_req, worst = 0, 0.0
+    for rid, (_, n, depth, seed) in enumerate(stream):
+        if n > 18:
+            continue
+        _, zsum = oracle.expect_z_all(oracle.run(n, serving_circuit(n, depth, seed)), n)
+        n_req += 1
+        if rid in done:
+            worst = max(worst, abs(done[rid].result - zsum))
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": n_req / t, "unit": "req/s", "cores": oracle.n_threads(), "kind": "oracle",
+            "sample": "the first %d requests with n <= 18 of the stream, one at a time (%.1f s)" % (n_req, t),
+            "max_abs_diff_vs_served": worst}
+
+
 def bench_serving(args):
     """Poisson arrivals (default 2000 req/s for 60 s) of layered U3 + CNOT
     ladder circuits, n uniform 8..26, depth 5..40, sum <Z_i> each, complex64,
-    150 GB admission budget; against one request at a time."""
+    150 GB admission budget; against one request at a time, plus a sweep of
+    sub-saturation rates."""
     import paper_2608_09733_gb300 as sv
     from paper_2608_09733_gb300.serving import Server, run_sequential
     from workloads import serving_stream
@@ -290,15 +320,25 @@ def bench_serving(args):
     warm = serving_stream(rate=200.0, duration=0.2, seed=99)
     srv = Server(sv.SV_C64, budget_bytes=150e9)
     srv.run(warm)
-    stats, _ = srv.run(stream, time_limit=args.duration + 30.0)
+    stats, reqs = srv.run(stream, time_limit=args.duration + 30.0)
     seq_stream = [r for r in stream if r[0] < args.seq_duration]
     seq, _ = run_sequential(seq_stream, sv.SV_C64, time_limit=args.seq_duration + 30.0)
-    print(json.dumps({
+    sweep = []
+    for rate in [float(x) for x in args.sweep_rates.split(",") if x.strip()]:
+        st = serving_stream(rate=rate, duration=args.sweep_duration, seed=1)
+        s_stats, _ = Server(sv.SV_C64, budget_bytes=150e9).run(st, time_limit=args.sweep_duration + 60.0)
+        d = s_stats.as_dict()
+        sweep.append({"rate": rate, **{k: d[k] for k in ("offered", "completed", "rejected", "unfinished",
+                                                           "req_per_s", "p50_ms", "p99_ms")}})
+    line = {
         "metric": "serving req/s + p99 (Poisson %.0f req/s, n 8-26, depth 5-40, c64)" % args.rate,
         "value": stats.req_per_s, "unit": "req/s", "n_gpus": 1, "higher_is_better": True, "dtype": "c64",
         "data": "synthetic", "config": {"workload": "serving_poisson_%.0fhz_%.0fs" % (args.rate, args.duration),
                                         "budget_gb": 150},
-        "served": stats.as_dict(), "sequential": seq.as_dict()}), flush=True)
+        "served": stats.as_dict(), "sequential": seq.as_dict(), "rate_sweep": sweep}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = serving_cpu_baseline(stream, reqs)
+    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ our arm

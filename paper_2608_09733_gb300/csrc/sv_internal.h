@@ -269,8 +269,6 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
 
 template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream);
-// True (once) if a pass kernel gave up waiting for its tile copies since the last call.
-bool sweep_timed_out();
 template <typename R>
 cudaError_t launch_init_basis(Cx<R>* state, int n, uint64_t index, cudaStream_t stream);
 // One CTA per small request (whole state in shared memory): request b runs

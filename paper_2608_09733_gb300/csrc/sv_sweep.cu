@@ -20,11 +20,7 @@
 // phase, with an XOR swizzle of 16-byte granules so the strided register
 // groups do not collide in banks.  Dense k >= 3 operations (the paper's fused
 // blocks) run group by group straight in shared memory.
-#include <cuda.h>
 #include <cuda_runtime.h>
-
-#include <cstring>
-#include <mutex>
 
 #include "sv_internal.h"
 
@@ -303,7 +299,13 @@ __device__ __forceinline__ void r_diag(Cx<R> (&v)[1 << RQ], const DevOp& op, con
 #define SV_KRON_FENCE() ((void)0)
 #endif
 
-template <typename R, int RQ>
+// Op sets a pass kernel is compiled for: the code of op kinds a program never
+// uses still costs registers and moves, so the launch picks the smallest set.
+constexpr int kOpsRot = 0;   // KROT, PHASE (and sign flips)
+constexpr int kOpsPerm = 1;  // + anti-diagonal (X, CNOT ...) and SWAP
+constexpr int kOpsAll = 2;   // + KRON, dense/real k <= 2, general diagonals
+
+template <typename R, int RQ, int OPS>
 __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, uint32_t code, const Cx<R>* pool,
                                           uint32_t tb, uint64_t base) {
   const uint32_t fl = (code >> 4) & 7u;
@@ -314,6 +316,7 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
   switch (code & 15u) {
     case OPK_KRON:  // one-qubit gates on distinct slots commute: apply each present block
       // (the fences keep one block's coefficients live at a time)
+      if constexpr (OPS >= kOpsAll) {
       if (rm & 1u) r_u1<R, RQ, 0>(v, cf);
       SV_KRON_FENCE();
       if (rm & 2u) r_u1<R, RQ, 1>(v, cf + 4);
@@ -324,6 +327,7 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
       if constexpr (RQ > 4) {
         SV_KRON_FENCE();
         if (rm & 16u) r_u1<R, RQ, 4>(v, cf + 16);
+      }
       }
       break;
     case OPK_KROT:  // rotations on distinct slots commute
@@ -360,6 +364,7 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
     }
     case OPK_DENSE:
     case OPK_REAL:
+      if constexpr (OPS >= kOpsAll) {
       if (op.k == 1) {
         if ((code & 15u) == OPK_REAL) {
           SV_SLOT_CASES(r_dense1, true, v, cf, rm, rv)
@@ -369,16 +374,23 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
       } else {
         SV_PAIR_CASES(r_dense2, v, cf, rm, rv)
       }
+      }
       break;
     case OPK_ANTIDIAG:
+      if constexpr (OPS >= kOpsPerm) {
       if (fl & OPF_FLIP) {  // pure bit flip (X, CNOT): no multiplies
         SV_SLOT_CASES(r_anti1, true, v, cf, rm, rv)
       } else {
         SV_SLOT_CASES(r_anti1, false, v, cf, rm, rv)
       }
+      }
       break;
-    case OPK_SWAP: SV_PAIR_CASES(r_swap, v, rm, rv) break;
-    case OPK_DIAG: r_diag<R, RQ>(v, op, cf, tb, base); break;
+    case OPK_SWAP:
+      if constexpr (OPS >= kOpsPerm) { SV_PAIR_CASES(r_swap, v, rm, rv) }
+      break;
+    case OPK_DIAG:
+      if constexpr (OPS >= kOpsAll) r_diag<R, RQ>(v, op, cf, tb, base);
+      break;
     default: break;
   }
 }
@@ -523,7 +535,7 @@ __device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const
 // Runs every phase of a program on a tile that is already in shared memory.
 // KMAX: widest dense operation the program runs in shared memory; RQ: the
 // register qubits of its register phases.
-template <typename R, int KMAX, int RQ>
+template <typename R, int KMAX, int RQ, int OPS>
 __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, const Cx<R>* coef, Cx<R>* s, int tsz,
                                            uint64_t base) {
   const ProgramHeader& h = P.h;
@@ -564,7 +576,7 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, const Cx<R>
             apply_neg<R, RQ>(v, neg);
             neg = 0;
           }
-          apply_reg<R, RQ>(v, op, code, coef, tb, base);
+          apply_reg<R, RQ, OPS>(v, op, code, coef, tb, base);
         }
         if (neg) apply_neg<R, RQ>(v, neg);
         reg_store<R, RQ>(v, s, tb, m);
@@ -625,7 +637,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // behind the arithmetic.  Without DBUF (tiles too large for two buffers) the
 // copies of a tile are waited for before it runs.  Each tile is scattered back
 // with 16-byte stores.
-template <typename R, int KMAX, int RQ, bool DBUF>
+template <typename R, int KMAX, int RQ, bool DBUF, int OPS>
 __global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
                                   sizeof(R) == 4 ? (RQ == 5 ? SV_RQ5_MINB : SV_SWEEP_MIN_BLOCKS) : 1)
     k_sweep(Cx<R>* __restrict__ state, const __grid_constant__ SweepProgram<R> P) {
@@ -676,7 +688,7 @@ __global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
     }
     __syncthreads();  // ... and every thread's
     Cx<R>* s = buf[cur];
-    run_phases<R, KMAX, RQ>(P, scoef, s, tsz, base);
+    run_phases<R, KMAX, RQ, OPS>(P, scoef, s, tsz, base);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const uint32_t l = (uint32_t)(v * A);
       *reinterpret_cast<uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask)))) =
@@ -684,133 +696,6 @@ __global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
     }
     __syncthreads();  // the buffer is free for the next copies
   }
-}
-
-// ---------------------------------------------------------------- TMA tiles
-//
-// The tile gather and scatter as tensor copies.  The state is described to the
-// copy engine as a 5-D tensor whose dimension d holds the amplitude bits
-// lo[d] .. lo[d] + width[d] - 1 (dimension 0: the lowest 16 elements, 128
-// bytes).  Each dimension's range starts at a run of consecutive tile qubits,
-// which its box covers; tile qubits above the fourth run are "enumerated": one
-// copy per value of those bits, all of them inside the last dimension's range.
-// The copy engine's 128-byte swizzle XORs the 16-byte chunk index with bits
-// 7..9 of the shared-memory address, which is exactly the layout phys<R>()
-// describes for a 1024-byte aligned tile, so the register phases run unchanged.
-// Every wait is bounded: after about two seconds a thread gives up, records the
-// timeout in *err and leaves the kernel.
-struct TmaGeom {
-  int32_t lo[5];      // first amplitude bit of each dimension (lo[0] = 0)
-  int32_t width[5];   // amplitude bits of each dimension's range (0: a padding dimension)
-  int32_t ebit[8];    // enumerated tile qubits: bit offset inside dimension `last`
-  int32_t nenum;      // number of enumerated tile qubits (copies per tile = 2^nenum)
-  int32_t last;       // the dimension that holds the enumerated bits
-  int32_t box_amps;   // amplitudes per copy
-  int32_t tile_bytes;
-};
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for phase `parity` of the barrier for at most ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (globaltimer_ns() - t0 > 2000000000ull) return false;
-  return true;
-}
-
-template <typename R, int KMAX, int RQ>
-__global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
-                                  sizeof(R) == 4 ? (RQ == 5 ? SV_RQ5_MINB : SV_SWEEP_MIN_BLOCKS) : 1)
-    k_sweep_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepProgram<R> P,
-                const __grid_constant__ TmaGeom g, unsigned* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long bar_storage;
-  const ProgramHeader& h = P.h;
-  const int tsz = 1 << h.m;
-  const uint32_t raw_sa = (uint32_t)__cvta_generic_to_shared(smem_raw);
-  const uint32_t pad = (1024u - (raw_sa & 1023u)) & 1023u;
-  Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw + pad);  // 1024-byte aligned tile
-  const uint32_t s_sa = raw_sa + pad;
-  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_storage);
-  const uint64_t tmap_addr = reinterpret_cast<uint64_t>(&tmap);
-  const uint64_t ntiles = 1ull << (h.n - h.m);
-  const int ncopy = 1 << g.nenum;
-  const uint32_t box_bytes = (uint32_t)g.box_amps * (uint32_t)sizeof(Cx<R>);
-  Cx<R>* scoef = s + tsz;  // the coefficient pool, staged once per CTA
-  for (int c = threadIdx.x; c < h.ncoef; c += blockDim.x) scoef[c] = P.coef[c];
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
-  // box origin of copy e of the tile whose outside bits are `base`
-  auto coords = [&](uint64_t base, int e, int (&c)[5]) {
-    c[0] = 0;
-#pragma unroll
-    for (int d = 1; d < 5; d++)
-      c[d] = g.width[d] ? (int)((base >> g.lo[d]) & ((1ull << g.width[d]) - 1ull)) : 0;
-    for (int i = 0; i < g.nenum; i++)
-      if ((e >> i) & 1) c[g.last] |= 1 << g.ebit[i];
-  };
-  uint32_t parity = 0;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    uint64_t base = tile;
-    for (int i = 0; i < h.m; i++) base = ins0_64(base, h.tq[i]);
-    if (threadIdx.x == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(g.tile_bytes) : "memory");
-      for (int e = 0; e < ncopy; e++) {
-        int c[5];
-        coords(base, e, c);
-        asm volatile(
-            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-            "%5, %6}], [%7];" ::"r"(s_sa + (uint32_t)e * box_bytes),
-            "l"(tmap_addr), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(bar)
-            : "memory");
-      }
-    }
-    if (!mbar_wait_bounded(bar, parity)) {
-      atomicOr(err, 1u);
-      mbar_wait_bounded(bar, parity);  // give the copies in flight one more chance to land
-      return;
-    }
-    parity ^= 1u;
-    run_phases<R, KMAX, RQ>(P, scoef, s, tsz, base);
-    // the threads' shared-memory writes must be visible to the copy engine
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int e = 0; e < ncopy; e++) {
-        int c[5];
-        coords(base, e, c);
-        asm volatile(
-            "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
-                tmap_addr),
-            "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(s_sa + (uint32_t)e * box_bytes)
-            : "memory");
-      }
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the tile buffer may be refilled
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Packed small states (serving): CTA b simulates request b entirely in shared
@@ -830,7 +715,7 @@ __global__ void __launch_bounds__(256) k_small_batch(const SweepProgram<R>* __re
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) s[phys<R>(a)] = Cx<R>{R(a == 0 ? 1 : 0), R(0)};
   __syncthreads();
   for (int p = first_prog[b]; p < first_prog[b + 1]; p++)
-    run_phases<R, 5, kRegQ>(progs[p], progs[p].coef, s, tsz, 0ull);
+    run_phases<R, 5, kRegQ, kOpsAll>(progs[p], progs[p].coef, s, tsz, 0ull);
   double acc = 0.0;
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
     const Cx<R> x = s[phys<R>(a)];
@@ -870,7 +755,7 @@ int sweep_threads(int m, int rq) {
   return t > 256 ? 256 : t;
 }
 
-template <typename R, int KMAX, int RQ, bool DBUF>
+template <typename R, int KMAX, int RQ, bool DBUF, int OPS>
 static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
   const int smem = ((int)sizeof(Cx<R>) << (prog.h.m + (DBUF ? 1 : 0))) + (8 << (prog.h.m - prog.h.L)) +
                    (int)sizeof(Cx<R>) * prog.h.ncoef;
@@ -881,210 +766,56 @@ static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cud
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (smem > 48 * 1024 && smem > configured_bytes[dev]) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_sweep<R, KMAX, RQ, DBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_sweep<R, KMAX, RQ, DBUF, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured_bytes[dev] = smem;
   }
   const int threads = sweep_threads(prog.h.m, RQ);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX, RQ, DBUF>, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX, RQ, DBUF, OPS>, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
   uint64_t grid = (uint64_t)device_sm_count() * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_sweep<R, KMAX, RQ, DBUF><<<(unsigned)grid, threads, smem, stream>>>(state, prog);
+  k_sweep<R, KMAX, RQ, DBUF, OPS><<<(unsigned)grid, threads, smem, stream>>>(state, prog);
   return cudaGetLastError();
 }
 
 template <typename R, int RQ, bool DBUF>
 static cudaError_t launch_sweep_rq(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
   int kmax = 1;
+  bool perm = false, other = false;
   for (int p = 0; p < prog.h.nphases; p++) {
     const Phase& ph = prog.ph[p];
-    if (ph.kind != PH_SMEM) continue;
+    if (ph.kind != PH_SMEM) {
+      for (int o = ph.first; o < ph.first + ph.nops; o++) {
+        const uint32_t kind = prog.ops[o].pad & 15u;
+        if (kind == OPK_ANTIDIAG || kind == OPK_SWAP)
+          perm = true;
+        else if (kind != OPK_KROT && kind != OPK_PHASE && kind != OPK_SIGN)
+          other = true;
+      }
+      continue;
+    }
     const DevOp& op = prog.ops[ph.first];
     if ((op.kind == OPK_DENSE || op.kind == OPK_REAL) && op.k > kmax) kmax = op.k;
   }
-  if (kmax <= 2) return launch_sweep_k<R, 2, RQ, DBUF>(state, prog, stream);
-  if (kmax == 3) return launch_sweep_k<R, 3, RQ, DBUF>(state, prog, stream);
-  return launch_sweep_k<R, 5, RQ, DBUF>(state, prog, stream);
-}
-
-// ---------------------------------------------------------------- TMA launch
-
-#ifndef SV_SWEEP_TMA
-#define SV_SWEEP_TMA 0
-#endif
-
-namespace {
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_tiled_fn() {
-  static EncodeTiledFn fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      return (EncodeTiledFn) nullptr;
-    }
-    return (EncodeTiledFn)p;
-  }();
-  return fn;
-}
-
-unsigned* g_err_host = nullptr;  // mapped pinned flag the pass kernels set on a timed-out wait
-unsigned* g_err_dev = nullptr;
-
-unsigned* error_flag_dev() {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* h = nullptr;
-    if (cudaHostAlloc(&h, sizeof(unsigned), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
-    void* d = nullptr;
-    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFreeHost(h);
-      return;
-    }
-    g_err_host = (unsigned*)h;
-    *g_err_host = 0;
-    g_err_dev = (unsigned*)d;
-  });
-  return g_err_dev;
-}
-
-// Tensor description of the state for one pass's tile qubits; false if the
-// tile does not fit the scheme (small states).
-template <typename R>
-bool make_tma_geom(const ProgramHeader& h, Cx<R>* state, CUtensorMap* map, TmaGeom* g) {
-  EncodeTiledFn enc = encode_tiled_fn();
-  if (!enc) return false;
-  const int eb = sizeof(Cx<R>) == 16 ? 1 : 0;  // element bits per amplitude (8-byte elements)
-  const int b0 = 4 - eb;                        // amplitude bits of dimension 0 (128 bytes)
-  if (h.n < 16 || h.m < b0 + 1 || h.L < b0 + 1) return false;
-  std::memset(g, 0, sizeof(*g));
-  // runs of consecutive tile qubits from bit b0, at most 8 bits each (box limit 256)
-  int run_first[kMaxTileQ], run_len[kMaxTileQ], nrun = 0;
-  for (int i = b0; i < h.m; i++) {
-    const int q = h.tq[i];
-    if (nrun && q == run_first[nrun - 1] + run_len[nrun - 1] && run_len[nrun - 1] < 8) {
-      run_len[nrun - 1]++;
-    } else {
-      run_first[nrun] = q;
-      run_len[nrun] = 1;
-      nrun++;
-    }
+  if (kmax <= 2 && !other) {
+    if (!perm) return launch_sweep_k<R, 2, RQ, DBUF, kOpsRot>(state, prog, stream);
+    return launch_sweep_k<R, 2, RQ, DBUF, kOpsPerm>(state, prog, stream);
   }
-  const int D = nrun < 4 ? nrun : 4;
-  cuuint64_t gdim[5], gstride[4];
-  cuuint32_t box[5], estride[5] = {1, 1, 1, 1, 1};
-  gdim[0] = 16;
-  box[0] = 16;
-  g->lo[0] = 0;
-  g->width[0] = b0;
-  int box_bits = b0;
-  for (int d = 1; d <= 4; d++) {
-    if (d <= D) {
-      g->lo[d] = run_first[d - 1];
-      g->width[d] = (d < D ? run_first[d] : h.n) - run_first[d - 1];
-      gdim[d] = 1ull << g->width[d];
-      box[d] = 1u << run_len[d - 1];
-      box_bits += run_len[d - 1];
-      gstride[d - 1] = (cuuint64_t)sizeof(Cx<R>) << g->lo[d];
-    } else {  // padding dimension of one element
-      g->lo[d] = h.n;
-      g->width[d] = 0;
-      gdim[d] = 1;
-      box[d] = 1;
-      gstride[d - 1] = (cuuint64_t)sizeof(Cx<R>) << h.n;
-    }
-  }
-  g->last = D;
-  g->nenum = 0;
-  for (int r = D; r < nrun; r++)
-    for (int b = 0; b < run_len[r]; b++) {
-      if (g->nenum >= 8) return false;
-      g->ebit[g->nenum++] = run_first[r] + b - g->lo[D];
-    }
-  if (box_bits + g->nenum != h.m) return false;
-  g->box_amps = 1 << box_bits;
-  g->tile_bytes = (int)(sizeof(Cx<R>) << h.m);
-  if (g->box_amps * (int)sizeof(Cx<R>) < 1024) return false;  // copies stay 1024-byte aligned
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, (void*)state, gdim, gstride, box, estride,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
-template <typename R, int KMAX, int RQ>
-cudaError_t launch_sweep_tma_k(const CUtensorMap& map, const TmaGeom& g, const SweepProgram<R>& prog,
-                               cudaStream_t stream) {
-  const int smem = (int)(sizeof(Cx<R>) << prog.h.m) + 1024 + (int)sizeof(Cx<R>) * prog.h.ncoef;
-  static int configured_bytes[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (smem > 48 * 1024 && smem > configured_bytes[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_tma<R, KMAX, RQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured_bytes[dev] = smem;
-  }
-  unsigned* err = error_flag_dev();
-  if (!err) return cudaErrorMemoryAllocation;
-  const int threads = sweep_threads(prog.h.m, RQ);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_tma<R, KMAX, RQ>, threads, smem);
-  if (per_sm < 1) per_sm = 1;
-  const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
-  uint64_t grid = (uint64_t)device_sm_count() * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  k_sweep_tma<R, KMAX, RQ><<<(unsigned)grid, threads, smem, stream>>>(map, prog, g, err);
-  return cudaGetLastError();
-}
-
-template <typename R, int RQ>
-cudaError_t launch_sweep_tma_rq(const CUtensorMap& map, const TmaGeom& g, const SweepProgram<R>& prog,
-                                cudaStream_t stream) {
-  int kmax = 1;
-  for (int p = 0; p < prog.h.nphases; p++) {
-    const Phase& ph = prog.ph[p];
-    if (ph.kind != PH_SMEM) continue;
-    const DevOp& op = prog.ops[ph.first];
-    if ((op.kind == OPK_DENSE || op.kind == OPK_REAL) && op.k > kmax) kmax = op.k;
-  }
-  if (kmax <= 2) return launch_sweep_tma_k<R, 2, RQ>(map, g, prog, stream);
-  if (kmax == 3) return launch_sweep_tma_k<R, 3, RQ>(map, g, prog, stream);
-  return launch_sweep_tma_k<R, 5, RQ>(map, g, prog, stream);
-}
-
-}  // namespace
-
-bool sweep_timed_out() {
-  if (g_err_host && *(volatile unsigned*)g_err_host) {
-    *(volatile unsigned*)g_err_host = 0;
-    return true;
-  }
-  return false;
+  if (kmax <= 2) return launch_sweep_k<R, 2, RQ, DBUF, kOpsAll>(state, prog, stream);
+  if (kmax == 3) return launch_sweep_k<R, 3, RQ, DBUF, kOpsAll>(state, prog, stream);
+  return launch_sweep_k<R, 5, RQ, DBUF, kOpsAll>(state, prog, stream);
 }
 
 template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
-  if (SV_SWEEP_TMA) {
-    CUtensorMap map;
-    TmaGeom g;
-    if (make_tma_geom<R>(prog.h, state, &map, &g)) {
-      if (prog.h.rq == 5) return launch_sweep_tma_rq<R, 5>(map, g, prog, stream);
-      return launch_sweep_tma_rq<R, 4>(map, g, prog, stream);
-    }
-  }
-  // four register qubits with two tile buffers, or five with one (large tiles)
-  if (prog.h.rq == 5) return launch_sweep_rq<R, 5, SV_RQ5_DBUF>(state, prog, stream);
+  // four register qubits with two tile buffers, or five with one (13-qubit
+  // complex64 tiles; complex128 tiles have 11 qubits)
+  if constexpr (sizeof(R) == 4)
+    if (prog.h.rq == 5) return launch_sweep_rq<R, 5, SV_RQ5_DBUF>(state, prog, stream);
+  if (prog.h.rq != 4) return cudaErrorInvalidValue;
   return launch_sweep_rq<R, 4, true>(state, prog, stream);
 }
 
