@@ -371,7 +371,7 @@ def main():
 
     _build.build()
     sv.load()
-    stamp = _build._stamp()
+    stamp = _build.sweep_stamp()
     n, dt = args.n, (sv.SV_C64 if args.dtype == "c64" else sv.SV_C128)
     amp = 8 if dt == sv.SV_C64 else 16
     tdt = torch.complex64 if dt == sv.SV_C64 else torch.complex128

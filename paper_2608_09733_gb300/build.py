@@ -51,6 +51,22 @@ def _stamp(extra=()) -> str:
     return h.hexdigest()
 
 
+# Sources that decide what the pass kernel does (the kernel, the program
+# builder, the planner and the shared structures).
+SWEEP_SOURCES = ["sv_sweep.cu", "sv_program.cpp", "sv_plan.cpp", "sv_internal.h"]
+
+
+def sweep_stamp() -> str:
+    """Hash of the pass kernel's sources and flags: ncu counters recorded
+    for one stamp say nothing about another."""
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT, exist_ok=True)
     stamp_file = os.path.join(OUT, "libsv.stamp")
