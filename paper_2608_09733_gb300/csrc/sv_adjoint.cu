@@ -16,6 +16,10 @@
 // a fixed order by a second kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "sv_internal.h"
 
 namespace sv {
@@ -377,9 +381,103 @@ __device__ __forceinline__ void b_diag(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp
   }
 }
 
+// Uncontrolled one-qubit op on register slot S, with the structure of the
+// common rotations written out: REAL matrices (RY, H ...) take real products,
+// and the gradient term Im <lambda|G|psi> of an X or Y generator (RX, RY) is
+// read off the pair directly (GK = 1: X, 2: Y; 0: no gradient).
+template <typename R, int S, bool REV, bool REAL, int GK>
+__device__ __forceinline__ void b_u1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M, R& acc) {
+  const bool dag = op.dagger;
+  const Cx<R> u00 = uel<R, 2>(M, 0, 0, dag), u01 = uel<R, 2>(M, 0, 1, dag);
+  const Cx<R> u10 = uel<R, 2>(M, 1, 0, dag), u11 = uel<R, 2>(M, 1, 1, dag);
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if (j & (1 << S)) continue;
+    const int j1 = j | (1 << S);
+    const Cx<R> a = p[j], b = p[j1];
+    if (REV && GK == 1) {  // (X psi) = (b, a)
+      acc += im_cdot(l[j], b) + im_cdot(l[j1], a);
+    } else if (REV && GK == 2) {  // (Y psi) = (-i b, i a)
+      acc += (l[j1].re * a.re + l[j1].im * a.im) - (l[j].re * b.re + l[j].im * b.im);
+    }
+    if (REAL) {
+      p[j] = {fma(u00.re, a.re, u01.re * b.re), fma(u00.re, a.im, u01.re * b.im)};
+      p[j1] = {fma(u10.re, a.re, u11.re * b.re), fma(u10.re, a.im, u11.re * b.im)};
+    } else {
+      p[j] = cfma(u01, b, cmul(u00, a));
+      p[j1] = cfma(u11, b, cmul(u10, a));
+    }
+    if (REV) {
+      const Cx<R> c = l[j], d = l[j1];
+      if (REAL) {
+        l[j] = {fma(u00.re, c.re, u01.re * d.re), fma(u00.re, c.im, u01.re * d.im)};
+        l[j1] = {fma(u10.re, c.re, u11.re * d.re), fma(u10.re, c.im, u11.re * d.im)};
+      } else {
+        l[j] = cfma(u01, d, cmul(u00, c));
+        l[j1] = cfma(u11, d, cmul(u10, c));
+      }
+    }
+  }
+}
+
+// Uncontrolled one-qubit diagonal on register slot S (RZ, S, T ...); with GZ
+// the gradient term of a Z generator, sum of +-Im(conj(lambda) psi).
+template <typename R, int S, bool REV, bool GZ>
+__device__ __forceinline__ void b_d1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M, R& acc) {
+  const bool dag = op.dagger;
+  const Cx<R> f0 = dag ? conjx(M[0]) : M[0], f1 = dag ? conjx(M[1]) : M[1];
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    const bool one = (j >> S) & 1;
+    if (REV && GZ) acc += one ? -im_cdot(l[j], p[j]) : im_cdot(l[j], p[j]);
+    p[j] = cmul(one ? f1 : f0, p[j]);
+    if (REV) l[j] = cmul(one ? f1 : f0, l[j]);
+  }
+}
+
+// F<R, slot, rest...>(args) for the op's register slot; the last macro
+// argument closes the template list and carries the call.
+#define SV_SLOT4(F, ...)                    \
+  switch (op.rs[0]) {                       \
+    case 0: F<R, 0, __VA_ARGS__; break;     \
+    case 1: F<R, 1, __VA_ARGS__; break;     \
+    case 2: F<R, 2, __VA_ARGS__; break;     \
+    default: F<R, 3, __VA_ARGS__; break;    \
+  }
+
 template <typename R, bool REV>
 __device__ __forceinline__ void b_apply(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
                                         const Cx<R>* G, uint32_t tb, uint64_t base, R& acc) {
+  const bool plain = op.rmask == 0 && op.rs[0] != 0xFF;  // uncontrolled, on a register slot
+  if (plain && op.k == 1 && (op.kind == OPK_DENSE || op.kind == OPK_REAL)) {
+    const bool real = op.flags & OPF_REALM;
+    const int gk = !(REV && op.grad) ? 0 : (op.flags & OPF_GX) ? 1 : (op.flags & OPF_GY) ? 2 : 3;
+    if (gk != 3) {
+      if (real && gk == 2) {
+        SV_SLOT4(b_u1, REV, true, 2>(p, l, op, M, acc))
+      } else if (real && gk == 0) {
+        SV_SLOT4(b_u1, REV, true, 0>(p, l, op, M, acc))
+      } else if (gk == 1) {
+        SV_SLOT4(b_u1, REV, false, 1>(p, l, op, M, acc))
+      } else if (gk == 0) {
+        SV_SLOT4(b_u1, REV, false, 0>(p, l, op, M, acc))
+      } else {
+        SV_SLOT4(b_u1, REV, false, 2>(p, l, op, M, acc))
+      }
+      return;
+    }
+  }
+  if (plain && op.k == 1 && op.kind == OPK_DIAG) {
+    const bool gz = REV && op.grad && (op.flags & OPF_GZ);
+    if (gz || !(REV && op.grad)) {
+      if (gz) {
+        SV_SLOT4(b_d1, REV, true>(p, l, op, M, acc))
+      } else {
+        SV_SLOT4(b_d1, REV, false>(p, l, op, M, acc))
+      }
+      return;
+    }
+  }
   switch (op.kind) {
     case OPK_DENSE:
     case OPK_REAL:
@@ -433,7 +531,7 @@ __device__ __forceinline__ void b_apply(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BO
 }
 
 template <typename R, bool REV>
-__global__ void __launch_bounds__(256) k_batch_sweep(Cx<R>* __restrict__ psi, Cx<R>* __restrict__ lam,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_sweep(Cx<R>* __restrict__ psi, Cx<R>* __restrict__ lam,
                                                      const Cx<R>* __restrict__ table, double* __restrict__ gscratch,
                                                      const __grid_constant__ BatchProgram<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -617,6 +715,84 @@ __global__ void __launch_bounds__(256) k_pauli_accum(const Cx<R>* __restrict__ p
   }
 }
 
+// lam (+)= H psi for the X-masks whose qubits all lie in one tile: the tile of
+// psi is gathered into shared memory, and each amplitude sums, over the pass's
+// terms, c_j i^{nY_j} (-1)^{popc(src & z_j)} psi[src] with src = b ^ x_j
+// (Sec. 4.4: P|b> = i^{nY} (-1)^{popc(b & z)} |b ^ x>).  Terms are sorted by
+// x, so each partner amplitude is read once per distinct x.
+constexpr int kPauliTileTerms = 96;
+struct PauliTilePass {
+  int32_t n, m, L, nterms;
+  int32_t accumulate, pad;
+  int8_t tq[16];                      // tile qubits, ascending; tq[i] = i for i < L
+  uint32_t xl[kPauliTileTerms];       // x in local tile bits
+  uint64_t xg[kPauliTileTerms];       // x in global bits
+  uint64_t z[kPauliTileTerms];
+  double cr[kPauliTileTerms], ci[kPauliTileTerms];  // c_j i^{nY_j}
+};
+
+// The pass's coefficients in the state's precision (FP64 is a slow pipe on
+// GB300), staged in shared memory by the kernel.
+template <typename R>
+struct PauliTileCoef {
+  R cr, ci;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ psi, Cx<R>* __restrict__ lam,
+                                                     const __grid_constant__ PauliTilePass P, uint64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
+  const int tsz = 1 << P.m;
+  uint64_t* hi_off = reinterpret_cast<uint64_t*>(s + tsz);
+  const int nhi = 1 << (P.m - P.L);
+  __shared__ PauliTileCoef<R> cf[kPauliTileTerms];
+  for (int c = threadIdx.x; c < nhi; c += blockDim.x) {
+    uint64_t off = 0;
+    for (int i = P.L; i < P.m; i++)
+      if (((uint32_t)c >> (i - P.L)) & 1u) off |= 1ull << P.tq[i];
+    hi_off[c] = off;
+  }
+  for (int j = threadIdx.x; j < P.nterms; j += blockDim.x) cf[j] = {(R)P.cr[j], (R)P.ci[j]};
+  __syncthreads();
+  const uint32_t lowmask = (1u << P.L) - 1u;
+  const int per_state_log = P.n - P.m;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t b = tile >> per_state_log;
+    uint64_t base = tile & ((1ull << per_state_log) - 1ull);
+    for (int i = 0; i < P.m; i++) base = ins0_64(base, P.tq[i]);
+    const uint64_t sbase = b << P.n;
+    for (int l = threadIdx.x; l < tsz; l += blockDim.x)
+      s[l] = psi[sbase + (base | hi_off[l >> P.L] | (l & lowmask))];
+    __syncthreads();
+    for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
+      const uint64_t g = base | hi_off[l >> P.L] | (l & lowmask);
+      R ar = R(0), ai = R(0);
+      for (int j = 0; j < P.nterms;) {
+        const uint32_t xl = P.xl[j];
+        const uint64_t src = g ^ P.xg[j];
+        R fr = R(0), fi = R(0);
+        for (; j < P.nterms && P.xl[j] == xl; j++) {
+          const bool neg = __popcll(src & P.z[j]) & 1;
+          fr += neg ? -cf[j].cr : cf[j].cr;
+          fi += neg ? -cf[j].ci : cf[j].ci;
+        }
+        const Cx<R> v = s[l ^ xl];
+        ar = fma(fr, v.re, fma(-fi, v.im, ar));
+        ai = fma(fr, v.im, fma(fi, v.re, ai));
+      }
+      Cx<R>* o = lam + sbase + g;
+      if (P.accumulate) {
+        const Cx<R> w = *o;
+        ar += w.re;
+        ai += w.im;
+      }
+      *o = Cx<R>{ar, ai};
+    }
+    __syncthreads();
+  }
+}
+
 constexpr int kDotThreads = 256;
 constexpr int kDotGridX = 16;
 
@@ -723,6 +899,115 @@ cudaError_t launch_pauli_accum(const Cx<R>* psi, Cx<R>* lam, int n, int batch, u
   return cudaSuccess;
 }
 
+// lam (+)= sum_j c_j P_j psi: the X-masks are covered greedily by tiles of m
+// qubits that always hold the lowest L (coalesced runs); all terms whose x
+// lies in a tile are applied in that tile's pass.  Masks no tile can hold
+// fall back to one pass per mask (launch_pauli_accum).
+template <typename R>
+cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, const sv_pauli_term* terms,
+                               int nterms, bool accumulate, cudaStream_t stream) {
+  const int L = std::min(n, sizeof(R) == 4 ? 5 : 4);
+  const int m = std::min(n, sizeof(R) == 4 ? 13 : 12);  // 64 KiB tiles
+  std::vector<int> idx(nterms);
+  for (int t = 0; t < nterms; t++) idx[t] = t;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return terms[a].x_mask < terms[b].x_mask; });
+  const uint64_t low = (1ull << L) - 1ull;
+  std::vector<char> done(nterms, 0);
+  bool acc = accumulate;
+  int remaining = nterms;
+  while (remaining > 0) {
+    // tile qubits: the low L, then the qubits of uncovered masks that fit
+    uint64_t T = low;
+    for (int t : idx) {
+      if (done[t]) continue;
+      const uint64_t u = T | terms[t].x_mask;
+      if (__builtin_popcountll(u) <= m) T = u;
+    }
+    bool any = false;
+    for (int t : idx)
+      if (!done[t] && (terms[t].x_mask & ~T) == 0) any = true;
+    if (!any) break;  // the rest need wider tiles
+    for (int q = 0; q < n && __builtin_popcountll(T) < m; q++) T |= 1ull << q;
+    PauliTilePass P;
+    std::memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.m = m;
+    P.L = L;
+    int loc[64], k = 0;
+    for (int q = 0; q < n; q++)
+      if ((T >> q) & 1ull) {
+        loc[q] = k;
+        P.tq[k++] = (int8_t)q;
+      }
+    auto flush = [&]() -> cudaError_t {
+      if (!P.nterms) return cudaSuccess;
+      P.accumulate = acc ? 1 : 0;
+      const uint64_t ntiles = (uint64_t)batch << (n - m);
+      const int smem = (int)(sizeof(Cx<R>) << m) + (8 << (m - L));
+      static int configured[64] = {0};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+      if (smem > 48 * 1024 && smem > configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_pauli_tiles<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = smem;
+      }
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_tiles<R>, 256, smem);
+      uint64_t grid = (uint64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+      if (grid > ntiles) grid = ntiles;
+      k_pauli_tiles<R><<<(unsigned)grid, 256, smem, stream>>>(psi, lam, P, ntiles);
+      acc = true;
+      P.nterms = 0;
+      return cudaGetLastError();
+    };
+    for (int t : idx) {
+      if (done[t] || (terms[t].x_mask & ~T)) continue;
+      if (P.nterms == kPauliTileTerms) {
+        cudaError_t e = flush();
+        if (e != cudaSuccess) return e;
+      }
+      const uint64_t x = terms[t].x_mask;
+      uint32_t xl = 0;
+      for (int q = 0; q < n; q++)
+        if ((x >> q) & 1ull) xl |= 1u << loc[q];
+      const int ny = __builtin_popcountll(x & terms[t].z_mask) & 3;  // i^{nY}
+      const double c = terms[t].coeff;
+      const int j = P.nterms++;
+      P.xl[j] = xl;
+      P.xg[j] = x;
+      P.z[j] = terms[t].z_mask;
+      P.cr[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
+      P.ci[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
+      done[t] = 1;
+      remaining--;
+    }
+    cudaError_t e = flush();
+    if (e != cudaSuccess) return e;
+  }
+  // masks wider than a tile: one pass per mask
+  for (int a = 0; a < nterms; a++) {
+    const int t0 = idx[a];
+    if (done[t0]) continue;
+    std::vector<uint64_t> zs;
+    std::vector<double> cs;
+    for (int b2 = a; b2 < nterms; b2++) {
+      const int t = idx[b2];
+      if (!done[t] && terms[t].x_mask == terms[t0].x_mask) {
+        done[t] = 1;
+        zs.push_back(terms[t].z_mask);
+        cs.push_back(terms[t].coeff);
+      }
+    }
+    cudaError_t e = launch_pauli_accum<R>(psi, lam, n, batch, terms[t0].x_mask, zs.data(), cs.data(), (int)zs.size(),
+                                          acc, stream);
+    if (e != cudaSuccess) return e;
+    acc = true;
+  }
+  return cudaSuccess;
+}
+
 size_t batch_dot_scratch_doubles(int batch) { return (size_t)batch * kDotGridX; }
 
 template <typename R>
@@ -752,6 +1037,8 @@ cudaError_t launch_grad_finish(const double* gscratch, int batch, int ngrad, int
   template cudaError_t launch_batch_init<R>(Cx<R>*, int, int, cudaStream_t);                                      \
   template cudaError_t launch_pauli_accum<R>(const Cx<R>*, Cx<R>*, int, int, uint64_t, const uint64_t*,           \
                                              const double*, int, bool, cudaStream_t);                             \
+  template cudaError_t launch_pauli_tiles<R>(const Cx<R>*, Cx<R>*, int, int, const sv_pauli_term*, int, bool,      \
+                                             cudaStream_t);                                                       \
   template cudaError_t launch_batch_dot<R>(const Cx<R>*, const Cx<R>*, int, int, double*, double*, cudaStream_t);
 SV_INST(float)
 SV_INST(double)

@@ -129,6 +129,12 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
     if (op.kind == OPK_ANTIDIAG && op.m.size() == 2 && op.m[0] == cplx(1.0) && op.m[1] == cplx(1.0))
       d.flags |= OPF_FLIP;
     if (g.param) {
+      // RY has real matrices; RX, RY, RZ have Pauli generators
+      const std::vector<cplx>& G = g.gen;
+      const cplx j(0.0, 1.0);
+      if (op.k == 1 && op.kind == OPK_DENSE && G == std::vector<cplx>{0.0, -j, j, 0.0}) d.flags |= OPF_REALM | OPF_GY;
+      if (op.k == 1 && op.kind == OPK_DENSE && G == std::vector<cplx>{0.0, 1.0, 1.0, 0.0}) d.flags |= OPF_GX;
+      if (op.k == 1 && op.kind == OPK_DIAG && G == std::vector<cplx>{1.0, -1.0}) d.flags |= OPF_GZ;
       d.table = 1;
       d.coef = (uint32_t)g.pidx;
       if (reverse) {
@@ -139,6 +145,9 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
         d.gen = (uint32_t)put(g.gen);
       }
     } else {
+      bool real = op.kind == OPK_DENSE;
+      for (const cplx& v : op.m) real = real && v.imag() == 0.0;
+      if (real) d.flags |= OPF_REALM;
       d.coef = (uint32_t)put(op.m);
     }
     P.ops[oi] = d;
@@ -333,27 +342,11 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
                  "checkpoint store");
   }
 
-  // ---- lambda = H psi, grouped by x mask; f = Re <psi|lambda>
+  // ---- lambda = H psi (tiles that hold whole X-masks); f = Re <psi|lambda>
   {
-    std::vector<char> used(nterms, 0);
-    bool first = true;
-    for (size_t t0 = 0; t0 < nterms; t0++) {
-      if (used[t0]) continue;
-      std::vector<uint64_t> zs;
-      std::vector<double> cs;
-      for (size_t t = t0; t < nterms; t++)
-        if (!used[t] && terms[t].x_mask == terms[t0].x_mask) {
-          used[t] = 1;
-          zs.push_back(terms[t].z_mask);
-          cs.push_back(terms[t].coeff);
-        }
-      Prof pr(stream, "pauli_accum", 3.0 * (double)sbytes);
-      cuda_check(launch_pauli_accum<R>(psi, lam, n, batch, terms[t0].x_mask, zs.data(), cs.data(), (int)zs.size(),
-                                       !first, stream),
-                 "H psi");
-      pr.done();
-      first = false;
-    }
+    Prof pr(stream, "pauli_accum", 2.0 * (double)sbytes);
+    cuda_check(launch_pauli_tiles<R>(psi, lam, n, batch, terms, (int)nterms, false, stream), "H psi");
+    pr.done();
     cuda_check(launch_batch_dot<R>(psi, lam, n, batch, dots, vout, stream), "value");
   }
 

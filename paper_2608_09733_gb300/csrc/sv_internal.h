@@ -38,7 +38,7 @@ enum OpKind : uint8_t {
                     // the slots present).  complex64: three shears, coef[s] = (tan(alpha/2), sin(alpha));
                     // complex128: scaled form, coef[s].re = S/C (bit s of rval clear) or C/S (set)
   OPK_PHASE = 8,    // register phase only: amplitude j of the thread's 2^RQ is multiplied by
-                    // coef[var * (2^RQ + 1) + j]; var collects k selector bits, selector i being bit
+                    // coef[var * table_stride(RQ) + j]; var collects k selector bits, selector i being bit
                     // gq[i] of the thread's local bits (gq[i] < 64) or global bit gq[i] - 64 of the tile
 };
 
@@ -46,6 +46,13 @@ enum OpKind : uint8_t {
 constexpr uint8_t OPF_FLIP = 1;   // anti-diagonal (1, 1): a pure bit flip
 constexpr uint8_t OPF_TCOND = 2;  // tmask/tval is not empty
 constexpr uint8_t OPF_XCOND = 4;  // xmask/xval is not empty
+// BOp.flags only (batched programs): the op's matrix is real, and the
+// generator of a parameterised one-qubit rotation is X, Y or Z (closed-form
+// gradient terms).
+constexpr uint16_t OPF_REALM = 8;
+constexpr uint16_t OPF_GX = 16;
+constexpr uint16_t OPF_GY = 32;
+constexpr uint16_t OPF_GZ = 64;
 
 // In a register phase DevOp.pad holds the op's dispatch word, so one load
 // decides what to do: kind | flags << 4 | rmask << 7 | rval << 12 | coef << 17
@@ -54,6 +61,14 @@ constexpr uint32_t op_code(uint32_t kind, uint32_t flags, uint32_t rmask, uint32
   return kind | (flags << 4) | (rmask << 7) | (rval << 12) | (coef << 17);
 }
 constexpr int kCodeCoefMax = 1 << 15;
+
+// Entries between the variants of a phase table: 2^rq plus padding so that
+// variants start in different shared-memory banks and (complex64) stay
+// 16-byte aligned for pairwise loads.
+template <typename R>
+constexpr int table_stride(int rq) {
+  return (1 << rq) + (sizeof(R) == 4 ? 2 : 1);
+}
 
 constexpr int kMaxTileQ = 14;  // 2^14 amplitudes: 128 KiB (c64) of shared memory
 constexpr int kMaxOps = 96;
@@ -121,6 +136,9 @@ struct SweepProgram {
   Phase ph[kMaxPhases];
   Cx<R> coef[kPool];
 };
+static_assert(sizeof(SweepProgram<float>) % 16 == 0 && sizeof(SweepProgram<double>) % 16 == 0,
+              "programs in an array keep 16-byte alignment");
+
 
 // ----------------------------------------------------------------- batched programs
 //
@@ -299,6 +317,10 @@ cudaError_t launch_batch_init(Cx<R>* psi, int n, int batch, cudaStream_t stream)
 template <typename R>
 cudaError_t launch_pauli_accum(const Cx<R>* psi, Cx<R>* lam, int n, int batch, uint64_t x, const uint64_t* z,
                                const double* c, int nt, bool accumulate, cudaStream_t stream);
+// lam (+)= sum_j c_j P_j psi over the batch, in tiles that hold whole X-masks.
+template <typename R>
+cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, const sv_pauli_term* terms,
+                               int n_terms, bool accumulate, cudaStream_t stream);
 // out[b] = Re <psi_b|lam_b> (partials in scratch: batch x grid doubles)
 template <typename R>
 cudaError_t launch_batch_dot(const Cx<R>* psi, const Cx<R>* lam, int n, int batch, double* scratch, double* out,

@@ -417,7 +417,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
         Tmp t = blank(OPK_PHASE);
         t.d.k = (uint8_t)sel.size();
         for (size_t i = 0; i < sel.size(); i++) t.d.gq[i] = (uint8_t)sel[i];
-        const int stride = NT + 1;  // padded: variants start in different banks
+        const int stride = table_stride<R>(rq);  // padded: variants start in different banks
         t.m.assign((size_t)nvar() * stride, 0.0);
         for (int v = 0; v < nvar(); v++)
           for (int j = 0; j < NT; j++) t.m[v * stride + j] = tab[v * NT + j] * sc;
@@ -607,7 +607,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
       ph.first = (uint8_t)nf;
       ph.nops = (uint8_t)((int)fin.size() - nf);
     }
-    for (const Tmp& t : fin) ncoef += t.m.size();
+    for (const Tmp& t : fin) ncoef += t.m.size() + (t.d.kind == OPK_PHASE ? 1 : 0);  // + alignment padding
     return (int)fin.size() <= kMaxOps && ncoef <= (size_t)SweepProgram<R>::kPool;
   };
   if (!make_fin(g_rot_split, 3) && !make_fin(g_rot_split, 2) && !make_fin(g_rot_split, 0) && !make_fin(false, 0))
@@ -616,6 +616,11 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
 
   int coef = 0;
   for (size_t oi = 0; oi < fin.size(); oi++) {
+    if (fin[oi].d.kind == OPK_PHASE && sizeof(R) == 4 && (coef & 1)) {  // tables are read in 16-byte pairs
+      if (coef >= SweepProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: coefficient pool overflow");
+      P.coef[coef].re = P.coef[coef].im = (R)0;
+      coef++;
+    }
     fin[oi].d.coef = (uint32_t)coef;
     for (const cplx& v : fin[oi].m) {
       if (coef >= SweepProgram<R>::kPool) fail(SV_ERR_INVALID, "internal: coefficient pool overflow");
@@ -742,7 +747,7 @@ void emulate_reg_op(const SweepProgram<R>& P, const DevOp& op, uint32_t code, in
         const uint32_t bit = c < 64 ? (tb >> c) & 1u : (uint32_t)(base >> (c - 64)) & 1u;
         var |= bit << i;
       }
-      for (int j = 0; j < NR; j++) v[j] *= cz(cf[var * (NR + 1) + j]);
+      for (int j = 0; j < NR; j++) v[j] *= cz(cf[var * table_stride<R>(rq) + j]);
       break;
     }
     case OPK_DENSE:

@@ -22,6 +22,8 @@
 // blocks) run group by group straight in shared memory.
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "sv_internal.h"
 
 namespace sv {
@@ -305,6 +307,8 @@ constexpr int kOpsRot = 0;   // KROT, PHASE (and sign flips)
 constexpr int kOpsPerm = 1;  // + anti-diagonal (X, CNOT ...) and SWAP
 constexpr int kOpsAll = 2;   // + KRON, dense/real k <= 2, general diagonals
 
+static_assert(offsetof(SweepProgram<float>, coef) % 16 == 0, "16-byte table pairs in a program's pool");
+
 template <typename R, int RQ, int OPS>
 __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, uint32_t code, const Cx<R>* pool,
                                           uint32_t tb, uint64_t base) {
@@ -345,20 +349,30 @@ __device__ __forceinline__ void apply_reg(Cx<R> (&v)[1 << RQ], const DevOp& op, 
       break;
     case OPK_PHASE: {
       // variant of the table picked by the selector bits (thread bits, or
-      // bits outside the tile); variants are 2^RQ + 1 entries apart
+      // bits outside the tile); variants are table_stride entries apart
       uint32_t var = 0;
       for (int i = 0; i < op.k; i++) {
         const uint32_t c = op.gq[i];
         const uint32_t b = c < 64 ? (tb >> c) & 1u : (uint32_t)(base >> (c - 64)) & 1u;
         var |= b << i;
       }
-      const Cx<R>* T0 = cf + var * ((1u << RQ) + 1u);
+      const Cx<R>* T0 = cf + var * (uint32_t)table_stride<R>(RQ);
+      // v *= T with one temporary: everything else in place
+      auto mul = [](Cx<R>& x, R tr, R ti) {
+        const R t = x.im * ti;
+        x.im = fma(x.re, ti, x.im * tr);
+        x.re = fma(x.re, tr, -t);
+      };
+      if constexpr (sizeof(R) == 4) {  // pairs of entries per 16-byte load
 #pragma unroll
-      for (int j = 0; j < (1 << RQ); j++) {  // v *= T with one temporary: everything else in place
-        const Cx<R> T = T0[j];
-        const R t = v[j].im * T.im;
-        v[j].im = fma(v[j].re, T.im, v[j].im * T.re);
-        v[j].re = fma(v[j].re, T.re, -t);
+        for (int j = 0; j < (1 << RQ); j += 2) {
+          const float4 w = *reinterpret_cast<const float4*>(T0 + j);
+          mul(v[j], (R)w.x, (R)w.y);
+          mul(v[j + 1], (R)w.z, (R)w.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < (1 << RQ); j++) mul(v[j], T0[j].re, T0[j].im);
       }
       break;
     }
@@ -653,8 +667,9 @@ __global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
   uint64_t* hi_off = reinterpret_cast<uint64_t*>(buf[1] + tsz);
   const int nhi = 1 << (h.m - h.L);
   for (int c = threadIdx.x; c < nhi; c += blockDim.x) hi_off[c] = local_offset((uint32_t)c << h.L, h);
-  // the coefficient pool, staged once per CTA (broadcast reads from shared memory)
-  Cx<R>* scoef = reinterpret_cast<Cx<R>*>(hi_off + nhi);
+  // the coefficient pool, staged once per CTA (broadcast reads from shared
+  // memory), 16-byte aligned
+  Cx<R>* scoef = reinterpret_cast<Cx<R>*>(hi_off + nhi + (nhi & 1));
   for (int c = threadIdx.x; c < h.ncoef; c += blockDim.x) scoef[c] = P.coef[c];
   const uint32_t lowmask = (1u << h.L) - 1u;
   __syncthreads();
@@ -751,13 +766,12 @@ int device_sm_count() {
 
 int sweep_threads(int m, int rq) {
   // one thread per register group of 2^rq amplitudes; at least one warp
-  int t = m - rq >= 5 ? (1 << (m - rq)) : 32;
-  return t > 256 ? 256 : t;
+  return m - rq >= 5 ? (1 << (m - rq)) : 32;
 }
 
 template <typename R, int KMAX, int RQ, bool DBUF, int OPS>
 static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
-  const int smem = ((int)sizeof(Cx<R>) << (prog.h.m + (DBUF ? 1 : 0))) + (8 << (prog.h.m - prog.h.L)) +
+  const int smem = ((int)sizeof(Cx<R>) << (prog.h.m + (DBUF ? 1 : 0))) + (8 << (prog.h.m - prog.h.L)) + 8 +
                    (int)sizeof(Cx<R>) * prog.h.ncoef;
   // raise the dynamic shared-memory limit to what this launch needs (per device)
   static int configured_bytes[64] = {0};
@@ -771,6 +785,7 @@ static cudaError_t launch_sweep_k(Cx<R>* state, const SweepProgram<R>& prog, cud
     configured_bytes[dev] = smem;
   }
   const int threads = sweep_threads(prog.h.m, RQ);
+  if (threads > (RQ == 5 ? SV_RQ5_MAXT : 256)) return cudaErrorInvalidConfiguration;  // a group per thread
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<R, KMAX, RQ, DBUF, OPS>, threads, smem);
   if (per_sm < 1) per_sm = 1;
