@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="oracle sample size (0 = auto)")
-    ap.add_argument("--workload", choices=["gates", "adjoint", "serving"], default="gates")
+    ap.add_argument("--workload", choices=["gates", "adjoint", "serving", "precision", "latency", "sampling"],
+                    default="gates")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -341,6 +342,137 @@ def bench_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_precision(args):
+    """24 qubits, 600 gates (400 Haar U(2) + 200 Haar SU(4) on random pairs,
+    seeded shuffle), complex64 and complex128 on the GPU against the FP64
+    oracle (timed as the CPU baseline of this workload): fidelity
+    |<psi_oracle|psi>|^2 and max |psi - psi_oracle| after 100, 200 and 600
+    gates."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2608_09733_gb300 as sv
+    from workloads import precision_sweep
+    n = 24
+    gates = precision_sweep(n, 400, 200, seed=0)
+    cuts = (100, 200, 600)
+    t0 = time.perf_counter()
+    refs, psi = {}, None
+    for a, b in zip((0,) + cuts[:-1], cuts):
+        psi = oracle.run(n, gates[a:b], init=psi)
+        refs[b] = psi.copy()
+    t_oracle = time.perf_counter() - t0
+    rows = []
+    for dt, tdt in ((sv.SV_C64, torch.complex64), (sv.SV_C128, torch.complex128)):
+        st = torch.empty(1 << n, dtype=tdt, device="cuda")
+        sv.sv_init_basis(st, 0)
+        done = 0
+        for cut in cuts:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sv.sv_apply_circuit(st, gates[done:cut], fuse_max_k=5)
+            e1.record()
+            torch.cuda.synchronize()
+            done = cut
+            got = st.cpu().numpy().astype(np.complex128)
+            ref = refs[cut]
+            rows.append({"dtype": "c64" if dt == sv.SV_C64 else "c128", "gates": cut,
+                         "fidelity": float(abs(np.vdot(ref, got)) ** 2),
+                         "max_abs_err": float(np.abs(got - ref).max()),
+                         "rel_l2_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                         "segment_ms": e0.elapsed_time(e1)})
+    print(json.dumps({
+        "metric": "precision sweep: fidelity and max-abs error vs FP64 after 100/200/600 gates (24q)",
+        "value": rows[2]["max_abs_err"], "unit": "max |psi - psi_fp64| (c64, 600 gates)", "n_gpus": 1,
+        "higher_is_better": False, "dtype": "c64+c128", "data": "synthetic",
+        "config": {"workload": "precision_sweep_24q_400u2_200su4", "fuse_max_k": 5}, "rows": rows,
+        "cpu_baseline": {"value": t_oracle, "unit": "s for 600 gates", "cores": oracle.n_threads(), "kind": "oracle",
+                         "sample": "the whole 600-gate circuit, complex128"}}), flush=True)
+
+
+def bench_latency(args):
+    """12 qubits, complex128, 10 layers of RY + RZ on every qubit and a CNOT
+    ladder (350 gates): wall-clock microseconds per circuit (init + apply +
+    <Z> read-out) on the device, one circuit after another on one stream, and
+    per circuit when 1024 of them share one packed launch."""
+    import torch
+    import paper_2608_09733_gb300 as sv
+    from workloads import layered_ry_rz_cnot
+    n, reps = 12, 200
+    g = sv.Gates(layered_ry_rz_cnot(n, 10, 0))
+    st = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    out = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+
+    def one():
+        sv.sv_init_basis(st, 0)
+        sv.sv_apply_circuit(st, g, fuse_max_k=5)
+        sv.sv_expect_z_all(st, out=out)
+    for _ in range(20):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one()
+    torch.cuda.synchronize()
+    seq_us = (time.perf_counter() - t0) / reps * 1e6
+    nb = 1024
+    res = torch.empty(nb, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        sv.sv_run_batch_small([n] * nb, [g] * nb, sv.SV_C128, out=res)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sv.sv_run_batch_small([n] * nb, [g] * nb, sv.SV_C128, out=res)
+    torch.cuda.synchronize()
+    packed_us = (time.perf_counter() - t0) / (5 * nb) * 1e6
+    print(json.dumps({
+        "metric": "12q c128 layered circuit latency (350 gates)", "value": seq_us, "unit": "us per circuit",
+        "n_gpus": 1, "higher_is_better": False, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "layered_ry_rz_cnot_12q_10layers_c128", "fuse_max_k": 5},
+        "packed_us_per_circuit": packed_us, "packed_batch": nb}), flush=True)
+
+
+def bench_sampling(args):
+    """Finite-shot measurement of the 30-qubit complex64 state of the fused
+    layered circuit: 2^20 shots per step from seeded uniforms (shots/s), and
+    the normalised probability vector (GB/s of state read)."""
+    import numpy as np
+    import torch
+    import paper_2608_09733_gb300 as sv
+    from workloads import fused_layered_u3_cz
+    n, shots = args.n, 1 << 20
+    st = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    sv.sv_init_basis(st, 0)
+    sv.sv_apply_circuit(st, fused_layered_u3_cz(n, 4, 0), fuse_max_k=5)
+    u = np.random.default_rng(0).random(shots)
+    out = torch.empty(shots, dtype=torch.int64, device="cuda")
+    for _ in range(args.warmup):
+        sv.sv_sample(st, u, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sv.sv_sample(st, u, out=out)
+    torch.cuda.synchronize()
+    t_s = (time.perf_counter() - t0) / args.steps
+    p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    sv.sv_probabilities(st, out=p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sv.sv_probabilities(st, out=p)
+    e1.record()
+    torch.cuda.synchronize()
+    t_p = e0.elapsed_time(e1) / args.steps / 1e3
+    print(json.dumps({
+        "metric": "finite-shot sampling shots/s (%dq c64 state, 2^20 shots per call)" % n, "value": shots / t_s,
+        "unit": "shots/s", "n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "sample_%dq_c64_1M_shots" % n}, "ms_per_call": t_s * 1e3,
+        "probabilities_ms": t_p * 1e3,
+        "probabilities_gbs": ((8 + 8 + 8) << n) / t_p / 1e9}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -355,7 +487,8 @@ def main():
         from paper_2608_09733_gb300 import build as _build
         _build.build()
         if rank == 0:
-            (bench_adjoint if args.workload == "adjoint" else bench_serving)(args)
+            {"adjoint": bench_adjoint, "serving": bench_serving, "precision": bench_precision,
+             "latency": bench_latency, "sampling": bench_sampling}[args.workload](args)
         return
 
     import numpy as np

@@ -208,6 +208,30 @@ sv_status sv_plan_info(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_
                        const double* param_values, size_t n_param_values, const sv_exec_opts* opts,
                        int* out_blocks, int* out_sweeps, int* block_starts);
 
+/* Measurement probabilities (Sec. 5.3, measurement equation):
+ * p_i = x_i^2 + y_i^2 for psi_i = x_i + i y_i, in double (each product and
+ * the sum rounded once), divided by their sum when normalise != 0.
+ *   state   device, 2^n amplitudes of `dtype`
+ *   out     device, 2^n doubles (caller-owned)
+ * Asynchronous on `stream`; errors as sv_expect. */
+sv_status sv_probabilities(const void* state, int n_qubits, sv_dtype dtype, double* out, int normalise,
+                           void* stream);
+
+/* Finite-shot measurement (Sec. 5.3: basis indices drawn from the probability
+ * vector), one draw per caller-supplied uniform u_k in [0, 1), by the inverse
+ * of the cumulative distribution taken in exact integer arithmetic:
+ *   q_i = floor(p_i 2^61) with p_i as in sv_probabilities (not normalised),
+ *   Q = sum_i q_i,  t_k = floor(floor(u_k 2^53) Q / 2^53),
+ *   index_k = the smallest i with q_0 + ... + q_i > t_k.
+ * The result does not depend on any summation order, so the same uniforms
+ * give the same indices on every device and on the host.
+ *   uniforms  host, n_shots doubles in [0, 1) (else SV_ERR_INVALID)
+ *   out       n_shots basis indices, host (out_on_device = 0: the call waits)
+ *             or device memory
+ * 5 <= n_qubits <= 34; a state with no mass above 2^-61 is SV_ERR_INVALID. */
+sv_status sv_sample(const void* state, int n_qubits, sv_dtype dtype, const double* uniforms, size_t n_shots,
+                    uint64_t* out, int out_on_device, void* stream);
+
 /* Host execution of the pass kernel's programs: builds the plan of `gates`
  * exactly as sv_apply_circuit_ex would for `dtype` (fusion, tiles, register
  * phases, rotations, phase tables), then runs every program on the host in

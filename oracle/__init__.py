@@ -60,7 +60,8 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=gnu99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC,
+               "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -85,6 +86,10 @@ def lib():
         L.og_expect_pauli.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]
         L.og_expect_pauli.restype = cd
         L.og_expect_z_all.argtypes = [ctypes.c_void_p, ctypes.c_int, P(cd), P(cd)]
+        L.og_probabilities.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, P(cd)]
+        L.og_probabilities.restype = None
+        L.og_sample.argtypes = [ctypes.c_void_p, ctypes.c_int, P(cd), ctypes.c_int64, P(ctypes.c_uint64)]
+        L.og_sample.restype = ctypes.c_int
         L.og_inner.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, P(cd), P(cd)]
         L.og_adjoint_grad.argtypes = [ctypes.c_int, P(OGGate), ctypes.c_int, P(ctypes.c_uint64),
                                       P(ctypes.c_uint64), P(cd), ctypes.c_int, P(cd), ctypes.c_int, P(cd)]
@@ -203,6 +208,26 @@ def expect_terms(psi: np.ndarray, n: int, terms) -> Tuple[float, np.ndarray]:
     for j in range(len(terms)):
         per[j] = lib().og_expect_pauli(_ptr(psi), n, int(xs[j]), int(zs[j]))
     return float(np.dot(cs, per)), per
+
+
+def probabilities(psi: np.ndarray, n: int, normalise: bool = True) -> np.ndarray:
+    """p_i = |psi_i|^2 (Sec. 5.3 measurement equation), optionally normalised."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    p = np.zeros(2 ** n)
+    lib().og_probabilities(_ptr(psi), n, 1 if normalise else 0, _dp(p))
+    return p
+
+
+def sample(psi: np.ndarray, n: int, u) -> np.ndarray:
+    """Basis indices drawn from |psi|^2 by the exact integer inverse CDF of
+    og_sample, one per uniform u_k in [0, 1)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(u.size, dtype=np.uint64)
+    rc = lib().og_sample(_ptr(psi), n, _dp(u), u.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if rc != 0:
+        raise ValueError("og_sample failed (%d)" % rc)
+    return out
 
 
 def expect_z_all(psi: np.ndarray, n: int) -> Tuple[np.ndarray, float]:

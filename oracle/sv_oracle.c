@@ -20,7 +20,11 @@
  *     over gates, g = Im <lambda|G|psi_k> for U = exp(-i theta G / 2));
  *   - the paper's gate fusion: consecutive gates joined, in order, while the
  *     union of their qubits stays within k (Sec. 4.3 `fuse`, Sec. 9.2);
- *     a block's matrix is the ordered product of its embedded gates.
+ *     a block's matrix is the ordered product of its embedded gates;
+ *   - measurement: p_i = x_i^2 + y_i^2 for psi_i = x_i + i y_i, normalised
+ *     (Sec. 5.3, measurement equation), and finite-shot draws of basis
+ *     indices from it by the inverse of its cumulative distribution, the
+ *     uniform draws given by the caller (see og_sample).
  *
  * No blocking, no fusion beyond the above, no reordering.  The group loops
  * carry an OpenMP pragma (each group is disjoint), which changes nothing in
@@ -465,6 +469,66 @@ int og_fuse(int n, const og_gate* gates, int ng, int kmax, int nblocks_max, int*
   }
   block_start[nb] = ng;
   return nb;
+}
+
+/* ------------------------------------------------------------ measurement */
+
+/* p_i = x_i^2 + y_i^2, divided by their sum when normalise != 0 (Sec. 5.3,
+ * measurement equation).  Each p_i is rounded once per product and once for
+ * the sum (this file is compiled without contraction into fused
+ * multiply-adds). */
+void og_probabilities(const cplx* psi, int n, int normalise, double* p) {
+  const uint64_t N = 1ull << n;
+  double tot = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    const double x = creal(psi[i]), y = cimag(psi[i]);
+    p[i] = x * x + y * y;
+    tot += p[i];
+  }
+  if (normalise && tot > 0.0)
+    for (uint64_t i = 0; i < N; i++) p[i] /= tot;
+}
+
+/* Finite-shot draws (Sec. 5.3: basis indices drawn from the probability
+ * vector).  The distribution is taken in exact integer arithmetic so that the
+ * draw does not depend on the order of any floating-point sum:
+ *   q_i = floor(p_i 2^61)      (p_i as in og_probabilities, not normalised),
+ *   Q   = sum_i q_i,
+ *   t_k = floor(floor(u_k 2^53) Q / 2^53)  for the caller's u_k in [0, 1),
+ *   index_k = the smallest i with q_0 + ... + q_i > t_k.
+ * Dividing every q_i by Q is the normalisation; the exact prefix sums are the
+ * cumulative distribution.  Returns -1 if every q_i is 0. */
+int og_sample(const cplx* psi, int n, const double* u, int64_t nshots, uint64_t* out) {
+  const uint64_t N = 1ull << n;
+  uint64_t* cum = (uint64_t*)malloc(sizeof(uint64_t) * N);
+  if (!cum) return -2;
+  uint64_t run = 0;
+  for (uint64_t i = 0; i < N; i++) {
+    const double x = creal(psi[i]), y = cimag(psi[i]);
+    const double pi = x * x + y * y;
+    run += (uint64_t)ldexp(pi, 61);
+    cum[i] = run;
+  }
+  const uint64_t Q = run;
+  if (Q == 0) {
+    free(cum);
+    return -1;
+  }
+  for (int64_t k = 0; k < nshots; k++) {
+    const uint64_t m = (uint64_t)ldexp(u[k], 53);
+    const uint64_t t = (uint64_t)(((unsigned __int128)m * Q) >> 53);
+    uint64_t lo = 0, hi = N - 1;  /* first i with cum[i] > t */
+    while (lo < hi) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if (cum[mid] > t)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    out[k] = lo;
+  }
+  free(cum);
+  return 0;
 }
 
 int og_num_threads(void) {

@@ -24,11 +24,13 @@ from .binding import (  # noqa: F401
     sv_expect_z_all,
     sv_init_basis,
     sv_plan_info,
+    sv_probabilities,
     sv_profile_enable,
     sv_profile_read,
     sv_release_scratch,
     sv_run_host,
     sv_run_batch_small,
+    sv_sample,
     GateArray,
     layered_u3_cnot_gates,
     sv_version,

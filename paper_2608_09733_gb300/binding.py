@@ -35,7 +35,7 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_expect_z_all",
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
-           "sv_expect_z_all_noalloc", "sv_emulate_apply"]
+           "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample"]
 
 
 class SvError(RuntimeError):
@@ -99,6 +99,8 @@ def load():
             "sv_apply_circuit_ex": ([vp, ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), vp], ci),
             "sv_plan_info": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), P(ci), P(ci), P(ci)], ci),
             "sv_emulate_apply": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), vp], ci),
+            "sv_probabilities": ([vp, ci, ci, vp, ci, vp], ci),
+            "sv_sample": ([vp, ci, ci, P(cd), sz, vp, ci, vp], ci),
             "sv_run_host": ([ci, ci, vp, P(SvGate), sz, P(cd), sz, ci, P(cd), vp, vp], ci),
             "sv_alloc": ([ci, ci, vp, P(vp)], ci),
             "sv_free": ([vp], ci),
@@ -321,6 +323,35 @@ def sv_plan_info(n: int, dtype: int, gates, param_values=None, fuse_max_k: int =
     _check(load().sv_plan_info(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), ctypes.byref(nb), ctypes.byref(ns),
                                starts))
     return nb.value, ns.value, [starts[i] for i in range(nb.value + 1)]
+
+
+def sv_probabilities(state, normalise: bool = True, out=None, stream=None):
+    """|psi_i|^2 as a device float64 tensor (normalised by default)."""
+    import torch
+    n = _n_of(state)
+    if out is None:
+        out = torch.empty(1 << n, dtype=torch.float64, device=state.device)
+    _check(load().sv_probabilities(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state),
+                                   ctypes.c_void_p(out.data_ptr()), 1 if normalise else 0, _stream(stream)))
+    return out
+
+
+def sv_sample(state, uniforms, out=None, stream=None) -> np.ndarray:
+    """Basis indices drawn from |psi|^2, one per uniform in [0, 1) (host
+    numpy array); into the device uint64-compatible tensor ``out`` (int64)
+    if given, else returned as a numpy uint64 array."""
+    n = _n_of(state)
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    if out is not None:
+        _check(load().sv_sample(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state),
+                                u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
+                                ctypes.c_void_p(out.data_ptr()), 1, _stream(stream)))
+        return out
+    host = np.zeros(u.size, dtype=np.uint64)
+    _check(load().sv_sample(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state),
+                            u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
+                            ctypes.c_void_p(host.ctypes.data), 0, _stream(stream)))
+    return host
 
 
 def sv_emulate_apply(state: np.ndarray, n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0,
