@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -208,17 +209,97 @@ void Prof::done() {
 
 namespace {
 
+// ----------------------------------------------------------- compiled circuits
+//
+// The pass programs of the last few circuits, keyed by the exact bytes of
+// everything that decides them (n, precision, options, the gate records with
+// their matrices, the parameter values).  A circuit applied again with the
+// same inputs skips the host planning; every kernel still runs.
+
+struct Compiled {
+  std::vector<unsigned char> key;
+  int n = 0;
+  std::vector<SweepProgram<float>> pf;
+  std::vector<SweepProgram<double>> pd;
+};
+
+constexpr size_t kCompiledMax = 8;                  // circuits kept
+constexpr size_t kCompiledMaxPasses = 512;          // larger plans are not kept
+
+std::mutex g_compiled_mu;
+std::list<std::shared_ptr<const Compiled>> g_compiled;  // most recent first
+
+std::vector<unsigned char> circuit_key(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const double* pv,
+                                       size_t npv, const sv_exec_opts& opts) {
+  std::vector<unsigned char> k;
+  auto put = [&](const void* p, size_t b) {
+    const unsigned char* c = (const unsigned char*)p;
+    k.insert(k.end(), c, c + b);
+  };
+  const int32_t hdr[2] = {n, (int32_t)dtype};
+  put(hdr, sizeof(hdr));
+  put(&opts, sizeof(opts));
+  put(&ng, sizeof(ng));
+  put(&npv, sizeof(npv));
+  for (size_t i = 0; i < ng; i++) {
+    sv_gate g = gates[i];
+    const double* m = g.matrix;
+    g.matrix = nullptr;
+    put(&g, sizeof(g));
+    if (m && g.type == SV_GATE_UNITARY && g.n_targets >= 1 && g.n_targets <= 5)
+      put(m, sizeof(double) * 2 * ((size_t)1 << (2 * g.n_targets)));
+  }
+  if (npv && pv) put(pv, sizeof(double) * npv);
+  return k;
+}
+
+std::shared_ptr<const Compiled> compiled_circuit(int n, sv_dtype dtype, const sv_gate* gates, size_t ng,
+                                                 const double* pv, size_t npv, const sv_exec_opts& opts) {
+  std::vector<unsigned char> key = circuit_key(n, dtype, gates, ng, pv, npv, opts);
+  {
+    std::lock_guard<std::mutex> lk(g_compiled_mu);
+    for (auto it = g_compiled.begin(); it != g_compiled.end(); ++it)
+      if ((*it)->key == key) {
+        std::shared_ptr<const Compiled> c = *it;
+        g_compiled.erase(it);
+        g_compiled.push_front(c);
+        return c;
+      }
+  }
+  Plan plan = make_plan(n, dtype, gates, ng, pv, npv, opts);
+  auto c = std::make_shared<Compiled>();
+  c->n = n;
+  if (dtype == SV_C64) {
+    c->pf.resize(plan.sweeps.size());
+    for (size_t i = 0; i < plan.sweeps.size(); i++) build_program<float>(plan, plan.sweeps[i], c->pf[i]);
+  } else {
+    c->pd.resize(plan.sweeps.size());
+    for (size_t i = 0; i < plan.sweeps.size(); i++) build_program<double>(plan, plan.sweeps[i], c->pd[i]);
+  }
+  if (plan.sweeps.size() <= kCompiledMaxPasses) {
+    c->key = std::move(key);
+    std::lock_guard<std::mutex> lk(g_compiled_mu);
+    g_compiled.push_front(c);
+    while (g_compiled.size() > kCompiledMax) g_compiled.pop_back();
+  }
+  return c;
+}
+
 template <typename R>
-void run_plan(void* state, const Plan& plan, cudaStream_t stream) {
-  static thread_local std::unique_ptr<SweepProgram<R>> prog;
-  if (!prog) prog.reset(new SweepProgram<R>());
-  const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << plan.n);  // read + write the state
-  for (const Sweep& sw : plan.sweeps) {
-    build_program<R>(plan, sw, *prog);
+void run_programs(void* state, int n, const std::vector<SweepProgram<R>>& progs, cudaStream_t stream) {
+  const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << n);  // read + write the state
+  for (const SweepProgram<R>& P : progs) {
     Prof pr(stream, "sweep", bytes);
-    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), *prog, stream), "sweep launch");
+    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), P, stream), "sweep launch");
     pr.done();
   }
+}
+
+void run_compiled(void* state, const Compiled& c, sv_dtype dtype, cudaStream_t stream) {
+  if (dtype == SV_C64)
+    run_programs<float>(state, c.n, c.pf, stream);
+  else
+    run_programs<double>(state, c.n, c.pd, stream);
 }
 
 sv_exec_opts opts_of(const sv_exec_opts* o) {
@@ -236,11 +317,7 @@ sv_exec_opts fuse_opts(int fuse) {
 
 void apply_circuit(void* state, int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* pv,
                    size_t npv, const sv_exec_opts& opts, cudaStream_t stream) {
-  Plan plan = make_plan(n, dtype, gates, n_gates, pv, npv, opts);
-  if (dtype == SV_C64)
-    run_plan<float>(state, plan, stream);
-  else
-    run_plan<double>(state, plan, stream);
+  run_compiled(state, *compiled_circuit(n, dtype, gates, n_gates, pv, npv, opts), dtype, stream);
 }
 
 void expect_z_all_dev(const void* state, int n, sv_dtype dtype, double* out_dev, cudaStream_t stream) {
@@ -387,7 +464,8 @@ sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const 
   return guarded([&] {
     check_dtype_n(n_qubits, dtype);
     if (!out_z) fail(SV_ERR_INVALID, "out_z is NULL");
-    Plan plan = make_plan(n_qubits, dtype, gates, n_gates, param_values, n_param_values, fuse_opts(fuse_max_k));
+    std::shared_ptr<const Compiled> prog =
+        compiled_circuit(n_qubits, dtype, gates, n_gates, param_values, n_param_values, fuse_opts(fuse_max_k));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = amp_bytes(dtype) << n_qubits;
     Workspace& w = workspace(s, expect_z_all_scratch_doubles(n_qubits), n_qubits + 1, bytes);
@@ -398,10 +476,7 @@ sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const 
     } else {
       cuda_check(launch_init_basis<double>((Cx<double>*)w.state, n_qubits, 0, s), "init launch");
     }
-    if (dtype == SV_C64)
-      run_plan<float>(w.state, plan, s);
-    else
-      run_plan<double>(w.state, plan, s);
+    run_compiled(w.state, *prog, dtype, s);
     expect_z_all_dev(w.state, n_qubits, dtype, w.out, s);
     cuda_check(cudaMemcpyAsync(out_z, w.out, (n_qubits + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
                "result copy");
