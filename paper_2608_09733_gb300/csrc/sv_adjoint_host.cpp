@@ -20,7 +20,7 @@
 #include <cstring>
 #include <memory>
 
-#include "sv_internal.h"
+#include "sv_adjoint.h"
 
 namespace sv {
 namespace {
