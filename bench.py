@@ -54,8 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="oracle sample size (0 = auto)")
-    ap.add_argument("--workload", choices=["gates", "adjoint", "serving", "precision", "latency", "sampling"],
-                    default="gates")
+    ap.add_argument("--workload", choices=["gates", "adjoint", "serving", "precision", "latency", "sampling",
+                                           "batchlayer"], default="gates")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -473,6 +473,46 @@ def bench_sampling(args):
         "probabilities_gbs": ((8 + 8 + 8) << n) / t_p / 1e9}), flush=True)
 
 
+def bench_batchlayer(args):
+    """BatchLayer (angle encoding RY(x_q), then 4 layers of RY, RZ weights and
+    a CNOT ring) on 16 qubits, complex64: a batch of 256 input rows through
+    forward (per-qubit <Z>) and backward (one batched adjoint pass): rows per
+    second for forward + backward."""
+    import numpy as np
+    import torch
+    import paper_2608_09733_gb300 as sv
+    from workloads import Gate
+    n, layers, batch = 16, 4, 256
+    gates, slot = [Gate("ry", [q], slots=[q]) for q in range(n)], n
+    for _ in range(layers):
+        for q in range(n):
+            gates += [Gate("ry", [q], slots=[slot]), Gate("rz", [q], slots=[slot + 1])]
+            slot += 2
+        gates += [Gate("x", [(q + 1) % n], controls=[q]) for q in range(n)]
+    layer = sv.BatchLayer(gates, n, n_data=n, n_weights=slot - n, dtype=sv.SV_C64)
+    x = torch.tensor(np.random.default_rng(0).uniform(0, np.pi, size=(batch, n)), requires_grad=True)
+    target = torch.tensor(np.random.default_rng(1).normal(size=(batch, n)))
+
+    def step():
+        layer.zero_grad()
+        x.grad = None
+        loss = (layer(x) * target).sum()
+        loss.backward()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({
+        "metric": "BatchLayer rows/s, forward + backward (16q, 4 layers, batch 256, c64)", "value": batch / t,
+        "unit": "rows/s", "n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "batchlayer_16q_4layers_batch256", "parameters": slot}, "ms_per_step": t * 1e3}),
+        flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -488,7 +528,7 @@ def main():
         _build.build()
         if rank == 0:
             {"adjoint": bench_adjoint, "serving": bench_serving, "precision": bench_precision,
-             "latency": bench_latency, "sampling": bench_sampling}[args.workload](args)
+             "latency": bench_latency, "sampling": bench_sampling, "batchlayer": bench_batchlayer}[args.workload](args)
         return
 
     import numpy as np

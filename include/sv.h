@@ -271,6 +271,29 @@ sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, si
                           int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
                           double* out_grad, double* out_value, void* stream);
 
+/* sv_adjoint_grad with a Hamiltonian per state: state b uses
+ * H_b = sum_j row_coeffs[b * n_terms + j] P_j (the coeff field of `terms` is
+ * not used).  This is the backward pass of a layer whose outputs are the
+ * <P_j> of every state (Sec. 5.4 BatchLayer: per-qubit Z readout): with
+ * row_coeffs = the upstream gradient dL/d<P_j>_b, out_grad is dL/dtheta.
+ *   row_coeffs  host, batch x n_terms doubles
+ * Every X-mask of the terms must fit one tile (13 qubits for complex64, 12 for
+ * complex128, the lowest 5 / 4 included), else SV_ERR_UNSUPPORTED; Z-only
+ * terms always do.  Other arguments and errors as sv_adjoint_grad. */
+sv_status sv_adjoint_grad_rows(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                               const double* params, int batch, int n_params, const sv_pauli_term* terms,
+                               size_t n_terms, const double* row_coeffs, int checkpoint_every, double* out_grad,
+                               double* out_value, void* stream);
+
+/* Forward pass of a batched circuit template (Sec. 4.1 BatchSV, Sec. 5.4
+ * BatchLayer): state b = U(params_b)|0..0>, then <Z_q> for every qubit and
+ * their sum, per state.  The template rules are those of sv_adjoint_grad
+ * (parameterised gates are one-parameter rotations).
+ *   out_z   host, batch x (n_qubits + 1) doubles: <Z_0> .. <Z_{n-1}>, sum
+ * The call waits for the result.  1 <= n_qubits <= 30, 1 <= batch <= 65535. */
+sv_status sv_batch_expect_z(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                            const double* params, int batch, int n_params, double* out_z, void* stream);
+
 /* ---- serving: packed small states -------------------------------------------
  * Runs many small independent circuits in ONE kernel launch: request b gets one
  * CTA that keeps its whole state (2^n amplitudes, n <= SV_SMALL_MAX_QUBITS) in

@@ -15,6 +15,8 @@ from .binding import (  # noqa: F401
     load,
     pauli_terms,
     sv_adjoint_grad,
+    sv_adjoint_grad_rows,
+    sv_batch_expect_z,
     sv_apply_circuit,
     sv_apply_circuit_ex,
     SV_BLOCK_AUTO,
@@ -36,4 +38,4 @@ from .binding import (  # noqa: F401
     sv_version,
 )
 
-from .autograd import AdjointExpectation, adjoint_expectation  # noqa: E402,F401
+from .autograd import AdjointExpectation, BatchLayer, adjoint_expectation  # noqa: E402,F401

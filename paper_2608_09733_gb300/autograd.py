@@ -10,6 +10,8 @@ batched-template, per-parameter-gradient path of the paper's QML layers
 
 from __future__ import annotations
 
+from collections import namedtuple
+
 import numpy as np
 import torch
 
@@ -39,3 +41,58 @@ def adjoint_expectation(params: torch.Tensor, n: int, gates, terms, dtype: int =
     t = B.pauli_terms(terms) if not isinstance(terms, type(B.pauli_terms([]))) else terms
     out = AdjointExpectation.apply(p, n, dtype, g, t, checkpoint_every)
     return out[0] if squeeze else out
+
+
+_Term = namedtuple("_Term", "paulis qubits coeff")
+
+
+class _BatchLayerFn(torch.autograd.Function):
+    """Forward: <Z_q> of every qubit for every input row (one batched
+    forward pass).  Backward: one batched adjoint pass whose Hamiltonian for
+    row b is sum_q (dL/d<Z_q>_b) Z_q, which gives dL/dtheta_b directly."""
+
+    @staticmethod
+    def forward(ctx, x, w, n, dtype, gates, checkpoint_every):
+        xb = x.detach().to("cpu", torch.float64)
+        wb = w.detach().to("cpu", torch.float64).reshape(1, -1).expand(xb.shape[0], -1)
+        params = torch.cat([xb, wb], dim=1).contiguous().numpy()
+        z = B.sv_batch_expect_z(n, dtype, gates, params)[:, :n]
+        ctx.params, ctx.n, ctx.dtype, ctx.gates, ctx.ckpt = params, n, dtype, gates, checkpoint_every
+        ctx.n_data = x.shape[1]
+        ctx.devices = (x.device, x.dtype, w.device, w.dtype)
+        return torch.from_numpy(z).to(x.device, x.dtype)
+
+    @staticmethod
+    def backward(ctx, gz):
+        n = ctx.n
+        terms = B.pauli_terms([_Term("Z", [q], 1.0) for q in range(n)])
+        coeffs = gz.detach().to("cpu", torch.float64).contiguous().numpy()
+        _, grad = B.sv_adjoint_grad_rows(n, ctx.dtype, ctx.gates, ctx.params, terms, coeffs, ctx.ckpt)
+        xdev, xdt, wdev, wdt = ctx.devices
+        g = torch.from_numpy(grad)
+        dx = g[:, :ctx.n_data].to(xdev, xdt)
+        dw = g[:, ctx.n_data:].sum(dim=0).to(wdev, wdt)
+        return dx, dw, None, None, None, None
+
+
+class BatchLayer(torch.nn.Module):
+    """A fixed circuit template as a torch layer (Sec. 5.4 BatchLayer): the
+    template's parameter slots 0 .. n_data-1 take each input row's data,
+    slots n_data .. n_data+n_weights-1 the layer's trainable weights; the
+    output is <Z_q> for every qubit of every row, (batch, n).  All rows run
+    as one batched state; backward is one batched adjoint pass (no
+    parameter-shift loop).  Parameterised gates must be one-parameter
+    rotations (RX, RY, RZ, P, RXX, RYY, RZZ)."""
+
+    def __init__(self, gates, n_qubits: int, n_data: int, n_weights: int, dtype: int = B.SV_C64,
+                 checkpoint_every: int = 0, init_scale: float = 0.1, seed: int = 0):
+        super().__init__()
+        self.gates = gates if isinstance(gates, B.Gates) else B.Gates(gates)
+        self.n, self.n_data, self.dtype, self.ckpt = n_qubits, n_data, dtype, checkpoint_every
+        gen = torch.Generator().manual_seed(seed)
+        self.weight = torch.nn.Parameter(init_scale * torch.randn(n_weights, generator=gen, dtype=torch.float64))
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        if x.dim() != 2 or x.shape[1] != self.n_data:
+            raise ValueError("expected input rows of %d data values" % self.n_data)
+        return _BatchLayerFn.apply(x, self.weight, self.n, self.dtype, self.gates, self.ckpt)

@@ -35,7 +35,8 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_expect_z_all",
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
-           "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample"]
+           "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample", "sv_adjoint_grad_rows",
+           "sv_batch_expect_z"]
 
 
 class SvError(RuntimeError):
@@ -101,6 +102,9 @@ def load():
             "sv_emulate_apply": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), vp], ci),
             "sv_probabilities": ([vp, ci, ci, vp, ci, vp], ci),
             "sv_sample": ([vp, ci, ci, P(cd), sz, vp, ci, vp], ci),
+            "sv_adjoint_grad_rows": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(SvPauliTerm), sz, P(cd), ci, P(cd),
+                                      P(cd), vp], ci),
+            "sv_batch_expect_z": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(cd), vp], ci),
             "sv_run_host": ([ci, ci, vp, P(SvGate), sz, P(cd), sz, ci, P(cd), vp, vp], ci),
             "sv_alloc": ([ci, ci, vp, P(vp)], ci),
             "sv_free": ([vp], ci),
@@ -451,6 +455,45 @@ def sv_adjoint_grad(n: int, dtype: int, gates, params, terms, checkpoint_every: 
                                   grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                   val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st))
     return val, grad
+
+
+def sv_adjoint_grad_rows(n: int, dtype: int, gates, params, terms, row_coeffs, checkpoint_every: int = 0,
+                         stream=None):
+    """sv_adjoint_grad with H_b = sum_j row_coeffs[b, j] P_j per state:
+    (values (batch,), gradients (batch, n_params))."""
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    pv = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if pv.ndim == 1:
+        pv = pv.reshape(1, -1)
+    batch, npar = pv.shape
+    arr = terms if isinstance(terms, ctypes.Array) else pauli_terms(terms)
+    nt = len(arr)
+    rc = np.ascontiguousarray(np.asarray(row_coeffs, dtype=np.float64))
+    if rc.shape != (batch, nt):
+        raise ValueError("row_coeffs must be (batch, n_terms) = (%d, %d)" % (batch, nt))
+    grad = np.zeros((batch, npar), dtype=np.float64)
+    val = np.zeros(batch, dtype=np.float64)
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().sv_adjoint_grad_rows(n, dtype, g.arr, g.n, pv.ctypes.data_as(dp), batch, npar, arr, nt,
+                                       rc.ctypes.data_as(dp), int(checkpoint_every), grad.ctypes.data_as(dp),
+                                       val.ctypes.data_as(dp), st))
+    return val, grad
+
+
+def sv_batch_expect_z(n: int, dtype: int, gates, params, stream=None) -> np.ndarray:
+    """(batch, n + 1): <Z_q> of U(params_b)|0..0> for every qubit, then their sum."""
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    pv = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if pv.ndim == 1:
+        pv = pv.reshape(1, -1)
+    batch, npar = pv.shape
+    out = np.zeros((batch, n + 1), dtype=np.float64)
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().sv_batch_expect_z(n, dtype, g.arr, g.n, pv.ctypes.data_as(dp), batch, npar, out.ctypes.data_as(dp),
+                                    st))
+    return out
 
 
 def sv_run_batch_small(n_qubits, gate_sets, dtype: int = SV_C64, out=None, stream=None):

@@ -729,6 +729,9 @@ struct PauliTilePass {
   uint64_t xg[kPauliTileTerms];       // x in global bits
   uint64_t z[kPauliTileTerms];
   double cr[kPauliTileTerms], ci[kPauliTileTerms];  // c_j i^{nY_j}
+  uint16_t orig[kPauliTileTerms];     // the term's index in the caller's list (per-state coefficients)
+  uint8_t ny[kPauliTileTerms];        // nY_j mod 4
+  int32_t nterms_all;                 // terms per state in the per-state coefficient rows
 };
 
 // The pass's coefficients in the state's precision (FP64 is a slow pipe on
@@ -738,9 +741,12 @@ struct PauliTileCoef {
   R cr, ci;
 };
 
+// With `rowc` (device, batch x nterms_all doubles) state b takes its own
+// coefficients c_{b,j} in place of P.cr / P.ci.
 template <typename R>
 __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ psi, Cx<R>* __restrict__ lam,
-                                                     const __grid_constant__ PauliTilePass P, uint64_t ntiles) {
+                                                     const __grid_constant__ PauliTilePass P, uint64_t ntiles,
+                                                     const double* __restrict__ rowc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
   const int tsz = 1 << P.m;
@@ -753,8 +759,10 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
       if (((uint32_t)c >> (i - P.L)) & 1u) off |= 1ull << P.tq[i];
     hi_off[c] = off;
   }
-  for (int j = threadIdx.x; j < P.nterms; j += blockDim.x) cf[j] = {(R)P.cr[j], (R)P.ci[j]};
+  if (!rowc)
+    for (int j = threadIdx.x; j < P.nterms; j += blockDim.x) cf[j] = {(R)P.cr[j], (R)P.ci[j]};
   __syncthreads();
+  uint64_t staged = ~0ull;  // state whose coefficients cf holds (per-state mode)
   const uint32_t lowmask = (1u << P.L) - 1u;
   const int per_state_log = P.n - P.m;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -762,6 +770,14 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
     uint64_t base = tile & ((1ull << per_state_log) - 1ull);
     for (int i = 0; i < P.m; i++) base = ins0_64(base, P.tq[i]);
     const uint64_t sbase = b << P.n;
+    if (rowc && b != staged) {  // every thread sees the same b: uniform branch
+      for (int j = threadIdx.x; j < P.nterms; j += blockDim.x) {
+        const R c = (R)rowc[b * (uint64_t)P.nterms_all + P.orig[j]];
+        const int ny = P.ny[j];
+        cf[j] = {ny == 0 ? c : ny == 2 ? -c : R(0), ny == 1 ? c : ny == 3 ? -c : R(0)};
+      }
+      staged = b;
+    }
     for (int l = threadIdx.x; l < tsz; l += blockDim.x)
       s[l] = psi[sbase + (base | hi_off[l >> P.L] | (l & lowmask))];
     __syncthreads();
@@ -905,7 +921,7 @@ cudaError_t launch_pauli_accum(const Cx<R>* psi, Cx<R>* lam, int n, int batch, u
 // fall back to one pass per mask (launch_pauli_accum).
 template <typename R>
 cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, const sv_pauli_term* terms,
-                               int nterms, bool accumulate, cudaStream_t stream) {
+                               int nterms, bool accumulate, const double* rowc, cudaStream_t stream) {
   const int L = std::min(n, sizeof(R) == 4 ? 5 : 4);
   const int m = std::min(n, sizeof(R) == 4 ? 13 : 12);  // 64 KiB tiles
   std::vector<int> idx(nterms);
@@ -933,6 +949,7 @@ cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, c
     P.n = n;
     P.m = m;
     P.L = L;
+    P.nterms_all = nterms;
     int loc[64], k = 0;
     for (int q = 0; q < n; q++)
       if ((T >> q) & 1ull) {
@@ -957,7 +974,7 @@ cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, c
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_tiles<R>, 256, smem);
       uint64_t grid = (uint64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
       if (grid > ntiles) grid = ntiles;
-      k_pauli_tiles<R><<<(unsigned)grid, 256, smem, stream>>>(psi, lam, P, ntiles);
+      k_pauli_tiles<R><<<(unsigned)grid, 256, smem, stream>>>(psi, lam, P, ntiles, rowc);
       acc = true;
       P.nterms = 0;
       return cudaGetLastError();
@@ -980,13 +997,18 @@ cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, c
       P.z[j] = terms[t].z_mask;
       P.cr[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
       P.ci[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
+      P.orig[j] = (uint16_t)t;
+      P.ny[j] = (uint8_t)ny;
       done[t] = 1;
       remaining--;
     }
     cudaError_t e = flush();
     if (e != cudaSuccess) return e;
   }
-  // masks wider than a tile: one pass per mask
+  // masks wider than a tile: one pass per mask (shared coefficients only)
+  if (rowc)
+    for (int t = 0; t < nterms; t++)
+      if (!done[t]) return cudaErrorNotSupported;
   for (int a = 0; a < nterms; a++) {
     const int t0 = idx[a];
     if (done[t0]) continue;
@@ -1038,7 +1060,7 @@ cudaError_t launch_grad_finish(const double* gscratch, int batch, int ngrad, int
   template cudaError_t launch_pauli_accum<R>(const Cx<R>*, Cx<R>*, int, int, uint64_t, const uint64_t*,           \
                                              const double*, int, bool, cudaStream_t);                             \
   template cudaError_t launch_pauli_tiles<R>(const Cx<R>*, Cx<R>*, int, int, const sv_pauli_term*, int, bool,      \
-                                             cudaStream_t);                                                       \
+                                             const double*, cudaStream_t);                                        \
   template cudaError_t launch_batch_dot<R>(const Cx<R>*, const Cx<R>*, int, int, double*, double*, cudaStream_t);
 SV_INST(float)
 SV_INST(double)

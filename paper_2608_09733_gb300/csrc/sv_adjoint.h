@@ -83,10 +83,12 @@ cudaError_t launch_batch_init(Cx<R>* psi, int n, int batch, cudaStream_t stream)
 template <typename R>
 cudaError_t launch_pauli_accum(const Cx<R>* psi, Cx<R>* lam, int n, int batch, uint64_t x, const uint64_t* z,
                                const double* c, int nt, bool accumulate, cudaStream_t stream);
-// lam (+)= sum_j c_j P_j psi over the batch, in tiles that hold whole X-masks.
+// lam (+)= sum_j c_j P_j psi over the batch, in tiles that hold whole X-masks;
+// with `row_coeffs` (device, batch x n_terms) state b uses c_{b,j} (then every
+// X-mask must fit a tile, else cudaErrorNotSupported).
 template <typename R>
 cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, const sv_pauli_term* terms,
-                               int n_terms, bool accumulate, cudaStream_t stream);
+                               int n_terms, bool accumulate, const double* row_coeffs, cudaStream_t stream);
 // out[b] = Re <psi_b|lam_b> (partials in scratch: batch x grid doubles)
 template <typename R>
 cudaError_t launch_batch_dot(const Cx<R>* psi, const Cx<R>* lam, int n, int batch, double* scratch, double* out,

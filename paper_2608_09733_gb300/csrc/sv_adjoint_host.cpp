@@ -232,9 +232,12 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
 }
 
 template <typename R>
+// With row_coeffs (host, batch x nterms) state b uses H_b = sum_j c_{b,j} P_j.
+// With out_z (host, batch x (n + 1)) only the forward pass runs and
+// <Z_q> of every state (then their sum) is returned.
 void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const double* params, int batch, int npar,
                  const sv_pauli_term* terms, size_t nterms, int ckpt, double* out_grad, double* out_value,
-                 cudaStream_t stream) {
+                 const double* row_coeffs, double* out_z, cudaStream_t stream) {
   // ---- lower the template
   std::vector<AGate> ag(ng);
   int npg = 0;
@@ -342,10 +345,35 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
                  "checkpoint store");
   }
 
+  // ---- forward-only: <Z_q> of every state
+  if (out_z) {
+    const size_t zn = (size_t)n + 1;
+    double* zscr = (double*)scratch_buffer(stream, "adj_zscratch", sizeof(double) * expect_z_all_scratch_doubles(n));
+    double* zdev = (double*)scratch_buffer(stream, "adj_zout", sizeof(double) * zn * batch);
+    for (int b = 0; b < batch; b++)
+      cuda_check(launch_expect_z_all<R>(psi + (size_t)b * N, n, zscr, expect_z_all_scratch_doubles(n),
+                                        zdev + (size_t)b * zn, stream),
+                 "per-state <Z>");
+    cuda_check(cudaMemcpyAsync(out_z, zdev, sizeof(double) * zn * batch, cudaMemcpyDeviceToHost, stream),
+               "<Z> copy");
+    cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    return;
+  }
+
   // ---- lambda = H psi (tiles that hold whole X-masks); f = Re <psi|lambda>
   {
+    double* rowc = nullptr;
+    if (row_coeffs) {
+      rowc = (double*)scratch_buffer(stream, "adj_rowc", sizeof(double) * nterms * batch);
+      cuda_check(cudaMemcpyAsync(rowc, row_coeffs, sizeof(double) * nterms * batch, cudaMemcpyHostToDevice, stream),
+                 "row coefficients upload");
+    }
     Prof pr(stream, "pauli_accum", 2.0 * (double)sbytes);
-    cuda_check(launch_pauli_tiles<R>(psi, lam, n, batch, terms, (int)nterms, false, stream), "H psi");
+    const cudaError_t e = launch_pauli_tiles<R>(psi, lam, n, batch, terms, (int)nterms, false, rowc, stream);
+    if (e == cudaErrorNotSupported)
+      fail(SV_ERR_UNSUPPORTED, "per-state coefficients need every X-mask to fit one tile of " +
+                                   std::to_string(dtype == SV_C64 ? 13 : 12) + " qubits (with the lowest ones)");
+    cuda_check(e, "H psi");
     pr.done();
     cuda_check(launch_batch_dot<R>(psi, lam, n, batch, dots, vout, stream), "value");
   }
@@ -392,35 +420,84 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
 
 using namespace sv;
 
+namespace {
+
+void check_adjoint_args(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
+                        int batch, int n_params, int checkpoint_every) {
+  if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+  if (n_qubits < 1 || n_qubits > 30) fail(SV_ERR_INVALID, "n_qubits must be in 1..30 for the adjoint");
+  if (batch < 1 || batch > 65535) fail(SV_ERR_INVALID, "batch must be in 1..65535");
+  if (n_params < 0) fail(SV_ERR_INVALID, "n_params must be >= 0");
+  if (n_params > 0 && !params) fail(SV_ERR_INVALID, "params is NULL");
+  if (checkpoint_every < 0) fail(SV_ERR_INVALID, "checkpoint_every must be >= 0");
+  validate_gates(n_qubits, gates, n_gates, (size_t)n_params);
+  for (int b = 0; b < batch; b++)
+    for (int p = 0; p < n_params; p++)
+      if (!std::isfinite(params[(size_t)b * n_params + p])) fail(SV_ERR_INVALID, "a parameter is not finite");
+}
+
+void check_terms(int n_qubits, const sv_pauli_term* terms, size_t n_terms) {
+  if (n_terms < 1 || n_terms > 4096 || !terms) fail(SV_ERR_INVALID, "n_terms must be in 1..4096");
+  const uint64_t all = (1ull << n_qubits) - 1ull;
+  for (size_t j = 0; j < n_terms; j++)
+    if ((terms[j].x_mask | terms[j].z_mask) & ~all)
+      fail(SV_ERR_INVALID, "term " + std::to_string(j) + " names a qubit beyond n_qubits");
+}
+
+void adjoint_dispatch(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
+                      int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
+                      double* out_grad, double* out_value, const double* row_coeffs, double* out_z, void* stream) {
+  static double dummy_grad;
+  double* og = n_params > 0 && out_grad ? out_grad : &dummy_grad;
+  if (dtype == SV_C64)
+    run_adjoint<float>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                       og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
+  else
+    run_adjoint<double>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                        og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
+}
+
+}  // namespace
+
 extern "C" sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
                                      const double* params, int batch, int n_params, const sv_pauli_term* terms,
                                      size_t n_terms, int checkpoint_every, double* out_grad, double* out_value,
                                      void* stream) {
   return guarded([&] {
-    if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
-    if (n_qubits < 1 || n_qubits > 30) fail(SV_ERR_INVALID, "n_qubits must be in 1..30 for the adjoint");
-    if (batch < 1 || batch > 65535) fail(SV_ERR_INVALID, "batch must be in 1..65535");
-    if (n_params < 0) fail(SV_ERR_INVALID, "n_params must be >= 0");
-    if (n_params > 0 && !params) fail(SV_ERR_INVALID, "params is NULL");
-    if (checkpoint_every < 0) fail(SV_ERR_INVALID, "checkpoint_every must be >= 0");
-    if (n_terms < 1 || n_terms > 4096 || !terms) fail(SV_ERR_INVALID, "n_terms must be in 1..4096");
+    check_adjoint_args(n_qubits, dtype, gates, n_gates, params, batch, n_params, checkpoint_every);
+    check_terms(n_qubits, terms, n_terms);
     if (!out_grad && n_params > 0) fail(SV_ERR_INVALID, "out_grad is NULL");
     if (!out_value) fail(SV_ERR_INVALID, "out_value is NULL");
-    const uint64_t all = (1ull << n_qubits) - 1ull;
-    for (size_t j = 0; j < n_terms; j++)
-      if ((terms[j].x_mask | terms[j].z_mask) & ~all)
-        fail(SV_ERR_INVALID, "term " + std::to_string(j) + " names a qubit beyond n_qubits");
-    validate_gates(n_qubits, gates, n_gates, (size_t)n_params);
-    for (int b = 0; b < batch; b++)
-      for (int p = 0; p < n_params; p++)
-        if (!std::isfinite(params[(size_t)b * n_params + p])) fail(SV_ERR_INVALID, "a parameter is not finite");
-    static double dummy_grad;
-    double* og = n_params > 0 ? out_grad : &dummy_grad;
-    if (dtype == SV_C64)
-      run_adjoint<float>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
-                         og, out_value, (cudaStream_t)stream);
-    else
-      run_adjoint<double>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
-                          og, out_value, (cudaStream_t)stream);
+    adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                     out_grad, out_value, nullptr, nullptr, stream);
+  });
+}
+
+extern "C" sv_status sv_adjoint_grad_rows(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                          const double* params, int batch, int n_params, const sv_pauli_term* terms,
+                                          size_t n_terms, const double* row_coeffs, int checkpoint_every,
+                                          double* out_grad, double* out_value, void* stream) {
+  return guarded([&] {
+    check_adjoint_args(n_qubits, dtype, gates, n_gates, params, batch, n_params, checkpoint_every);
+    check_terms(n_qubits, terms, n_terms);
+    if (!row_coeffs) fail(SV_ERR_INVALID, "row_coeffs is NULL");
+    for (size_t i = 0; i < (size_t)batch * n_terms; i++)
+      if (!std::isfinite(row_coeffs[i])) fail(SV_ERR_INVALID, "a coefficient is not finite");
+    if (!out_grad && n_params > 0) fail(SV_ERR_INVALID, "out_grad is NULL");
+    if (!out_value) fail(SV_ERR_INVALID, "out_value is NULL");
+    adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                     out_grad, out_value, row_coeffs, nullptr, stream);
+  });
+}
+
+extern "C" sv_status sv_batch_expect_z(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                       const double* params, int batch, int n_params, double* out_z, void* stream) {
+  return guarded([&] {
+    check_adjoint_args(n_qubits, dtype, gates, n_gates, params, batch, n_params, 0);
+    if (!out_z) fail(SV_ERR_INVALID, "out_z is NULL");
+    static const sv_pauli_term z0 = {0, 1, 1.0};  // unused: forward only
+    double value_unused = 0.0;
+    adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, &z0, 1, 0, nullptr, &value_unused,
+                     nullptr, out_z, stream);
   });
 }
