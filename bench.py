@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--workload", choices=["gates", "adjoint", "serving", "precision", "latency", "sampling",
-                                           "batchlayer"], default="gates")
+                                           "batchlayer", "checkpoint"], default="gates")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -513,6 +513,42 @@ def bench_batchlayer(args):
         flush=True)
 
 
+def bench_checkpoint(args):
+    """Adjoint checkpoint policies (Sec. 7.3) on a 24-qubit HEA, 10 layers,
+    batch 4, complex64, a segment every 2 layers: time per gradient batch and
+    the device memory the kept states take, for every state kept, 2 kept (the
+    rest recomputed) and none kept."""
+    import numpy as np
+    import paper_2608_09733_gb300 as sv
+    from workloads import hea_hamiltonian, hea_params, hea_ring
+    n, layers, batch = 24, 10, 4
+    gates, H = hea_ring(n, layers), hea_hamiltonian(n)
+    P = 2 * n * layers
+    params = hea_params(batch, P, seed=0)
+    per_layer = 3 * n
+    state_bytes = 8 * 2 ** n * batch
+    segments = layers // 2
+    rows, ref = [], None
+    for stored in (-1, 2, 0):
+        kw = dict(checkpoint_every=2 * per_layer, stored_states=stored)
+        for _ in range(max(1, args.warmup)):
+            sv.sv_adjoint_grad_ex(n, sv.SV_C64, gates, params, H, **kw)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, g = sv.sv_adjoint_grad_ex(n, sv.SV_C64, gates, params, H, **kw)
+        t = (time.perf_counter() - t0) / args.steps
+        ref = g if ref is None else ref
+        kept = segments - 1 if stored < 0 else min(stored, segments - 1)
+        rows.append({"stored_states": stored, "kept": kept, "kept_gb": kept * state_bytes / 1e9,
+                     "ms_per_batch": t * 1e3, "grads_per_s": batch / t,
+                     "max_grad_diff_vs_all_kept": float(np.abs(g - ref).max())})
+    print(json.dumps({
+        "metric": "adjoint checkpoint policies: time vs kept-state memory (24q HEA, 10 layers, batch 4, c64)",
+        "value": rows[0]["grads_per_s"], "unit": "grads/s (all kept)", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "c64", "data": "synthetic", "config": {"workload": "hea_adjoint_24q_10layers_batch4_ckpt2layers"},
+        "policies": rows}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -528,7 +564,8 @@ def main():
         _build.build()
         if rank == 0:
             {"adjoint": bench_adjoint, "serving": bench_serving, "precision": bench_precision,
-             "latency": bench_latency, "sampling": bench_sampling, "batchlayer": bench_batchlayer}[args.workload](args)
+             "latency": bench_latency, "sampling": bench_sampling, "batchlayer": bench_batchlayer,
+             "checkpoint": bench_checkpoint}[args.workload](args)
         return
 
     import numpy as np

@@ -56,14 +56,25 @@ typedef enum {
 
 typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
-/* Gate families (Sec. 4.2 gate table).  Controlled forms (CX, CZ, CRX, CCX,
- * controlled phase ...) are the base family with n_controls > 0. */
+/* Gate families (Sec. 4.2 gate table).  Controlled forms (CX, CY, CZ, CRX,
+ * CRY, CRZ, CCX, controlled phase ...) are the base family with
+ * n_controls > 0.  The excitation families rotate the two basis states that
+ * exchange one or two excitations and leave the rest alone, with
+ * c = cos(theta/2), s = sin(theta/2) and i the matrix index:
+ *   SV_GATE_EXC1 (single excitation / Givens, 2 targets): on i = 1, 2
+ *     (|t0 t1> = |10>, |01>) the block [[c, -s], [s, c]];
+ *   SV_GATE_EXC2 (double excitation, 4 targets): on i = 3, 12 (t0 t1 set,
+ *     t2 t3 set) the same block.
+ * Both are exp(-i theta G / 2) with G = Y on that pair of states and 0
+ * elsewhere (spectrum {-1, 0, 1}, which is why the paper's shift rule for
+ * them has four terms). */
 typedef enum {
   SV_GATE_I = 0, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_H,
   SV_GATE_S, SV_GATE_SDG, SV_GATE_T, SV_GATE_TDG, SV_GATE_SX,
   SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ, SV_GATE_P, SV_GATE_U2, SV_GATE_U3,
   SV_GATE_SWAP, SV_GATE_RXX, SV_GATE_RYY, SV_GATE_RZZ,
   SV_GATE_UNITARY,
+  SV_GATE_EXC1, SV_GATE_EXC2,
   SV_GATE_COUNT_
 } sv_gate_type;
 
@@ -73,8 +84,8 @@ typedef enum {
 
 /* One circuit operation (Sec. 4.2).
  *   type             sv_gate_type
- *   n_targets        1 for one-qubit families, 2 for SWAP/RXX/RYY/RZZ,
- *                    1..5 for SV_GATE_UNITARY
+ *   n_targets        1 for one-qubit families, 2 for SWAP/RXX/RYY/RZZ/EXC1,
+ *                    4 for EXC2, 1..5 for SV_GATE_UNITARY
  *   targets          target qubits; targets[0] = least significant matrix bit
  *   n_controls       0..5 control qubits, distinct from the targets
  *   control_zero_mask bit j set: controls[j] enables the gate when it is |0>
@@ -83,7 +94,7 @@ typedef enum {
  *                    param_values[param_slot[i]] of the call (a shared
  *                    parameter vector); a slot beyond the supplied vector is
  *                    SV_ERR_UNBOUND_PARAM
- *   params           angles: RX/RY/RZ/P/RXX/RYY/RZZ use params[0]; U2 uses
+ *   params           angles: RX/RY/RZ/P/RXX/RYY/RZZ/EXC1/EXC2 use params[0]; U2 uses
  *                    (phi, lambda); U3 uses (theta, phi, lambda)
  *   matrix           SV_GATE_UNITARY only: host pointer to 2^k x 2^k complex
  *                    entries, row-major, interleaved (re, im) doubles; read
@@ -253,7 +264,7 @@ sv_status sv_emulate_apply(int n_qubits, sv_dtype dtype, const sv_gate* gates, s
  * derivative of Sec. 4.2).  At each checkpoint the reverse pass replaces psi
  * by the stored forward state, which bounds the complex64 uncompute drift.
  *   gates            template; parameterised gates (param_slot[0] >= 0) must
- *                    be RX, RY, RZ, P, RXX, RYY or RZZ (else
+ *                    be RX, RY, RZ, P, RXX, RYY, RZZ or EXC1 (else
  *                    SV_ERR_UNSUPPORTED); every gate has <= 2 targets
  *   params           host, batch x n_params doubles, row-major; row b binds
  *                    the slots of state b
@@ -270,6 +281,34 @@ sv_status sv_emulate_apply(int n_qubits, sv_dtype dtype, const sv_gate* gates, s
 sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
                           int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
                           double* out_grad, double* out_value, void* stream);
+
+/* Checkpoint policy of the adjoint (Sec. 7.3: no checkpointing, a
+ * user-selected interval, or automatic placement; discarded states are
+ * recomputed in the backward pass).
+ *   checkpoint_every     gates per segment: the reverse pass re-anchors psi
+ *                        at every segment start (0 = never: psi is only
+ *                        uncomputed, gate by gate)
+ *   stored_states        -1: keep every segment-start state from the forward
+ *                        pass (memory: segments x batch x 2^n amplitudes);
+ *                        k >= 0: keep at most k of them, evenly spaced; the
+ *                        others are recomputed in the reverse pass by applying
+ *                        the gates again from the nearest kept state below
+ *                        (or from |0..0>)
+ *   memory_budget_bytes  > 0: automatic placement, stored_states = the number
+ *                        of batch states the budget holds (overrides
+ *                        stored_states) */
+typedef struct sv_adjoint_opts {
+  int32_t checkpoint_every;
+  int32_t stored_states;
+  double memory_budget_bytes;
+} sv_adjoint_opts;
+
+/* sv_adjoint_grad with a checkpoint policy (sv_adjoint_opts); the results are
+ * the same whatever the policy, up to rounding. */
+sv_status sv_adjoint_grad_ex(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                             const double* params, int batch, int n_params, const sv_pauli_term* terms,
+                             size_t n_terms, const sv_adjoint_opts* opts, double* out_grad, double* out_value,
+                             void* stream);
 
 /* sv_adjoint_grad with a Hamiltonian per state: state b uses
  * H_b = sum_j row_coeffs[b * n_terms + j] P_j (the coeff field of `terms` is

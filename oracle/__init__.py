@@ -37,8 +37,10 @@ KINDS = {
     "i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,
     "rx": 10, "ry": 11, "rz": 12, "p": 13, "u2": 14, "u3": 15,
     "swap": 16, "rxx": 17, "ryy": 18, "rzz": 19, "unitary": 20,
+    "exc1": 21, "exc2": 22,
 }
-ROTATIONS = {"rx", "ry", "rz", "p", "rxx", "ryy", "rzz"}
+ROTATIONS = {"rx", "ry", "rz", "p", "rxx", "ryy", "rzz", "exc1", "exc2"}
+EXCITATIONS = {"exc1", "exc2"}  # generators with spectrum {-1, 0, 1}: four-term shift rule
 
 
 class OGGate(ctypes.Structure):
@@ -292,15 +294,24 @@ def param_shift_grad(n: int, gates, param_values, terms, n_slots: int) -> np.nda
             # distance 2 apart; a control projector adds a third eigenvalue
             raise ValueError("shift rule needs an uncontrolled rotation at gate %d" % i)
         s = g.slots[0]
-        vals = []
-        for shift in (+math.pi / 2, -math.pi / 2):
+
+        def shifted(shift):
             gs = list(base)
             h = copy.copy(g)
             h.params = [float(param_values[s]) + shift] + list(g.params[1:])
             h.slots = [-1] + list(g.slots[1:])
             gs[i] = h
-            vals.append(energy(n, gs, param_values, terms))
-        grad[s] += 0.5 * (vals[0] - vals[1])
+            return energy(n, gs, param_values, terms)
+        if g.name in EXCITATIONS:
+            # generator spectrum {-1, 0, 1}: f has frequencies 1/2 and 1 in
+            # theta, and the four-term rule (Sec. 4.2) with shifts pi/2 and
+            # 3 pi/2 and weights (sqrt2 +- 1) / (4 sqrt2) is exact
+            c1 = (math.sqrt(2) + 1) / (4 * math.sqrt(2))
+            c2 = (math.sqrt(2) - 1) / (4 * math.sqrt(2))
+            grad[s] += c1 * (shifted(math.pi / 2) - shifted(-math.pi / 2)) \
+                - c2 * (shifted(3 * math.pi / 2) - shifted(-3 * math.pi / 2))
+        else:
+            grad[s] += 0.5 * (shifted(math.pi / 2) - shifted(-math.pi / 2))
     return grad
 
 

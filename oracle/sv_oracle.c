@@ -48,7 +48,7 @@ typedef double complex cplx;
 enum {
   OK_I = 0, OK_X, OK_Y, OK_Z, OK_H, OK_S, OK_SDG, OK_T, OK_TDG, OK_SX,
   OK_RX, OK_RY, OK_RZ, OK_P, OK_U2, OK_U3,
-  OK_SWAP, OK_RXX, OK_RYY, OK_RZZ, OK_UNITARY, OK_NKINDS
+  OK_SWAP, OK_RXX, OK_RYY, OK_RZZ, OK_UNITARY, OK_EXC1, OK_EXC2, OK_NKINDS
 };
 
 #define OG_MAXQ 10
@@ -146,6 +146,20 @@ int og_gate_matrix(const og_gate* g, double* out_re_im) {
       d = 1 << g->nt;
       for (int i = 0; i < d * d; i++) U[i] = g->mat[2 * i] + I * g->mat[2 * i + 1];
       break;
+    case OK_EXC1:
+    case OK_EXC2: {
+      /* Single / double excitation (Sec. 4.2 gate table): the two basis states
+       * that exchange the excitation(s) -- matrix indices 1, 2 (|t0 t1> =
+       * |10>, |01>) or 3, 12 (t0 t1 set, t2 t3 set) -- rotate by
+       * [[cos, -sin], [sin, cos]] of theta/2; every other state is unchanged. */
+      d = g->kind == OK_EXC1 ? 4 : 16;
+      const int a = g->kind == OK_EXC1 ? 1 : 3, b = g->kind == OK_EXC1 ? 2 : 12;
+      const double c = cos(g->p[0] / 2.0), s = sin(g->p[0] / 2.0);
+      for (int i = 0; i < d * d; i++) U[i] = 0;
+      for (int i = 0; i < d; i++) U[i * d + i] = 1;
+      U[a * d + a] = c; U[a * d + b] = -s; U[b * d + a] = s; U[b * d + b] = c;
+      break;
+    }
     default: return 0;
   }
   for (int i = 0; i < d * d; i++) {
@@ -306,7 +320,7 @@ void og_inner(const cplx* a, const cplx* b, int n, double* re, double* im) {
  * on its targets (without the control projector).  Returns its dimension,
  * or 0 for a gate that has no such generator. */
 static int generator(const og_gate* g, double* G) {
-  cplx P[16], Q[4], R[4];
+  cplx P[256], Q[4], R[4];
   int d;
   switch (g->kind) {
     case OK_RX: pauli_1q(1, P); d = 2; break;
@@ -321,6 +335,14 @@ static int generator(const og_gate* g, double* G) {
       for (int r = 0; r < 4; r++)
         for (int q = 0; q < 4; q++) P[r * 4 + q] = Q[(r >> 1) * 2 + (q >> 1)] * R[(r & 1) * 2 + (q & 1)];
       d = 4;
+      break;
+    }
+    case OK_EXC1: case OK_EXC2: { /* Y on the pair of states the gate rotates */
+      d = g->kind == OK_EXC1 ? 4 : 16;
+      const int a = g->kind == OK_EXC1 ? 1 : 3, b = g->kind == OK_EXC1 ? 2 : 12;
+      for (int i = 0; i < d * d; i++) P[i] = 0;
+      P[a * d + b] = -I;
+      P[b * d + a] = I;
       break;
     }
     default: return 0;
@@ -365,7 +387,7 @@ int og_adjoint_grad(int n, const og_gate* gates, int ng, const uint64_t* xs, con
   for (int k = ng - 1; k >= 0; k--) {
     const og_gate* g = &gates[k];
     if (g->slot >= 0) {
-      double G[2 * 16];
+      double G[2 * 256];
       if (!generator(g, G)) { rc = -1; break; }
       /* proj = (control projector (x) G) psi: zero the amplitudes that fail
        * the controls, then apply G on the targets. */

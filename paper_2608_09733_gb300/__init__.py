@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     load,
     pauli_terms,
     sv_adjoint_grad,
+    sv_adjoint_grad_ex,
     sv_adjoint_grad_rows,
     sv_batch_expect_z,
     sv_apply_circuit,

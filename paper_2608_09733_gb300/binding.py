@@ -28,6 +28,7 @@ GATE_TYPES = {
     "i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,
     "rx": 10, "ry": 11, "rz": 12, "p": 13, "u2": 14, "u3": 15,
     "swap": 16, "rxx": 17, "ryy": 18, "rzz": 19, "unitary": 20,
+    "exc1": 21, "exc2": 22,
 }
 
 # Every symbol include/sv.h declares (checked by the CPU tests).
@@ -36,7 +37,7 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
            "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample", "sv_adjoint_grad_rows",
-           "sv_batch_expect_z"]
+           "sv_batch_expect_z", "sv_adjoint_grad_ex"]
 
 
 class SvError(RuntimeError):
@@ -73,6 +74,11 @@ class SvProfileEntry(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
+class SvAdjointOpts(ctypes.Structure):
+    _fields_ = [("checkpoint_every", ctypes.c_int32), ("stored_states", ctypes.c_int32),
+                ("memory_budget_bytes", ctypes.c_double)]
+
+
 class SvPauliTerm(ctypes.Structure):
     _fields_ = [("x_mask", ctypes.c_uint64), ("z_mask", ctypes.c_uint64), ("coeff", ctypes.c_double)]
 
@@ -105,6 +111,8 @@ def load():
             "sv_adjoint_grad_rows": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(SvPauliTerm), sz, P(cd), ci, P(cd),
                                       P(cd), vp], ci),
             "sv_batch_expect_z": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(cd), vp], ci),
+            "sv_adjoint_grad_ex": ([ci, ci, P(SvGate), sz, P(cd), ci, ci, P(SvPauliTerm), sz, P(SvAdjointOpts),
+                                    P(cd), P(cd), vp], ci),
             "sv_run_host": ([ci, ci, vp, P(SvGate), sz, P(cd), sz, ci, P(cd), vp, vp], ci),
             "sv_alloc": ([ci, ci, vp, P(vp)], ci),
             "sv_free": ([vp], ci),
@@ -454,6 +462,27 @@ def sv_adjoint_grad(n: int, dtype: int, gates, params, terms, checkpoint_every: 
                                   npar, arr, nt, int(checkpoint_every),
                                   grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                   val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st))
+    return val, grad
+
+
+def sv_adjoint_grad_ex(n: int, dtype: int, gates, params, terms, checkpoint_every: int = 0,
+                       stored_states: int = -1, memory_budget_bytes: float = 0.0, stream=None):
+    """sv_adjoint_grad with a checkpoint policy: keep stored_states of the
+    segment-start states (-1: all) or as many as memory_budget_bytes holds;
+    the others are recomputed in the reverse pass."""
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    pv = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if pv.ndim == 1:
+        pv = pv.reshape(1, -1)
+    batch, npar = pv.shape
+    arr = terms if isinstance(terms, ctypes.Array) else pauli_terms(terms)
+    grad = np.zeros((batch, npar), dtype=np.float64)
+    val = np.zeros(batch, dtype=np.float64)
+    o = SvAdjointOpts(int(checkpoint_every), int(stored_states), float(memory_budget_bytes))
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().sv_adjoint_grad_ex(n, dtype, g.arr, g.n, pv.ctypes.data_as(dp), batch, npar, arr, len(arr),
+                                     ctypes.byref(o), grad.ctypes.data_as(dp), val.ctypes.data_as(dp), st))
     return val, grad
 
 

@@ -27,7 +27,7 @@ namespace {
 
 bool is_rotation(int t) {
   return t == SV_GATE_RX || t == SV_GATE_RY || t == SV_GATE_RZ || t == SV_GATE_P || t == SV_GATE_RXX ||
-         t == SV_GATE_RYY || t == SV_GATE_RZZ;
+         t == SV_GATE_RYY || t == SV_GATE_RZZ || t == SV_GATE_EXC1 || t == SV_GATE_EXC2;
 }
 bool rotation_is_diagonal(int t) { return t == SV_GATE_RZ || t == SV_GATE_P || t == SV_GATE_RZZ; }
 
@@ -50,6 +50,12 @@ std::vector<cplx> generator_of(int t) {
       std::vector<cplx> m(16, 0.0);
       m[0 * 4 + 3] = m[3 * 4 + 0] = -1.0;
       m[1 * 4 + 2] = m[2 * 4 + 1] = 1.0;
+      return m;
+    }
+    case SV_GATE_EXC1: {  // Y on the pair (|10>, |01>) = indices (1, 2)
+      std::vector<cplx> m(16, 0.0);
+      m[1 * 4 + 2] = -j;
+      m[2 * 4 + 1] = j;
       return m;
     }
     default: return {};
@@ -235,9 +241,12 @@ template <typename R>
 // With row_coeffs (host, batch x nterms) state b uses H_b = sum_j c_{b,j} P_j.
 // With out_z (host, batch x (n + 1)) only the forward pass runs and
 // <Z_q> of every state (then their sum) is returned.
+// stored: how many of the segment-start states to keep (-1: all of them);
+// the others are recomputed in the reverse pass by applying the gates again
+// from the nearest kept state below (or |0..0>).
 void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const double* params, int batch, int npar,
-                 const sv_pauli_term* terms, size_t nterms, int ckpt, double* out_grad, double* out_value,
-                 const double* row_coeffs, double* out_z, cudaStream_t stream) {
+                 const sv_pauli_term* terms, size_t nterms, int ckpt, int stored, double* out_grad,
+                 double* out_value, const double* row_coeffs, double* out_z, cudaStream_t stream) {
   // ---- lower the template
   std::vector<AGate> ag(ng);
   int npg = 0;
@@ -254,7 +263,7 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
       if (!is_rotation(g.type) || g.param_slot[0] < 0)
         fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) +
                                      ": a parameterised gate needs a generator, exp(-i theta G / 2) "
-                                     "(RX, RY, RZ, P, RXX, RYY, RZZ)");
+                                     "(RX, RY, RZ, P, RXX, RYY, RZZ, EXC1)");
       a.param = true;
       a.slot = g.param_slot[0];
       a.pidx = npg++;
@@ -310,7 +319,11 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   const int grid_x = batch_grid_x(n, m, batch);
   Cx<R>* psi = (Cx<R>*)scratch_buffer(stream, "adj_psi", sbytes);
   Cx<R>* lam = (Cx<R>*)scratch_buffer(stream, "adj_lam", sbytes);
-  Cx<R>* ck = nck ? (Cx<R>*)scratch_buffer(stream, "adj_ckpt", sbytes * nck) : nullptr;
+  // boundaries j = 1..nck (the state after j*c gates); kept ones get a slot
+  std::vector<int> slot_of(nck + 1, -1);
+  int nkeep = stored < 0 ? nck : std::min(stored, nck);
+  for (int i = 0; i < nkeep; i++) slot_of[(int)(((long long)(i + 1) * nck) / nkeep)] = i;  // evenly spaced
+  Cx<R>* ck = nkeep ? (Cx<R>*)scratch_buffer(stream, "adj_ckpt", sbytes * nkeep) : nullptr;
   Cx<R>* dtab = (Cx<R>*)scratch_buffer(stream, "adj_table", table.size() * sizeof(Cx<R>));
   double* gscr = (double*)scratch_buffer(stream, "adj_gscratch", sizeof(double) * (size_t)batch * std::max(npg, 1) * grid_x);
   double* gout = (double*)scratch_buffer(stream, "adj_gout", sizeof(double) * (size_t)batch * std::max(npg, 1));
@@ -323,27 +336,32 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   const int pool_cap = BatchProgram<R>::kPool / 2;
   const double sweep_bytes_f = 2.0 * (double)sbytes, sweep_bytes_r = 4.0 * (double)sbytes;
 
-  // ---- forward, segment by segment
+  // ---- forward over gates [g0, g1) in segments of c, keeping the chosen
+  // segment-start states when `keep`
+  auto forward = [&](size_t g0, size_t g1, bool keep) {
+    for (size_t a = g0; a < g1; a += c) {
+      const size_t b = std::min(g1, a + c);
+      std::vector<int> order;
+      std::vector<LOp> ops;
+      for (size_t i = a; i < b; i++) {
+        order.push_back((int)i);
+        ops.push_back(ag[i].op);
+      }
+      std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, pool_cap, 64);
+      for (const Sweep& sw : sws) {
+        fill_program<R>(ag, order, sw, n, batch, npg, false, *prog);
+        Prof pr(stream, "batch_sweep_fwd", sweep_bytes_f);
+        cuda_check(launch_batch_sweep<R>(psi, nullptr, dtab, gscr, grid_x, *prog, false, stream), "forward sweep");
+        pr.done();
+      }
+      const int j = (int)(b / c);  // boundary reached (state after j*c gates)
+      if (keep && b % c == 0 && j >= 1 && j <= nck && slot_of[j] >= 0)
+        cuda_check(cudaMemcpyAsync(ck + (size_t)slot_of[j] * N * batch, psi, sbytes, cudaMemcpyDeviceToDevice, stream),
+                   "checkpoint store");
+    }
+  };
   cuda_check(launch_batch_init<R>(psi, n, batch, stream), "batch init");
-  for (int seg = 0; (size_t)seg * c < ng; seg++) {
-    size_t g0 = (size_t)seg * c, g1 = std::min(ng, g0 + c);
-    std::vector<int> order;
-    std::vector<LOp> ops;
-    for (size_t i = g0; i < g1; i++) {
-      order.push_back((int)i);
-      ops.push_back(ag[i].op);
-    }
-    std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, pool_cap, 64);
-    for (const Sweep& sw : sws) {
-      fill_program<R>(ag, order, sw, n, batch, npg, false, *prog);
-      Prof pr(stream, "batch_sweep_fwd", sweep_bytes_f);
-      cuda_check(launch_batch_sweep<R>(psi, nullptr, dtab, gscr, grid_x, *prog, false, stream), "forward sweep");
-      pr.done();
-    }
-    if (g1 < ng && seg + 1 <= nck)
-      cuda_check(cudaMemcpyAsync(ck + (size_t)seg * N * batch, psi, sbytes, cudaMemcpyDeviceToDevice, stream),
-                 "checkpoint store");
-  }
+  forward(0, ng, true);
 
   // ---- forward-only: <Z_q> of every state
   if (out_z) {
@@ -395,9 +413,23 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
       cuda_check(launch_batch_sweep<R>(psi, lam, dtab, gscr, grid_x, *prog, true, stream), "reverse sweep");
       pr.done();
     }
-    if (seg >= 1 && seg <= nck)  // psi is now psi after seg*c gates: take the stored copy
-      cuda_check(cudaMemcpyAsync(psi, ck + (size_t)(seg - 1) * N * batch, sbytes, cudaMemcpyDeviceToDevice, stream),
-                 "checkpoint load");
+    if (seg >= 1 && seg <= nck) {  // psi is now psi after seg*c gates: re-anchor it
+      if (slot_of[seg] >= 0) {
+        cuda_check(cudaMemcpyAsync(psi, ck + (size_t)slot_of[seg] * N * batch, sbytes, cudaMemcpyDeviceToDevice,
+                                   stream),
+                   "checkpoint load");
+      } else {  // recompute from the nearest kept state below, or from |0..0>
+        int i = seg - 1;
+        while (i >= 1 && slot_of[i] < 0) i--;
+        if (i >= 1)
+          cuda_check(cudaMemcpyAsync(psi, ck + (size_t)slot_of[i] * N * batch, sbytes, cudaMemcpyDeviceToDevice,
+                                     stream),
+                     "checkpoint load");
+        else
+          cuda_check(launch_batch_init<R>(psi, n, batch, stream), "batch init");
+        forward((size_t)(i >= 1 ? i : 0) * c, (size_t)seg * c, false);
+      }
+    }
   }
   if (npg) cuda_check(launch_grad_finish(gscr, batch, npg, grid_x, gout, stream), "gradient reduce");
 
@@ -446,15 +478,16 @@ void check_terms(int n_qubits, const sv_pauli_term* terms, size_t n_terms) {
 
 void adjoint_dispatch(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
                       int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
-                      double* out_grad, double* out_value, const double* row_coeffs, double* out_z, void* stream) {
+                      double* out_grad, double* out_value, const double* row_coeffs, double* out_z, void* stream,
+                      int stored = -1) {
   static double dummy_grad;
   double* og = n_params > 0 && out_grad ? out_grad : &dummy_grad;
   if (dtype == SV_C64)
     run_adjoint<float>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
-                       og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
+                       stored, og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
   else
     run_adjoint<double>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
-                        og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
+                        stored, og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -499,5 +532,28 @@ extern "C" sv_status sv_batch_expect_z(int n_qubits, sv_dtype dtype, const sv_ga
     double value_unused = 0.0;
     adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, &z0, 1, 0, nullptr, &value_unused,
                      nullptr, out_z, stream);
+  });
+}
+
+extern "C" sv_status sv_adjoint_grad_ex(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                        const double* params, int batch, int n_params, const sv_pauli_term* terms,
+                                        size_t n_terms, const sv_adjoint_opts* opts, double* out_grad,
+                                        double* out_value, void* stream) {
+  return guarded([&] {
+    if (!opts) fail(SV_ERR_INVALID, "opts is NULL");
+    check_adjoint_args(n_qubits, dtype, gates, n_gates, params, batch, n_params, opts->checkpoint_every);
+    check_terms(n_qubits, terms, n_terms);
+    if (!out_grad && n_params > 0) fail(SV_ERR_INVALID, "out_grad is NULL");
+    if (!out_value) fail(SV_ERR_INVALID, "out_value is NULL");
+    if (opts->stored_states < -1) fail(SV_ERR_INVALID, "stored_states must be >= -1");
+    if (!(opts->memory_budget_bytes >= 0.0)) fail(SV_ERR_INVALID, "memory_budget_bytes must be >= 0");
+    int stored = opts->stored_states;
+    if (opts->memory_budget_bytes > 0.0) {  // automatic placement: as many states as the budget holds
+      const double state_bytes = (double)(dtype == SV_C64 ? 8 : 16) * (double)(1ull << n_qubits) * (double)batch;
+      const double fit = std::floor(opts->memory_budget_bytes / state_bytes);
+      stored = fit > 1e9 ? -1 : (int)fit;
+    }
+    adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms,
+                     opts->checkpoint_every, out_grad, out_value, nullptr, nullptr, stream, stored);
   });
 }

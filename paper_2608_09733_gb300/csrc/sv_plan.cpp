@@ -23,8 +23,9 @@ namespace {
 const int kTargetsOf[SV_GATE_COUNT_] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1,  // I..SX
                                         1, 1, 1, 1, 1, 1,              // RX..U3
                                         2, 2, 2, 2,                    // SWAP, RXX, RYY, RZZ
-                                        -1};                           // UNITARY
-const int kAnglesOf[SV_GATE_COUNT_] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 3, 0, 1, 1, 1, 0};
+                                        -1,                            // UNITARY
+                                        2, 4};                         // EXC1, EXC2
+const int kAnglesOf[SV_GATE_COUNT_] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 3, 0, 1, 1, 1, 0, 1, 1};
 
 uint64_t gate_qubit_mask(const sv_gate& g) {
   uint64_t m = 0;
@@ -158,6 +159,21 @@ std::vector<cplx> gate_matrix(const sv_gate& g, const double* pv) {
       int d = 1 << g.n_targets;
       std::vector<cplx> m(d * d);
       for (int i = 0; i < d * d; i++) m[i] = cplx(g.matrix[2 * i], g.matrix[2 * i + 1]);
+      return m;
+    }
+    case SV_GATE_EXC1:
+    case SV_GATE_EXC2: {
+      // identity except the rotation [[c, -s], [s, c]] on the two states that
+      // exchange the excitation: indices (1, 2) of 4, or (3, 12) of 16
+      const int d = g.type == SV_GATE_EXC1 ? 4 : 16, a = g.type == SV_GATE_EXC1 ? 1 : 3,
+                b = g.type == SV_GATE_EXC1 ? 2 : 12;
+      const double c = std::cos(0.5 * ang(0)), s = std::sin(0.5 * ang(0));
+      std::vector<cplx> m(d * d, 0.0);
+      for (int r = 0; r < d; r++) m[r * d + r] = 1.0;
+      m[a * d + a] = c;
+      m[a * d + b] = -s;
+      m[b * d + a] = s;
+      m[b * d + b] = c;
       return m;
     }
     default: fail(SV_ERR_INVALID, "unknown gate type");

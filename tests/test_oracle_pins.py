@@ -377,3 +377,66 @@ def test_fusion_block_boundaries_on_a_known_sequence():
     # no reordering: H0 X1 H0 with k=1 stays three blocks
     g2 = [Gate("h", [0]), Gate("x", [1]), Gate("h", [0])]
     assert len(oracle.fuse(2, g2, 1)) == 3
+
+
+# ---------------------------------------------------------------- excitation gates
+# Single and double excitation (Sec. 4.2 gate table): a rotation by theta/2
+# between the two basis states that exchange the excitation(s), identity on
+# every other state; generator spectrum {-1, 0, 1} (four-term shift rule).
+
+def _basis(n, bits):
+    psi = np.zeros(2 ** n, complex)
+    psi[sum(1 << q for q in bits)] = 1.0
+    return psi
+
+
+def test_exc1_rotates_the_exchanged_pair():
+    from workloads import Gate
+    n, th = 4, 0.83
+    c, s = np.cos(th / 2), np.sin(th / 2)
+    out = oracle.run(n, [Gate("exc1", [1, 3], params=[th])], init=_basis(n, [1]))  # |t0 t1> = |10>
+    want = c * _basis(n, [1]) + s * _basis(n, [3])
+    assert np.abs(out - want).max() < 1e-15
+    for occ in ([], [1, 3], [0, 2]):  # |00>, |11> and spectators: unchanged
+        assert np.abs(oracle.run(n, [Gate("exc1", [1, 3], params=[th])], init=_basis(n, occ)) - _basis(n, occ)).max() == 0
+
+
+def test_exc2_rotates_the_exchanged_pair():
+    from workloads import Gate
+    n, th = 5, -1.37
+    c, s = np.cos(th / 2), np.sin(th / 2)
+    t = [4, 0, 3, 1]
+    out = oracle.run(n, [Gate("exc2", t, params=[th])], init=_basis(n, [4, 0]))
+    assert np.abs(out - (c * _basis(n, [4, 0]) + s * _basis(n, [3, 1]))).max() < 1e-15
+    out = oracle.run(n, [Gate("exc2", t, params=[th])], init=_basis(n, [3, 1]))
+    assert np.abs(out - (-s * _basis(n, [4, 0]) + c * _basis(n, [3, 1]))).max() < 1e-15
+    assert np.abs(oracle.run(n, [Gate("exc2", t, params=[th])], init=_basis(n, [4, 3])) - _basis(n, [4, 3])).max() == 0
+
+
+def test_excitations_conserve_the_number_of_ones():
+    from workloads import Gate
+    rng = np.random.default_rng(4)
+    n = 7
+    gates = []
+    for _ in range(40):
+        q = [int(x) for x in rng.permutation(n)[:4]]
+        gates.append(Gate("exc1", q[:2], params=[rng.uniform(0, 6.3)]) if rng.random() < 0.5
+                     else Gate("exc2", q, params=[rng.uniform(0, 6.3)]))
+    out = oracle.run(n, gates, init=_basis(n, [0, 2, 5]))
+    weights = np.array([bin(i).count("1") for i in range(2 ** n)])
+    assert np.abs(out[weights != 3]).max() < 1e-14
+    assert abs(np.linalg.norm(out) - 1) < 1e-13
+
+
+def test_excitation_gradients_four_term_rule_fd_and_adjoint_agree():
+    from workloads import Gate, Term
+    n = 6
+    gates = random_circuit(n, 25, seed=8) + [Gate("exc1", [1, 3], slots=[0]), Gate("ry", [2], slots=[1]),
+                                             Gate("exc2", [0, 2, 4, 5], slots=[2]), Gate("exc1", [4, 0], slots=[3])]
+    pv = np.array([0.3, 1.1, -0.7, 2.0])
+    H = [Term("ZZ", [0, 1], 0.6), Term("X", [3], 0.4), Term("YZ", [2, 5], -0.8)]
+    _, adj = oracle.adjoint_grad(n, gates, pv, H, 4)
+    shift = oracle.param_shift_grad(n, gates, pv, H, 4)
+    fd = oracle.fd_grad(n, gates, pv, H, 4)
+    assert np.abs(shift - adj).max() < 1e-12  # the four-term rule is exact
+    assert np.abs(fd - adj).max() < 1e-6      # O(h^2), h = 1e-3

@@ -25,7 +25,7 @@ GATE_ARITY = {
     "rx": (1, 1), "ry": (1, 1), "rz": (1, 1), "p": (1, 1),
     "u2": (1, 2), "u3": (1, 3),
     "swap": (2, 0), "rxx": (2, 1), "ryy": (2, 1), "rzz": (2, 1),
-    "unitary": (None, 0),
+    "unitary": (None, 0), "exc1": (2, 1), "exc2": (4, 1),
 }
 
 
