@@ -66,6 +66,25 @@ def parse_args():
     return ap.parse_args()
 
 
+def max_over_ranks(ms: float, ws: int, device) -> float:
+    """The job's time for the timed steps: the slowest rank's (all-reduce
+    MAX over the process group), then a barrier.  One rank: its own."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, steps: int, ws: int, ms: float) -> float:
+    """Whole-job throughput: every rank processes its own replica of the
+    workload (weak scaling), so the units of all ranks over the job's time."""
+    return ws * steps * units_per_rank_step / (ms / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -620,17 +639,12 @@ def main():
     torch.cuda.synchronize()
     prof = sv.sv_profile_read(reset=True)
     sv.sv_profile_enable(False)
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     clk = clocks.stop(None) if rank == 0 else None
 
     bytes_step = (2 * npasses + 2) * (2 ** n) * amp  # passes r+w, init write, read-out read
-    value = ws * args.steps * bytes_step / (ms / 1e3) / 1e9
-    gates_per_s = ws * args.steps * len(gates) / (ms / 1e3)
+    value = job_rate(bytes_step, args.steps, ws, ms) / 1e9
+    gates_per_s = job_rate(len(gates), args.steps, ws, ms)
     peaks, peak_src = measured_peaks()
     sw = prof.get("sweep", {"launches": 0, "total_ms": float("nan"), "bytes": 0.0})
     launches = sum(v["launches"] for v in prof.values()) + args.steps  # + init kernel per step
