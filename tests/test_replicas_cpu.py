@@ -33,7 +33,7 @@ def _rank(rank, ws, port, out):
 def test_two_replicas_take_the_slowest_time_and_sum_the_work():
     import torch.multiprocessing as mp
     ws, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_rank, args=(ws, port, out), nprocs=ws, start_method="spawn", join=True)
         res = dict(out)
