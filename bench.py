@@ -187,8 +187,9 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic",
-            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers" % (n, args.layers), "n_qubits": n,
-                       "gates_per_step": sample},
+            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers_%s" % (n, args.layers, args.dtype),
+                       "n_qubits": n, "layers": args.layers, "gates": len(gates), "gates_per_step": sample,
+                       "parallelism": "single"},
             "gates_per_s": args.steps * sample / t,
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.n_threads(), "kind": "oracle",
                              "sample": "%d consecutive gates of the %d-gate circuit per step on a %d-qubit "
