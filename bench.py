@@ -292,7 +292,7 @@ def bench_adjoint(args):
     rev = prof.get("batch_sweep_rev", {"bytes": 0, "total_ms": float("nan"), "launches": 0})
     gbs = rev["bytes"] / (rev["total_ms"] / 1e3) / 1e9 if rev["launches"] else None
     print(json.dumps({
-        "metric": "adjoint grads/s (20q HEA, 400 params, batch 64, c64)", "value": args.steps * batch / t,
+        "metric": "adjoint grads/s (20q HEA, 400 params, batch %d, c64)" % args.batch, "value": args.steps * batch / t,
         "unit": "grads/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
         "config": {"workload": "hea_adjoint_20q_10layers_batch%d_ckpt2layers" % batch},

@@ -214,10 +214,6 @@ __device__ __forceinline__ void bop_swap(Cx<R>* sp, Cx<R>* sl, int tsz, const BO
 
 constexpr int NR = 1 << kRegQ;
 
-__device__ __forceinline__ uint32_t reg_bits(int j, const uint32_t (&m)[kRegQ]) {
-  return ((j & 1) ? m[0] : 0u) | ((j & 2) ? m[1] : 0u) | ((j & 4) ? m[2] : 0u) | ((j & 8) ? m[3] : 0u);
-}
-
 // Matrix element (r, c) of U (or U^dag) of dimension D.
 template <typename R, int D>
 __device__ __forceinline__ Cx<R> uel(const Cx<R>* M, int r, int c, bool dag) {
@@ -579,17 +575,43 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_sweep(Cx<
       if (ph.kind == PH_REG) {
         const bool active = threadIdx.x < (1u << ph.ntpos);
         if ((threadIdx.x & ~31u) < (1u << ph.ntpos)) {  // the warp holds at least one group
-          uint32_t tb = 0;
-          for (int i = 0; i < ph.ntpos; i++)
-            if ((threadIdx.x >> i) & 1u) tb |= 1u << ph.tpos[i];
-          const uint32_t m[kRegQ] = {1u << ph.rp[0], 1u << ph.rp[1], 1u << ph.rp[2], 1u << ph.rp[3]};
+          // thread bits: the thread index with zeros inserted at the register
+          // positions (ascending); the swizzle is linear over XOR, so each
+          // register slot is one XOR away from one formed before it
+          uint32_t tb = threadIdx.x;
+#pragma unroll
+          for (int i = 0; i < kRegQ; i++) tb = ins0(tb, ph.rp[i]);
+          auto slots = [&](uint32_t (&off)[NR]) {  // formed again for the store: no registers held across ops
+            off[0] = sw<R>(tb);
+#pragma unroll
+            for (int j = 1; j < NR; j++) {
+              const int low = j & -j;
+              const int i = low == 1 ? 0 : low == 2 ? 1 : low == 4 ? 2 : 3;
+              off[j] = off[j ^ low] ^ sw<R>(1u << ph.rp[i]);
+            }
+          };
           Cx<R> p[NR], l[NR];
           if (active) {
+            uint32_t off[NR];
+            slots(off);
+            if (sizeof(Cx<R>) == 8 && ph.rp[0] == 0) {  // pairs (j, j+1) share a 16-byte granule
 #pragma unroll
-            for (int j = 0; j < NR; j++) {
-              const uint32_t a = sw<R>(tb | reg_bits(j, m));
-              p[j] = sp[a];
-              if (REV) l[j] = sl[a];
+              for (int j = 0; j < NR; j += 2) {
+                const float4 a = *reinterpret_cast<const float4*>(sp + off[j]);
+                p[j] = Cx<R>{(R)a.x, (R)a.y};
+                p[j + 1] = Cx<R>{(R)a.z, (R)a.w};
+                if (REV) {
+                  const float4 b = *reinterpret_cast<const float4*>(sl + off[j]);
+                  l[j] = Cx<R>{(R)b.x, (R)b.y};
+                  l[j + 1] = Cx<R>{(R)b.z, (R)b.w};
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < NR; j++) {
+                p[j] = sp[off[j]];
+                if (REV) l[j] = sl[off[j]];
+              }
             }
           }
           for (int o = ph.first; o < ph.first + ph.nops; o++) {
@@ -609,11 +631,23 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_sweep(Cx<
             }
           }
           if (active) {
+            uint32_t off[NR];
+            slots(off);
+            if (sizeof(Cx<R>) == 8 && ph.rp[0] == 0) {
 #pragma unroll
-            for (int j = 0; j < NR; j++) {
-              const uint32_t a = sw<R>(tb | reg_bits(j, m));
-              sp[a] = p[j];
-              if (REV) sl[a] = l[j];
+              for (int j = 0; j < NR; j += 2) {
+                *reinterpret_cast<float4*>(sp + off[j]) =
+                    make_float4((float)p[j].re, (float)p[j].im, (float)p[j + 1].re, (float)p[j + 1].im);
+                if (REV)
+                  *reinterpret_cast<float4*>(sl + off[j]) =
+                      make_float4((float)l[j].re, (float)l[j].im, (float)l[j + 1].re, (float)l[j + 1].im);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < NR; j++) {
+                sp[off[j]] = p[j];
+                if (REV) sl[off[j]] = l[j];
+              }
             }
           }
         }
@@ -866,23 +900,16 @@ cudaError_t launch_batch_sweep(Cx<R>* psi, Cx<R>* lam, const Cx<R>* table, doubl
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   dim3 grid((unsigned)grid_x, (unsigned)prog.h.batch);
-  if (reverse) {
-    if (smem > 48 * 1024 && smem > configured[1][dev]) {
-      cudaError_t e = cudaFuncSetAttribute(k_batch_sweep<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto go = [&](auto kernel, int which) -> cudaError_t {
+    if (smem > 48 * 1024 && smem > configured[which][dev]) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
-      configured[1][dev] = smem;
+      configured[which][dev] = smem;
     }
-    k_batch_sweep<R, true><<<grid, 256, smem, stream>>>(psi, lam, table, gscratch, prog);
-  } else {
-    if (smem > 48 * 1024 && smem > configured[0][dev]) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_batch_sweep<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      configured[0][dev] = smem;
-    }
-    k_batch_sweep<R, false><<<grid, 256, smem, stream>>>(psi, lam, table, gscratch, prog);
-  }
-  return cudaGetLastError();
+    kernel<<<grid, 256, smem, stream>>>(psi, lam, table, gscratch, prog);
+    return cudaGetLastError();
+  };
+  return reverse ? go(k_batch_sweep<R, true>, 0) : go(k_batch_sweep<R, false>, 1);
 }
 
 template <typename R>
