@@ -82,6 +82,16 @@ __device__ __forceinline__ uint32_t sw(uint32_t l) {
     return l ^ ((l >> 3) & 7u);
 }
 
+// Asynchronous 16-byte global -> shared copy; cp_async_commit_wait_all()
+// waits for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Element (r, c) of the op's matrix, or of its conjugate transpose.
 template <typename R>
 __device__ __forceinline__ Cx<R> mel(const Cx<R>* M, int d, int r, int c, bool dag) {
@@ -563,12 +573,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_sweep(Cx<
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     uint64_t base = tile;
     for (int i = 0; i < h.m; i++) base = ins0_64(base, h.tq[i]);
+    // asynchronous 16-byte copies, all in flight before one wait
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const uint32_t l = (uint32_t)(v * A);
       const uint64_t off = base + (hi_off[l >> h.L] | (l & lowmask));
-      *reinterpret_cast<uint4*>(sp + sw<R>(l)) = *reinterpret_cast<const uint4*>(ps + off);
-      if (REV) *reinterpret_cast<uint4*>(sl + sw<R>(l)) = *reinterpret_cast<const uint4*>(ls + off);
+      cp_async16(sp + sw<R>(l), ps + off);
+      if (REV) cp_async16(sl + sw<R>(l), ls + off);
     }
+    cp_async_commit_wait_all();
     __syncthreads();
     for (int ph_i = 0; ph_i < h.nphases; ph_i++) {
       const Phase& ph = P.ph[ph_i];
