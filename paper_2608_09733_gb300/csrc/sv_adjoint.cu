@@ -303,9 +303,11 @@ __device__ __forceinline__ void b_dense2(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const B
   }
 }
 
-template <typename R, int S, bool REV>
+// Anti-diagonal 2x2 on register slot S; FLIP: a pure bit flip (X, CNOT),
+// moves only.
+template <typename R, int S, bool REV, bool FLIP>
 __device__ __forceinline__ void b_anti1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M) {
-  const bool flip = op.flags & OPF_FLIP;
+  constexpr bool flip = FLIP;
   const Cx<R> a = op.dagger ? conjx(M[1]) : M[0], b = op.dagger ? conjx(M[0]) : M[1];
   const uint32_t rm = op.rmask, rv = op.rval;
 #pragma unroll
@@ -387,6 +389,32 @@ __device__ __forceinline__ void b_diag(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp
   }
 }
 
+// x a + y b for real x, y: in single precision the real and imaginary parts
+// go through one packed two-lane FP32 multiply and FMA (sm_100 and later),
+// rounded as the scalar forms.
+template <typename R>
+__device__ __forceinline__ Cx<R> rmix2(R x, Cx<R> a, R y, Cx<R> b) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 r = __ffma2_rn(make_float2(x, x), make_float2(a.re, a.im),
+                                __fmul2_rn(make_float2(y, y), make_float2(b.re, b.im)));
+    return {r.x, r.y};
+  } else {
+    return {fma(x, a.re, y * b.re), fma(x, a.im, y * b.im)};
+  }
+}
+// f p as p.re (f.re, f.im) + p.im (-f.im, f.re): one packed multiply and FMA
+// in single precision.
+template <typename R>
+__device__ __forceinline__ Cx<R> pmul(Cx<R> f, Cx<R> v) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 r = __ffma2_rn(make_float2(v.im, v.im), make_float2(-f.im, f.re),
+                                __fmul2_rn(make_float2(v.re, v.re), make_float2(f.re, f.im)));
+    return {r.x, r.y};
+  } else {
+    return cmul(f, v);
+  }
+}
+
 // Uncontrolled one-qubit op on register slot S, with the structure of the
 // common rotations written out: REAL matrices (RY, H ...) take real products,
 // and the gradient term Im <lambda|G|psi> of an X or Y generator (RX, RY) is
@@ -406,7 +434,10 @@ __device__ __forceinline__ void b_u1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& 
     } else if (REV && GK == 2) {  // (Y psi) = (-i b, i a)
       acc += (l[j1].re * a.re + l[j1].im * a.im) - (l[j].re * b.re + l[j].im * b.im);
     }
-    if (REAL) {
+    if (REAL && sizeof(R) == 4) {  // re and im together: packed two-lane FP32
+      p[j] = rmix2(u00.re, a, u01.re, b);
+      p[j1] = rmix2(u10.re, a, u11.re, b);
+    } else if (REAL) {
       p[j] = {fma(u00.re, a.re, u01.re * b.re), fma(u00.re, a.im, u01.re * b.im)};
       p[j1] = {fma(u10.re, a.re, u11.re * b.re), fma(u10.re, a.im, u11.re * b.im)};
     } else {
@@ -415,7 +446,10 @@ __device__ __forceinline__ void b_u1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& 
     }
     if (REV) {
       const Cx<R> c = l[j], d = l[j1];
-      if (REAL) {
+      if (REAL && sizeof(R) == 4) {
+        l[j] = rmix2(u00.re, c, u01.re, d);
+        l[j1] = rmix2(u10.re, c, u11.re, d);
+      } else if (REAL) {
         l[j] = {fma(u00.re, c.re, u01.re * d.re), fma(u00.re, c.im, u01.re * d.im)};
         l[j1] = {fma(u10.re, c.re, u11.re * d.re), fma(u10.re, c.im, u11.re * d.im)};
       } else {
@@ -436,8 +470,8 @@ __device__ __forceinline__ void b_d1(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& 
   for (int j = 0; j < NR; j++) {
     const bool one = (j >> S) & 1;
     if (REV && GZ) acc += one ? -im_cdot(l[j], p[j]) : im_cdot(l[j], p[j]);
-    p[j] = cmul(one ? f1 : f0, p[j]);
-    if (REV) l[j] = cmul(one ? f1 : f0, l[j]);
+    p[j] = pmul(one ? f1 : f0, p[j]);
+    if (REV) l[j] = pmul(one ? f1 : f0, l[j]);
   }
 }
 
@@ -512,11 +546,10 @@ __device__ __forceinline__ void b_apply(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BO
       }
       break;
     case OPK_ANTIDIAG:
-      switch (op.rs[0]) {
-        case 0: b_anti1<R, 0, REV>(p, l, op, M); break;
-        case 1: b_anti1<R, 1, REV>(p, l, op, M); break;
-        case 2: b_anti1<R, 2, REV>(p, l, op, M); break;
-        default: b_anti1<R, 3, REV>(p, l, op, M); break;
+      if (op.flags & OPF_FLIP) {
+        SV_SLOT4(b_anti1, REV, true>(p, l, op, M))
+      } else {
+        SV_SLOT4(b_anti1, REV, false>(p, l, op, M))
       }
       break;
     case OPK_SWAP: {

@@ -123,11 +123,20 @@ __device__ __forceinline__ void r_u1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf) {
 
 // Real rotation [[C, -S], [S, C]] on register slot S.
 //  - float (issue-bound): three in-place shears a -= t b; b += s a; a -= t b
-//    with coef = (t, s) = (tan(alpha/2), sin(alpha)); no temporaries.
+//    with coef = (t, s) = (tan(alpha/2), sin(alpha)); no temporaries, one
+//    packed FMA per shear.
 //  - double (FP64-pipe-bound): two FMAs per component in scaled form, the
 //    scale carried by a later phase table: coef.re = t and, with COT clear,
 //    (a, b) -> (a - t b, b + t a) (scale C, t = S/C); with COT set,
 //    (a, b) -> (t a - b, a + t b) (scale S, t = C/S).
+// a += c * b for the real and imaginary parts at once: one packed two-lane
+// FP32 FMA (sm_100 and later), rounded exactly as two scalar FMAs.
+__device__ __forceinline__ void shear2(Cx<float>& a, float2 c, const Cx<float>& b) {
+  const float2 r = __ffma2_rn(c, make_float2(b.re, b.im), make_float2(a.re, a.im));
+  a.re = r.x;
+  a.im = r.y;
+}
+
 template <typename R, int RQ, int S, bool COT>
 __device__ __forceinline__ void r_rot(Cx<R> (&v)[1 << RQ], Cx<R> ts) {
   constexpr int NR = 1 << RQ;
@@ -137,12 +146,10 @@ __device__ __forceinline__ void r_rot(Cx<R> (&v)[1 << RQ], Cx<R> ts) {
     if (j & (1 << S)) continue;
     const int j1 = j | (1 << S);
     if constexpr (sizeof(R) == 4) {
-      v[j].re = fma(-t, v[j1].re, v[j].re);
-      v[j].im = fma(-t, v[j1].im, v[j].im);
-      v[j1].re = fma(sn, v[j].re, v[j1].re);
-      v[j1].im = fma(sn, v[j].im, v[j1].im);
-      v[j].re = fma(-t, v[j1].re, v[j].re);
-      v[j].im = fma(-t, v[j1].im, v[j].im);
+      const float2 mt = make_float2(-t, -t), ms = make_float2(sn, sn);
+      shear2(v[j], mt, v[j1]);
+      shear2(v[j1], ms, v[j]);
+      shear2(v[j], mt, v[j1]);
     } else {
       const Cx<R> a = v[j], b = v[j1];
       if (COT) {
