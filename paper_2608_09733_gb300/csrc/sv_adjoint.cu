@@ -344,51 +344,6 @@ __device__ __forceinline__ void b_swap(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp
   }
 }
 
-template <typename R, bool REV>
-__device__ __forceinline__ void b_diag(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
-                                       const Cx<R>* G, uint32_t tb, uint64_t base, R& acc) {
-  uint32_t dbase = 0;
-  int s0 = -1, s1 = -1, b0 = 0, b1 = 0;
-  for (int i = 0; i < op.k; i++) {
-    if (op.rs[i] != 0xFF) {
-      if (s0 < 0) {
-        s0 = op.rs[i];
-        b0 = i;
-      } else {
-        s1 = op.rs[i];
-        b1 = i;
-      }
-    } else if (op.pos[i] != 0xFF) {
-      dbase |= ((tb >> op.pos[i]) & 1u) << i;
-    } else {
-      dbase |= (uint32_t)((base >> op.gq[i]) & 1ull) << i;
-    }
-  }
-  const uint32_t i1 = s0 >= 0 ? (1u << b0) : 0u, i2 = s1 >= 0 ? (1u << b1) : 0u;
-  const bool dag = op.dagger, grad = REV && op.grad;
-  Cx<R> f[4], g[4];
-  const uint32_t di[4] = {dbase, dbase | i1, dbase | i2, dbase | i1 | i2};
-#pragma unroll
-  for (int c = 0; c < 4; c++) {
-    f[c] = dag ? conjx(M[di[c]]) : M[di[c]];
-    g[c] = grad ? G[di[c]] : Cx<R>{R(0), R(0)};
-  }
-  const int sh0 = s0 >= 0 ? s0 : 0, sh1 = s1 >= 0 ? s1 : 0;
-  const uint32_t m0 = s0 >= 0 ? 1u : 0u, m1 = s1 >= 0 ? 1u : 0u;
-#pragma unroll
-  for (int j = 0; j < NR; j++) {
-    if ((j & op.rmask) != op.rval) continue;
-    const uint32_t c0 = ((uint32_t)j >> sh0) & m0, c1 = ((uint32_t)j >> sh1) & m1;
-    const Cx<R> fj = c1 ? (c0 ? f[3] : f[2]) : (c0 ? f[1] : f[0]);
-    if (grad) {
-      const Cx<R> gj = c1 ? (c0 ? g[3] : g[2]) : (c0 ? g[1] : g[0]);
-      acc += im_cdot(l[j], cmul(gj, p[j]));
-    }
-    p[j] = cmul(fj, p[j]);
-    if (REV) l[j] = cmul(fj, l[j]);
-  }
-}
-
 // x a + y b for real x, y: in single precision the real and imaginary parts
 // go through one packed two-lane FP32 multiply and FMA (sm_100 and later),
 // rounded as the scalar forms.
@@ -412,6 +367,91 @@ __device__ __forceinline__ Cx<R> pmul(Cx<R> f, Cx<R> v) {
     return {r.x, r.y};
   } else {
     return cmul(f, v);
+  }
+}
+
+// Diagonal whose factor depends on at most one register slot S (S < 0: on
+// none; the thread's and the tile's fixed bits already picked the entries
+// fa / fb).  With GR the gradient term sum Im(conj(lambda) g psi) is added,
+// as g.re Im(conj(lambda) psi) + g.im Re(conj(lambda) psi).
+template <typename R, int S, bool REV, bool GR>
+__device__ __forceinline__ void b_diag_s(Cx<R> (&p)[NR], Cx<R> (&l)[NR], Cx<R> fa, Cx<R> fb, Cx<R> ga, Cx<R> gb,
+                                         R& acc) {
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    const bool one = S >= 0 && ((j >> (S < 0 ? 0 : S)) & 1);
+    if (REV && GR) {
+      const Cx<R> g = one ? gb : ga;
+      const R cre = fma(l[j].re, p[j].re, l[j].im * p[j].im), cim = fma(l[j].re, p[j].im, -l[j].im * p[j].re);
+      acc = fma(g.re, cim, fma(g.im, cre, acc));
+    }
+    p[j] = cmul(one ? fb : fa, p[j]);
+    if (REV) l[j] = cmul(one ? fb : fa, l[j]);
+  }
+}
+
+template <typename R, bool REV>
+__device__ __forceinline__ void b_diag(Cx<R> (&p)[NR], Cx<R> (&l)[NR], const BOp& op, const Cx<R>* M,
+                                       const Cx<R>* G, uint32_t tb, uint64_t base, R& acc) {
+  uint32_t dbase = 0;
+  int s0 = -1, s1 = -1, b0 = 0, b1 = 0;
+  for (int i = 0; i < op.k; i++) {
+    if (op.rs[i] != 0xFF) {
+      if (s0 < 0) {
+        s0 = op.rs[i];
+        b0 = i;
+      } else {
+        s1 = op.rs[i];
+        b1 = i;
+      }
+    } else if (op.pos[i] != 0xFF) {
+      dbase |= ((tb >> op.pos[i]) & 1u) << i;
+    } else {
+      dbase |= (uint32_t)((base >> op.gq[i]) & 1ull) << i;
+    }
+  }
+  const uint32_t i1 = s0 >= 0 ? (1u << b0) : 0u, i2 = s1 >= 0 ? (1u << b1) : 0u;
+  const bool dag = op.dagger, grad = REV && op.grad;
+  if (op.rmask == 0 && s1 < 0) {  // at most one register slot, no register controls
+    const Cx<R> fa = dag ? conjx(M[dbase]) : M[dbase], fb = dag ? conjx(M[dbase | i1]) : M[dbase | i1];
+    const Cx<R> z = {R(0), R(0)};
+    const Cx<R> ga = grad ? G[dbase] : z, gb = grad ? G[dbase | i1] : z;
+#define SV_DIAG_S(GR)                                                   \
+  switch (s0) {                                                         \
+    case -1: b_diag_s<R, -1, REV, GR>(p, l, fa, fb, ga, gb, acc); break; \
+    case 0: b_diag_s<R, 0, REV, GR>(p, l, fa, fb, ga, gb, acc); break;   \
+    case 1: b_diag_s<R, 1, REV, GR>(p, l, fa, fb, ga, gb, acc); break;   \
+    case 2: b_diag_s<R, 2, REV, GR>(p, l, fa, fb, ga, gb, acc); break;   \
+    default: b_diag_s<R, 3, REV, GR>(p, l, fa, fb, ga, gb, acc); break;  \
+  }
+    if (grad) {
+      SV_DIAG_S(true)
+    } else {
+      SV_DIAG_S(false)
+    }
+#undef SV_DIAG_S
+    return;
+  }
+  Cx<R> f[4], g[4];
+  const uint32_t di[4] = {dbase, dbase | i1, dbase | i2, dbase | i1 | i2};
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    f[c] = dag ? conjx(M[di[c]]) : M[di[c]];
+    g[c] = grad ? G[di[c]] : Cx<R>{R(0), R(0)};
+  }
+  const int sh0 = s0 >= 0 ? s0 : 0, sh1 = s1 >= 0 ? s1 : 0;
+  const uint32_t m0 = s0 >= 0 ? 1u : 0u, m1 = s1 >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int j = 0; j < NR; j++) {
+    if ((j & op.rmask) != op.rval) continue;
+    const uint32_t c0 = ((uint32_t)j >> sh0) & m0, c1 = ((uint32_t)j >> sh1) & m1;
+    const Cx<R> fj = c1 ? (c0 ? f[3] : f[2]) : (c0 ? f[1] : f[0]);
+    if (grad) {
+      const Cx<R> gj = c1 ? (c0 ? g[3] : g[2]) : (c0 ? g[1] : g[0]);
+      acc += im_cdot(l[j], cmul(gj, p[j]));
+    }
+    p[j] = cmul(fj, p[j]);
+    if (REV) l[j] = cmul(fj, l[j]);
   }
 }
 
