@@ -10,6 +10,9 @@ Default workload (the headline metric, one JSON line on stdout):
 value = effective HBM GB/s = algorithmic bytes of the step's kernels (each pass
 over the state reads and writes 2^n amplitudes; initialisation writes them once;
 the read-out reads them once) / device time of the step, summed over ranks.
+e2e = the same bytes over host wall time of one sv_run_host call per step
+(gate records in, <Z_q> read-out back); e2e.with_state_download also copies
+the final 8 GiB state to pinned host memory every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -660,20 +663,33 @@ def main():
     alu_peak = (152 * 128 * 2 * sm_mhz * 1e6 / 1e12) if dt == sv.SV_C64 else 1.25
     alu_achieved = flops_step * args.steps / (sw["total_ms"] / 1e3) / 1e12 if sw["launches"] else None
 
-    # e2e: the same workload through the host-buffer entry point (H2D/D2H inside)
+    # e2e: the same workload through the host-buffer entry point, one call per
+    # step: the gate records in, |0..0> prepared, every pass, the <Z_q> read-out
+    # copied back (the step's result); a second figure also downloads the
+    # whole final state into pinned host memory every step
     e2e = None
     if not args.no_e2e:
-        pinned = torch.empty(2 ** n, dtype=tdt).pin_memory()
-        host_state = pinned.numpy()
-        sv.sv_run_host(n, dt, G, fuse_max_k=args.fuse, state_out=host_state)  # warm the buffers
-        t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 3))
-        for _ in range(e2e_steps):
-            sv.sv_run_host(n, dt, G, fuse_max_k=args.fuse, state_out=host_state)
-        te = time.perf_counter() - t0
+
+        def e2e_time(state_out):
+            sv.sv_run_host(n, dt, G, fuse_max_k=args.fuse, state_out=state_out)  # warm the buffers
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                z = sv.sv_run_host(n, dt, G, fuse_max_k=args.fuse, state_out=state_out)
+            assert np.isfinite(z).all()
+            return time.perf_counter() - t0
+
+        te = e2e_time(None)
         e2e = {"value": ws * e2e_steps * bytes_step / te / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": len(gates) * 80, "d2h_bytes_per_step": (2 ** n) * amp + 8 * (n + 1),
-               "gates_per_s": ws * e2e_steps * len(gates) / te}
+               "h2d_bytes_per_step": len(gates) * 80, "d2h_bytes_per_step": 8 * (n + 1),
+               "gates_per_s": ws * e2e_steps * len(gates) / te, "result": "<Z_q> of every qubit and their sum"}
+        pinned = torch.empty(2 ** n, dtype=tdt).pin_memory()
+        ts = e2e_time(pinned.numpy())
+        e2e["with_state_download"] = {
+            "value": ws * e2e_steps * bytes_step / ts / 1e9, "unit": "GB/s",
+            "d2h_bytes_per_step": (2 ** n) * amp + 8 * (n + 1), "gates_per_s": ws * e2e_steps * len(gates) / ts,
+            "download_gbs": (2 ** n) * amp / max(1e-9, (ts - te) / e2e_steps) / 1e9}
+        del pinned
         sv.sv_release_scratch()
 
     cpu = None

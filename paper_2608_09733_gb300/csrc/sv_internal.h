@@ -217,6 +217,15 @@ int reg_qubits_for(int m);  // register qubits of a tile of m qubits (4, or 5 fo
 
 // The kernel program of one sweep (sv_program.cpp); rq_override > 0 forces the
 // register qubits of the register phases.
+// A 2x2 unitary U written as g * diag(1, ephi) * [[C, -S], [S, C]] * diag(1, elam)
+// (the Z-Y-Z Euler form, C = cos(alpha), S = sin(alpha), alpha in [0, pi/2]);
+// false if the reconstruction misses U by more than tol in any entry.
+struct RotSplit {
+  cplx g = 1.0, ephi = 1.0, elam = 1.0;
+  double C = 1.0, S = 0.0;
+};
+bool rot_split(const cplx* U, double tol, RotSplit& r);
+
 template <typename R>
 void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq_override = 0);
 

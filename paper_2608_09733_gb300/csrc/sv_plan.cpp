@@ -426,6 +426,95 @@ std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_
   return out;
 }
 
+// An uncontrolled complex one-qubit op g diag(1, ephi) R diag(1, elam)
+// (R = [[C, -S], [S, C]]) becomes two ops: R diag(1, elam), which the program
+// builder runs as in-place shears after a phase table, and the closing
+// diagonal g diag(1, ephi).  That diagonal is free to move (it commutes with
+// everything that does not target the qubit), so it can join the opening
+// table of the next gate on the same qubit, possibly in a later pass, instead
+// of costing a phase table of its own.  Ops the factors do not reproduce
+// within tol stay whole.
+static void split_one_qubit(std::vector<LOp>& ops, double tol) {
+  std::vector<LOp> out;
+  out.reserve(ops.size() * 2);
+  for (LOp& op : ops) {
+    RotSplit r;
+    if (!(op.kind == OPK_DENSE && op.k == 1 && op.nc == 0 && rot_split(op.m.data(), tol, r))) {
+      out.push_back(std::move(op));
+      continue;
+    }
+    auto part = [&](cplx m00, cplx m01, cplx m10, cplx m11) {
+      LOp d;
+      d.k = 1;
+      d.q[0] = op.q[0];
+      d.first_gate = op.first_gate;
+      d.m = {m00, m01, m10, m11};
+      classify(d);
+      return d;
+    };
+    out.push_back(part(r.C, -r.S * r.elam, r.S, r.C * r.elam));
+    out.push_back(part(r.g, 0.0, 0.0, r.g * r.ephi));
+  }
+  ops = std::move(out);
+}
+
+// A narrow diagonal commutes with every op that does not target one of its
+// qubits.  One that meets no such op (a "blocker") in the rest of its pass
+// moves to the front of the first later pass that holds one -- every pass in
+// between leaves its qubits alone -- where the program builder folds it into
+// the phase table of its blocker's register phase.  Without a later blocker,
+// or without room in that pass, it stays.
+static void defer_diagonals(const std::vector<LOp>& ops, std::vector<Sweep>& sw, int max_ops, int coef_pool) {
+  auto is_diag = [&](int i) { return ops[i].kind == OPK_DIAG && ops[i].k <= 2; };
+  auto targets = [&](int i) {
+    uint64_t t = 0;
+    for (int j = 0; j < ops[i].k; j++) t |= 1ull << ops[i].q[j];
+    return t;
+  };
+  const size_t ns = sw.size();
+  std::vector<int> n_ops(ns), n_coef(ns, 0);
+  std::vector<uint64_t> blockers(ns, 0);  // qubits targeted by each pass's non-diagonal ops
+  for (size_t s = 0; s < ns; s++) {
+    n_ops[s] = (int)sw[s].ops.size();
+    for (int i : sw[s].ops) {
+      n_coef[s] += coef_count(ops[i]);
+      if (!is_diag(i)) blockers[s] |= targets(i);
+    }
+  }
+  std::vector<std::vector<int>> front(ns);  // diagonals arriving at each pass, in order
+  for (size_t s = 0; s + 1 < ns; s++) {
+    std::vector<int> keep;
+    const std::vector<int>& cur = sw[s].ops;
+    for (size_t a = 0; a < cur.size(); a++) {
+      const int i = cur[a];
+      size_t dest = 0;
+      if (is_diag(i)) {
+        bool blocked_here = false;
+        for (size_t b = a + 1; b < cur.size() && !blocked_here; b++)
+          blocked_here = !is_diag(cur[b]) && (targets(cur[b]) & ops[i].touch);
+        if (!blocked_here)
+          for (size_t t = s + 1; t < ns && !dest; t++)
+            if (blockers[t] & ops[i].touch) dest = t;
+        const int c = coef_count(ops[i]);
+        if (dest && (n_ops[dest] + 1 > max_ops || n_coef[dest] + c > coef_pool)) dest = 0;
+        if (dest) {
+          front[dest].push_back(i);
+          n_ops[dest]++;
+          n_coef[dest] += c;
+          n_ops[s]--;
+          n_coef[s] -= c;
+        }
+      }
+      if (!dest) keep.push_back(i);
+    }
+    sw[s].ops = std::move(keep);
+    if (!front[s + 1].empty()) {
+      front[s + 1].insert(front[s + 1].end(), sw[s + 1].ops.begin(), sw[s + 1].ops.end());
+      sw[s + 1].ops = std::move(front[s + 1]);
+    }
+  }
+}
+
 Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
                size_t n_param_values, const sv_exec_opts& opts, int tile_q_override) {
   const int fuse_max_k = opts.fuse_max_k;
@@ -450,6 +539,7 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
     }
     p.block_starts.push_back((int)n_gates);
   }
+  if (opts.ops_per_pass != 1) split_one_qubit(p.ops, dtype == SV_C64 ? 1e-9 : 1e-13);
   // drop exact identities (e.g. the I gate): they move no amplitude
   std::vector<LOp> kept;
   kept.reserve(p.ops.size());
@@ -466,6 +556,8 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
   int pool = dtype == SV_C64 ? SweepProgram<float>::kPool : SweepProgram<double>::kPool;
   const int tile_q = tile_q_override > 0 ? tile_q_override : tile_qubits_for(dtype);
   p.sweeps = schedule_sweeps(n, p.ops, tile_q, low_qubits_for(dtype), pool, opts.ops_per_pass);
+  if (opts.ops_per_pass != 1)
+    defer_diagonals(p.ops, p.sweeps, opts.ops_per_pass > 0 ? std::min(opts.ops_per_pass, kMaxOps) : kMaxOps, pool);
   return p;
 }
 

@@ -24,15 +24,12 @@ namespace {
 #endif
 constexpr bool g_rot_split = SV_ROT_SPLIT != 0;  // register phases in rotation + phase-table form
 
+}  // namespace
+
 // A 2x2 unitary U written as g * diag(1, ephi) * [[C, -S], [S, C]] * diag(1, elam)
 // with C = |U00| and S = |U10| (C^2 + S^2 = 1, |g| = |ephi| = |elam| = 1): the
 // Z-Y-Z Euler form of a one-qubit gate, C = cos(alpha), S = sin(alpha), alpha
 // in [0, pi/2].
-struct RotSplit {
-  cplx g = 1.0, ephi = 1.0, elam = 1.0;
-  double C = 1.0, S = 0.0;
-};
-
 bool rot_split(const cplx* U, double tol, RotSplit& r) {
   double C = std::abs(U[0]), S = std::abs(U[2]);
   const double nrm = std::hypot(C, S);
@@ -66,8 +63,6 @@ bool rot_split(const cplx* U, double tol, RotSplit& r) {
 // positions and control masks; consecutive ops whose moving qubits fit four
 // register slots form one register phase; dense k >= 3 blocks and wide
 // diagonals get a shared-memory phase of their own.
-}  // namespace
-
 template <typename R>
 void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq_override) {
   std::memset(&P.h, 0, sizeof(P.h));
