@@ -487,6 +487,16 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
       }
       return true;
     };
+    // A diagonal whose selectors do not fit the current table starts a new
+    // one (the current table is emitted first: diagonals commute), so that it
+    // stays a table entry instead of a general diagonal op.  Sign flips that
+    // do not fit stay sign ops (a negation mask).
+    auto fold_or_restart = [&](const Tmp& t) {
+      if (fold_diag(t)) return true;
+      if (t.d.kind != OPK_DIAG || sel.empty()) return false;
+      flush();
+      return fold_diag(t);
+    };
     for (int o = first; o < first + nops;) {
       const Tmp& t = ts[o];
       const DevOp& d = t.d;
@@ -512,7 +522,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
           hoist.push_back(end);
         }
         for (int h : hoist)
-          if (!fold_diag(ts[h])) fin.push_back(ts[h]);
+          if (!fold_or_restart(ts[h])) fin.push_back(ts[h]);
         std::vector<cplx> mats;
         const uint32_t present = merge_ops(list, mats);
         o = end;
@@ -558,7 +568,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
         if (std::abs(sc) < 1e-30) flush();
         continue;
       }
-      if ((d.kind == OPK_SIGN || d.kind == OPK_DIAG) && fold_diag(t)) {
+      if ((d.kind == OPK_SIGN || d.kind == OPK_DIAG) && fold_or_restart(t)) {
         o++;
         continue;
       }
