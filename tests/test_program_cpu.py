@@ -43,6 +43,52 @@ def test_programs_match_oracle(name, n, make, dtype, fuse):
     assert np.abs(got - ref).max() <= TOL[dtype]
 
 
+def _closing_phase_circuit(n, layers, seed):
+    """Layers of one-qubit gates of every shape the rotation split meets --
+    general U3, diagonal (theta = 0), anti-diagonal (theta = pi), real, phase
+    and Clifford gates -- with CZ, CP and controlled RZ between near and far
+    qubits, so that closing phases and other diagonals must wait for later
+    passes (17 qubits: several 13-qubit tiles)."""
+    from workloads.circuits import Gate
+    rng = np.random.default_rng(seed)
+    one = ["u3", "u3", "u3z", "u3x", "h", "s", "t", "sx", "rx", "ry", "rz", "p", "y"]
+    gates = []
+    for _ in range(layers):
+        for q in range(n):
+            kind = one[rng.integers(len(one))]
+            if kind == "u3z":
+                gates.append(Gate("u3", [q], params=[0.0, *rng.uniform(-3, 3, 2)]))
+            elif kind == "u3x":
+                gates.append(Gate("u3", [q], params=[np.pi, *rng.uniform(-3, 3, 2)]))
+            elif kind == "u3":
+                gates.append(Gate("u3", [q], params=list(rng.uniform(-3, 3, 3))))
+            elif kind in ("rx", "ry", "rz", "p"):
+                gates.append(Gate(kind, [q], params=[float(rng.uniform(-3, 3))]))
+            else:
+                gates.append(Gate(kind, [q]))
+        for q in range(0, n - 1, 2):
+            gates.append(Gate("z", [q + 1], controls=[q]))
+        for _ in range(4):
+            a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+            if rng.integers(2):
+                gates.append(Gate("p", [a], controls=[b], params=[float(rng.uniform(-3, 3))]))
+            else:
+                gates.append(Gate("rz", [a], controls=[b], params=[float(rng.uniform(-3, 3))]))
+    return gates
+
+
+@pytest.mark.parametrize("dtype", [sv.SV_C64, sv.SV_C128])
+@pytest.mark.parametrize("fuse", [0, 5])
+def test_programs_closing_phases_across_passes(dtype, fuse):
+    n = 17
+    circ = _closing_phase_circuit(n, 6, seed=21)
+    _, passes, _ = sv.sv_plan_info(n, dtype, sv.Gates(circ), fuse_max_k=fuse)
+    assert passes >= 2
+    got = _emulate(n, circ, dtype, fuse_max_k=fuse)
+    ref = oracle.run(n, circ)
+    assert np.abs(got - ref).max() <= TOL[dtype]
+
+
 @pytest.mark.parametrize("dtype", [sv.SV_C64, sv.SV_C128])
 def test_programs_bound_parameters(dtype):
     n = 12
