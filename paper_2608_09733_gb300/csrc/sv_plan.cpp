@@ -435,11 +435,24 @@ std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_
 // of costing a phase table of its own.  Ops the factors do not reproduce
 // within tol stay whole.
 static void split_one_qubit(std::vector<LOp>& ops, double tol) {
+  // Worth it only where the closing diagonal has a table to join: the next
+  // op that targets the qubit (diagonals aside) is another uncontrolled
+  // one-qubit gate.  Before a CNOT target, say, it would cost a table anyway.
+  auto u1 = [&](const LOp& op) { return (op.kind == OPK_DENSE || op.kind == OPK_REAL) && op.k == 1 && op.nc == 0; };
+  std::vector<char> split(ops.size(), 0);
+  std::vector<int> next(64, -1);  // per qubit: the next non-diagonal op targeting it
+  for (int i = (int)ops.size() - 1; i >= 0; i--) {
+    const LOp& op = ops[i];
+    if (op.kind == OPK_DIAG) continue;
+    if (op.kind == OPK_DENSE && u1(op) && next[op.q[0]] >= 0 && u1(ops[next[op.q[0]]])) split[i] = 1;
+    for (int j = 0; j < op.k; j++) next[op.q[j]] = i;
+  }
   std::vector<LOp> out;
   out.reserve(ops.size() * 2);
-  for (LOp& op : ops) {
+  for (size_t i = 0; i < ops.size(); i++) {
+    LOp& op = ops[i];
     RotSplit r;
-    if (!(op.kind == OPK_DENSE && op.k == 1 && op.nc == 0 && rot_split(op.m.data(), tol, r))) {
+    if (!(split[i] && rot_split(op.m.data(), tol, r))) {
       out.push_back(std::move(op));
       continue;
     }
@@ -539,25 +552,40 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
     }
     p.block_starts.push_back((int)n_gates);
   }
-  if (opts.ops_per_pass != 1) split_one_qubit(p.ops, dtype == SV_C64 ? 1e-9 : 1e-13);
   // drop exact identities (e.g. the I gate): they move no amplitude
-  std::vector<LOp> kept;
-  kept.reserve(p.ops.size());
-  for (auto& op : p.ops) {
-    if (op.kind == OPK_DIAG) {
-      bool ident = true;
-      for (auto& v : op.m)
-        if (v != 1.0) ident = false;
-      if (ident) continue;
+  auto drop_identities = [](std::vector<LOp>& ops) {
+    std::vector<LOp> kept;
+    kept.reserve(ops.size());
+    for (auto& op : ops) {
+      if (op.kind == OPK_DIAG) {
+        bool ident = true;
+        for (auto& v : op.m)
+          if (v != 1.0) ident = false;
+        if (ident) continue;
+      }
+      kept.push_back(std::move(op));
     }
-    kept.push_back(std::move(op));
-  }
-  p.ops = std::move(kept);
+    ops = std::move(kept);
+  };
+  drop_identities(p.ops);
   int pool = dtype == SV_C64 ? SweepProgram<float>::kPool : SweepProgram<double>::kPool;
   const int tile_q = tile_q_override > 0 ? tile_q_override : tile_qubits_for(dtype);
+  const int max_ops = opts.ops_per_pass > 0 ? std::min(opts.ops_per_pass, kMaxOps) : kMaxOps;
   p.sweeps = schedule_sweeps(n, p.ops, tile_q, low_qubits_for(dtype), pool, opts.ops_per_pass);
-  if (opts.ops_per_pass != 1)
-    defer_diagonals(p.ops, p.sweeps, opts.ops_per_pass > 0 ? std::min(opts.ops_per_pass, kMaxOps) : kMaxOps, pool);
+  if (opts.ops_per_pass != 1) {
+    defer_diagonals(p.ops, p.sweeps, max_ops, pool);
+    // The split form has more ops, which can cut the greedy passes short and
+    // leave more of them: keep it only when it needs no more passes.
+    std::vector<LOp> ops2 = p.ops;
+    split_one_qubit(ops2, dtype == SV_C64 ? 1e-9 : 1e-13);
+    drop_identities(ops2);
+    std::vector<Sweep> sw2 = schedule_sweeps(n, ops2, tile_q, low_qubits_for(dtype), pool, opts.ops_per_pass);
+    if (sw2.size() <= p.sweeps.size()) {
+      defer_diagonals(ops2, sw2, max_ops, pool);
+      p.ops = std::move(ops2);
+      p.sweeps = std::move(sw2);
+    }
+  }
   return p;
 }
 
