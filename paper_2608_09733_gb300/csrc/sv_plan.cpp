@@ -258,7 +258,7 @@ static void apply_local(std::vector<cplx>& v, int nb, const sv_gate& g, const st
   }
   uint64_t tmask = 0;
   for (int i = 0; i < k; i++) tmask |= 1ull << t[i];
-  std::vector<cplx> in(d);
+  cplx in[32];  // k <= 5
   for (uint64_t b = 0; b < (1ull << nb); b++) {
     if (b & tmask) continue;  // enumerate group bases (target bits clear)
     if ((b & cmask) != cval) continue;
@@ -324,6 +324,23 @@ std::vector<LOp> fuse_greedy(int n, const sv_gate* gates, size_t n_gates, const 
       out.push_back(lower_gate(gates[start], pv, (int)start));
       continue;
     }
+    // The block's gates, kept (same pass, same result up to rounding) when
+    // they cost less than the block's dense matrix.  Below the cost of a real
+    // dense block the matrix is not even built: only a block that happened to
+    // be diagonal or a permutation could be cheaper.
+    std::vector<LOp> parts;
+    double parts_cost = 0.0;
+    if (!dense_always) {
+      for (size_t g = start; g < i; g++) {
+        parts.push_back(lower_gate(gates[g], pv, (int)start));
+        parts_cost += op_cost(parts.back());
+      }
+      const int kb = popc(mask);
+      if (parts_cost < 4.0 * (1 << kb) + (kb >= 3 ? 40.0 : 2.0)) {
+        for (auto& pp : parts) out.push_back(std::move(pp));
+        continue;
+      }
+    }
     // dense block over the union of its gates' qubits, ascending
     LOp op;
     int local_of[64];
@@ -338,24 +355,15 @@ std::vector<LOp> fuse_greedy(int n, const sv_gate* gates, size_t n_gates, const 
     op.m.assign((size_t)d * d, 0.0);
     std::vector<std::vector<cplx>> mats;
     for (size_t g = start; g < i; g++) mats.push_back(gate_matrix(gates[g], pv));
-    std::vector<cplx> col(d);
-    for (int c = 0; c < d; c++) {
-      std::fill(col.begin(), col.end(), cplx(0.0));
-      col[c] = 1.0;
-      for (size_t g = start; g < i; g++) apply_local(col, nb, gates[g], mats[g - start], local_of);
-      for (int r = 0; r < d; r++) op.m[(size_t)r * d + c] = col[r];
-    }
+    std::vector<std::vector<cplx>> cols((size_t)d, std::vector<cplx>((size_t)d, cplx(0.0)));
+    for (int c = 0; c < d; c++) cols[c][c] = 1.0;
+    for (size_t g = start; g < i; g++)  // gate by gate over every column (same order per column)
+      for (int c = 0; c < d; c++) apply_local(cols[c], nb, gates[g], mats[g - start], local_of);
+    for (int c = 0; c < d; c++)
+      for (int r = 0; r < d; r++) op.m[(size_t)r * d + c] = cols[c][r];
     op.first_gate = (int)start;
     classify(op);
     if (!dense_always) {
-      // keep the block's gates (same pass, same result up to rounding) when
-      // they cost less than the block's dense matrix
-      std::vector<LOp> parts;
-      double parts_cost = 0.0;
-      for (size_t g = start; g < i; g++) {
-        parts.push_back(lower_gate(gates[g], pv, (int)start));
-        parts_cost += op_cost(parts.back());
-      }
       if (parts_cost < op_cost(op)) {
         for (auto& pp : parts) out.push_back(std::move(pp));
         continue;
