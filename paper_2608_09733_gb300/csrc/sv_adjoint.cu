@@ -872,6 +872,14 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
   uint64_t* hi_off = reinterpret_cast<uint64_t*>(s + tsz);
   const int nhi = 1 << (P.m - P.L);
   __shared__ PauliTileCoef<R> cf[kPauliTileTerms];
+  // the terms' masks, staged once (broadcast reads in the inner loop)
+  __shared__ uint32_t sxl[kPauliTileTerms];
+  __shared__ uint64_t sxg[kPauliTileTerms], sz[kPauliTileTerms];
+  for (int j = threadIdx.x; j < P.nterms; j += blockDim.x) {
+    sxl[j] = P.xl[j];
+    sxg[j] = P.xg[j];
+    sz[j] = P.z[j];
+  }
   for (int c = threadIdx.x; c < nhi; c += blockDim.x) {
     uint64_t off = 0;
     for (int i = P.L; i < P.m; i++)
@@ -900,29 +908,54 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
     for (int l = threadIdx.x; l < tsz; l += blockDim.x)
       s[l] = psi[sbase + (base | hi_off[l >> P.L] | (l & lowmask))];
     __syncthreads();
-    for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
-      const uint64_t g = base | hi_off[l >> P.L] | (l & lowmask);
-      R ar = R(0), ai = R(0);
+    // four amplitudes per thread: each term's masks and coefficient are read
+    // once for all four, and the four sums are independent
+    constexpr int A = 4;
+    const int stride = (int)blockDim.x;
+    for (int l0 = threadIdx.x; l0 < tsz; l0 += A * stride) {
+      uint64_t g[A];
+      R ar[A], ai[A];
+#pragma unroll
+      for (int k = 0; k < A; k++) {
+        const int l = l0 + k * stride < tsz ? l0 + k * stride : l0;  // past the tile: a repeat, not stored
+        g[k] = base | hi_off[l >> P.L] | (l & lowmask);
+        ar[k] = ai[k] = R(0);
+      }
       for (int j = 0; j < P.nterms;) {
-        const uint32_t xl = P.xl[j];
-        const uint64_t src = g ^ P.xg[j];
-        R fr = R(0), fi = R(0);
-        for (; j < P.nterms && P.xl[j] == xl; j++) {
-          const bool neg = __popcll(src & P.z[j]) & 1;
-          fr += neg ? -cf[j].cr : cf[j].cr;
-          fi += neg ? -cf[j].ci : cf[j].ci;
+        const uint32_t xl = sxl[j];
+        const uint64_t xg = sxg[j];
+        R fr[A], fi[A];
+#pragma unroll
+        for (int k = 0; k < A; k++) fr[k] = fi[k] = R(0);
+        for (; j < P.nterms && sxl[j] == xl; j++) {
+          const uint64_t z = sz[j];
+          const PauliTileCoef<R> c = cf[j];
+#pragma unroll
+          for (int k = 0; k < A; k++) {
+            const bool neg = __popcll((g[k] ^ xg) & z) & 1;
+            fr[k] += neg ? -c.cr : c.cr;
+            fi[k] += neg ? -c.ci : c.ci;
+          }
         }
-        const Cx<R> v = s[l ^ xl];
-        ar = fma(fr, v.re, fma(-fi, v.im, ar));
-        ai = fma(fr, v.im, fma(fi, v.re, ai));
+#pragma unroll
+        for (int k = 0; k < A; k++) {
+          const int l = l0 + k * stride < tsz ? l0 + k * stride : l0;
+          const Cx<R> v = s[l ^ xl];
+          ar[k] = fma(fr[k], v.re, fma(-fi[k], v.im, ar[k]));
+          ai[k] = fma(fr[k], v.im, fma(fi[k], v.re, ai[k]));
+        }
       }
-      Cx<R>* o = lam + sbase + g;
-      if (P.accumulate) {
-        const Cx<R> w = *o;
-        ar += w.re;
-        ai += w.im;
+#pragma unroll
+      for (int k = 0; k < A; k++) {
+        if (l0 + k * stride >= tsz) continue;
+        Cx<R>* o = lam + sbase + g[k];
+        if (P.accumulate) {
+          const Cx<R> w = *o;
+          ar[k] += w.re;
+          ai[k] += w.im;
+        }
+        *o = Cx<R>{ar[k], ai[k]};
       }
-      *o = Cx<R>{ar, ai};
     }
     __syncthreads();
   }
