@@ -847,6 +847,8 @@ struct PauliTilePass {
   uint32_t xl[kPauliTileTerms];       // x in local tile bits
   uint64_t xg[kPauliTileTerms];       // x in global bits
   uint64_t z[kPauliTileTerms];
+  uint32_t zl[kPauliTileTerms];       // z in local tile bits
+  uint8_t gend[kPauliTileTerms];      // at the first term of a run of equal xl: one past the run
   double cr[kPauliTileTerms], ci[kPauliTileTerms];  // c_j i^{nY_j}
   uint16_t orig[kPauliTileTerms];     // the term's index in the caller's list (per-state coefficients)
   uint8_t ny[kPauliTileTerms];        // nY_j mod 4
@@ -873,13 +875,18 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
   const int nhi = 1 << (P.m - P.L);
   __shared__ PauliTileCoef<R> cf[kPauliTileTerms];
   // the terms' masks, staged once (broadcast reads in the inner loop)
-  __shared__ uint32_t sxl[kPauliTileTerms];
-  __shared__ uint64_t sxg[kPauliTileTerms], sz[kPauliTileTerms];
+  // The sign (-1)^{popc((g ^ x) & z)} of a term splits into the tile-local
+  // part popc(l & zl) and a part that is fixed over the tile (the bits
+  // outside it, and x inside it): sc0[j], restaged per tile.
+  __shared__ uint32_t sxl[kPauliTileTerms], szl[kPauliTileTerms];
+  __shared__ uint8_t sgend[kPauliTileTerms], sc0[kPauliTileTerms];
   for (int j = threadIdx.x; j < P.nterms; j += blockDim.x) {
     sxl[j] = P.xl[j];
-    sxg[j] = P.xg[j];
-    sz[j] = P.z[j];
+    szl[j] = P.zl[j];
+    sgend[j] = P.gend[j];
   }
+  uint64_t tile_mask = 0;
+  for (int i = 0; i < P.m; i++) tile_mask |= 1ull << P.tq[i];
   for (int c = threadIdx.x; c < nhi; c += blockDim.x) {
     uint64_t off = 0;
     for (int i = P.L; i < P.m; i++)
@@ -907,6 +914,8 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
     }
     for (int l = threadIdx.x; l < tsz; l += blockDim.x)
       s[l] = psi[sbase + (base | hi_off[l >> P.L] | (l & lowmask))];
+    for (int j = threadIdx.x; j < P.nterms; j += blockDim.x)
+      sc0[j] = (uint8_t)((__popcll((base ^ P.xg[j]) & P.z[j] & ~tile_mask) + __popc(P.xl[j] & P.zl[j])) & 1);
     __syncthreads();
     // four amplitudes per thread: each term's masks and coefficient are read
     // once for all four, and the four sums are independent
@@ -921,26 +930,28 @@ __global__ void __launch_bounds__(256) k_pauli_tiles(const Cx<R>* __restrict__ p
         g[k] = base | hi_off[l >> P.L] | (l & lowmask);
         ar[k] = ai[k] = R(0);
       }
+      int lk[A];
+#pragma unroll
+      for (int k = 0; k < A; k++) lk[k] = l0 + k * stride < tsz ? l0 + k * stride : l0;
       for (int j = 0; j < P.nterms;) {
         const uint32_t xl = sxl[j];
-        const uint64_t xg = sxg[j];
+        const int je = sgend[j];
         R fr[A], fi[A];
 #pragma unroll
         for (int k = 0; k < A; k++) fr[k] = fi[k] = R(0);
-        for (; j < P.nterms && sxl[j] == xl; j++) {
-          const uint64_t z = sz[j];
+        for (; j < je; j++) {
+          const uint32_t zl = szl[j], c0 = sc0[j];
           const PauliTileCoef<R> c = cf[j];
 #pragma unroll
           for (int k = 0; k < A; k++) {
-            const bool neg = __popcll((g[k] ^ xg) & z) & 1;
+            const bool neg = (__popc((uint32_t)lk[k] & zl) ^ c0) & 1u;
             fr[k] += neg ? -c.cr : c.cr;
             fi[k] += neg ? -c.ci : c.ci;
           }
         }
 #pragma unroll
         for (int k = 0; k < A; k++) {
-          const int l = l0 + k * stride < tsz ? l0 + k * stride : l0;
-          const Cx<R> v = s[l ^ xl];
+          const Cx<R> v = s[lk[k] ^ xl];
           ar[k] = fma(fr[k], v.re, fma(-fi[k], v.im, ar[k]));
           ai[k] = fma(fr[k], v.im, fma(fi[k], v.re, ai[k]));
         }
@@ -1103,6 +1114,8 @@ cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, c
       }
     auto flush = [&]() -> cudaError_t {
       if (!P.nterms) return cudaSuccess;
+      for (int j = P.nterms - 1; j >= 0; j--)  // runs of equal xl
+        P.gend[j] = (uint8_t)(j + 1 < P.nterms && P.xl[j + 1] == P.xl[j] ? P.gend[j + 1] : j + 1);
       P.accumulate = acc ? 1 : 0;
       const uint64_t ntiles = (uint64_t)batch << (n - m);
       const int smem = (int)(sizeof(Cx<R>) << m) + (8 << (m - L));
@@ -1140,6 +1153,10 @@ cudaError_t launch_pauli_tiles(const Cx<R>* psi, Cx<R>* lam, int n, int batch, c
       P.xl[j] = xl;
       P.xg[j] = x;
       P.z[j] = terms[t].z_mask;
+      uint32_t zl = 0;
+      for (int q = 0; q < n; q++)
+        if (((terms[t].z_mask >> q) & 1ull) && ((T >> q) & 1ull)) zl |= 1u << loc[q];
+      P.zl[j] = zl;
       P.cr[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
       P.ci[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
       P.orig[j] = (uint16_t)t;
