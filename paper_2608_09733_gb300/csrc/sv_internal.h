@@ -211,9 +211,9 @@ std::vector<Sweep> schedule_sweeps(int n, const std::vector<LOp>& ops, int tile_
 Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
                size_t n_param_values, const sv_exec_opts& opts, int tile_q_override = 0);
 double op_cost(const LOp& op);
-int tile_qubits_for(sv_dtype dtype);
+int tile_qubits_for(sv_dtype dtype, int n);
 int low_qubits_for(sv_dtype dtype);
-int reg_qubits_for(int m);  // register qubits of a tile of m qubits (4, or 5 for m >= 13)
+int reg_qubits_for(int m);  // register qubits of a tile of m qubits (4, or 5 for m >= 12)
 
 // The kernel program of one sweep (sv_program.cpp); rq_override > 0 forces the
 // register qubits of the register phases.

@@ -642,6 +642,10 @@ __device__ __forceinline__ void cp_async_wait() {
 #endif
 // Launch shape of the five-register-qubit (32 amplitudes per thread) passes:
 // largest block, resident CTAs per SM hint, and whether tiles are double-buffered.
+// The bound of 256 threads x 2 CTAs caps the kernel at 128 registers, which
+// also lets four 128-thread CTAs (12-qubit complex64 tiles, 32 KiB each) share
+// an SM: a CTA waiting at a barrier or for its tile's copies then leaves three
+// others to issue.
 #ifndef SV_RQ5_MAXT
 #define SV_RQ5_MAXT 256
 #endif
@@ -833,7 +837,7 @@ static cudaError_t launch_sweep_rq(Cx<R>* state, const SweepProgram<R>& prog, cu
 
 template <typename R>
 cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
-  // four register qubits with two tile buffers, or five with one (13-qubit
+  // four register qubits with two tile buffers, or five with one (12-qubit
   // complex64 tiles; complex128 tiles have 11 qubits)
   if constexpr (sizeof(R) == 4)
     if (prog.h.rq == 5) return launch_sweep_rq<R, 5, SV_RQ5_DBUF>(state, prog, stream);

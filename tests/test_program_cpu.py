@@ -48,7 +48,7 @@ def _closing_phase_circuit(n, layers, seed):
     general U3, diagonal (theta = 0), anti-diagonal (theta = pi), real, phase
     and Clifford gates -- with CZ, CP and controlled RZ between near and far
     qubits, so that closing phases and other diagonals must wait for later
-    passes (17 qubits: several 13-qubit tiles)."""
+    passes (17 qubits: several 12-qubit tiles)."""
     from workloads.circuits import Gate
     rng = np.random.default_rng(seed)
     one = ["u3", "u3", "u3z", "u3x", "h", "s", "t", "sx", "rx", "ry", "rz", "p", "y"]
