@@ -243,6 +243,46 @@ def test_library_owned_state(svlib, cuda_dev):
     s.free()
 
 
+def test_26q_c64_product_layers_then_cz_sampled_amplitudes(svlib, cuda_dev):
+    """The 12-qubit-tile path (complex64 states of 26 qubits and more) against
+    amplitudes the oracle computes one at a time: 12 layers of Haar-angle U3 on
+    every qubit leave a product state (per qubit, the oracle's 2-vector), and
+    a closing layer of CZ on even then odd neighbour pairs multiplies amplitude
+    b by (-1)^(number of neighbour pairs with both bits set).  Closing phases
+    cross passes and the CZs fold into tables on the way."""
+    import torch
+    n, layers = 26, 12
+    rng = np.random.default_rng(26)
+    gates = []
+    for _ in range(layers):
+        for q in range(n):
+            gates.append(Gate("u3", [q], params=list(rng.uniform(0, 2 * np.pi, 3))))
+    for start in (0, 1):
+        for q in range(start, n - 1, 2):
+            gates.append(Gate("z", [q + 1], controls=[q]))
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=5)
+    assert passes >= 2
+    st = torch.empty(2 ** n, dtype=torch.complex64, device="cuda")
+    B.sv_init_basis(st, 0)
+    B.sv_apply_circuit(st, gates, fuse_max_k=5)
+    torch.cuda.synchronize()
+    # per qubit: the oracle's one-qubit state after that qubit's gates
+    vec = []
+    for q in range(n):
+        mine = [Gate("u3", [0], params=g.params) for g in gates if g.name == "u3" and g.targets == [q]]
+        vec.append(oracle.run(1, mine))
+    idx = rng.integers(0, 2 ** n, 2000, dtype=np.int64)
+    got = st[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
+    for b, gv in zip(idx.tolist(), got):
+        bits = [(b >> q) & 1 for q in range(n)]
+        amp = complex(np.prod([vec[q][bits[q]] for q in range(n)]))
+        if sum(bits[q] & bits[q + 1] for q in range(n - 1)) & 1:
+            amp = -amp
+        assert abs(gv - amp) <= TOL_STATE[B.SV_C64], (b, gv, amp)
+    norm = float(torch.linalg.vector_norm(st.view(torch.float32).double()))
+    assert abs(norm - 1) < 1e-4
+
+
 @pytest.mark.slow
 def test_full_size_30q_c64_forward_then_inverse(svlib, cuda_dev):
     """At the bench's size (30 qubits, 2^30 amplitudes) the oracle cannot run
