@@ -1,0 +1,107 @@
+"""The serving loop's host logic on the CPU: admission against the HBM budget,
+routing by size, queue-limit and over-budget rejections, and that every
+request is accounted for.  The device calls are replaced by fakes that take
+time in proportion to the state size (no GPU is touched)."""
+import time
+
+import pytest
+import torch
+
+from paper_2608_09733_gb300 import binding as B
+from workloads import serving_stream
+
+
+class _Stream:
+    cuda_stream = 0
+
+
+class _Event:
+    def __init__(self, *a, **k):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = time.perf_counter()
+
+    def query(self):
+        return time.perf_counter() - self.t > 0.0005
+
+
+class _StreamCtx:
+    def __init__(self, s):
+        pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+@pytest.fixture
+def fake_device(monkeypatch):
+    calls = {"small": 0, "large": 0}
+    empty, zeros = torch.empty, torch.zeros
+
+    def host_empty(*a, **k):
+        k.pop("device", None)
+        return empty(*a, **k)
+
+    def host_zeros(*a, **k):
+        k.pop("device", None)
+        return zeros(*a, **k)
+
+    def small(nq, sets, dtype=0, out=None, stream=None):
+        calls["small"] += len(nq)
+        out.copy_(torch.tensor([float(n) for n in nq], dtype=out.dtype))  # sum <Z_q> of |0..0> = n
+        return out
+
+    def apply(st, gates, *a, **k):
+        calls["large"] += 1
+        time.sleep(2e-4 * (st.numel() >> 13))
+
+    def expect(st, out=None, stream=None):
+        n = out.numel() - 1
+        out[n] = float(n)
+        return out
+
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _Stream())
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "stream", _StreamCtx)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch, "empty", host_empty)
+    monkeypatch.setattr(torch, "zeros", host_zeros)
+    monkeypatch.setattr(B, "sv_run_batch_small", small)
+    monkeypatch.setattr(B, "sv_init_basis", lambda st, i=0, stream=None: None)
+    monkeypatch.setattr(B, "sv_apply_circuit", apply)
+    monkeypatch.setattr(B, "sv_expect_z_all", expect)
+    return calls
+
+
+def test_admission_routing_and_accounting(fake_device):
+    from paper_2608_09733_gb300.serving import Server
+    stream = serving_stream(rate=3000.0, duration=0.05, n_lo=8, n_hi=19, d_lo=2, d_hi=6, seed=3)
+    budget = 8 * (1 << 18) * 3  # three 18-qubit complex64 states; 19-qubit requests exceed it
+    srv = Server(B.SV_C64, budget_bytes=budget, workers=4, max_small_batch=64)
+    stats, reqs = srv.run(stream, time_limit=30.0)
+    assert stats.offered == len(stream)
+    assert stats.completed + stats.rejected + stats.failed + stats.unfinished == stats.offered
+    assert stats.failed == 0 and stats.unfinished == 0
+    assert 0 < stats.peak_inflight_bytes <= budget
+    for r in reqs:
+        if 8 * (1 << r.n) > budget:
+            assert r.path == "rejected"
+        elif r.path != "rejected":
+            assert r.path == ("small" if r.n <= srv.small_max_n else "large")
+            assert r.result == float(r.n)  # the fake's sum <Z_q> for |0..0>
+            assert r.done >= r.arrival
+    assert fake_device["small"] == stats.small and fake_device["large"] == stats.large
+    assert stats.small > 0 and stats.large > 0
+
+
+def test_queue_limit_rejects(fake_device):
+    from paper_2608_09733_gb300.serving import Server
+    stream = serving_stream(rate=20000.0, duration=0.02, n_lo=16, n_hi=17, d_lo=2, d_hi=3, seed=4)
+    srv = Server(B.SV_C64, budget_bytes=1e9, workers=1, max_queue=5)
+    stats, _ = srv.run(stream, time_limit=30.0)
+    assert stats.rejected > 0
+    assert stats.completed + stats.rejected == stats.offered
