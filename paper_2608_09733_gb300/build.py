@@ -63,7 +63,9 @@ def sweep_stamp() -> str:
     for f in SWEEP_SOURCES:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # flags without the include directory: that path differs between checkouts
+    # of the same sources, so it must not change the stamp
+    h.update(" ".join(ARCH + [f for f in FLAGS if not f.startswith("-I")]).encode())
     return h.hexdigest()
 
 

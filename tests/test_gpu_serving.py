@@ -21,7 +21,7 @@ def test_packed_small_batch_matches_oracle(svlib, cuda_dev, dt):
     tol = 1e-4 if dt == B.SV_C64 else 1e-10
     for n, g, v in zip(ns, sets, got):
         _, s = oracle.expect_z_all(oracle.run(n, g), n)
-        assert abs(v - s) < tol * max(1, n), (n, v, s)
+        assert abs(v - s) < tol, (n, v, s)
 
 
 def test_packed_small_batch_result_independent_of_batch(svlib, cuda_dev):
@@ -51,7 +51,7 @@ def test_serving_loop_results_alone_equal_in_the_mix(svlib, cuda_dev):
         if r.n <= 14:
             g = serving_circuit(r.n, r.depth, r.seed)
             _, s = oracle.expect_z_all(oracle.run(r.n, g), r.n)
-            assert abs(r.result - s) < 1e-4 * r.n
+            assert abs(r.result - s) < 1e-4, (r.n, r.result, s)
     torch.cuda.synchronize()
 
 

@@ -18,11 +18,13 @@ from workloads import fused_layered_u3_cz, random_circuit
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dt,n", [(B.SV_C64, 20), (B.SV_C128, 13), (B.SV_C64, 7)])
+# 24 qubits (complex64) and 23 (complex128) are the smallest states whose
+# read-out uses the full grid of partial rows, where the fixed array is most used.
+@pytest.mark.parametrize("dt,n", [(B.SV_C64, 24), (B.SV_C64, 20), (B.SV_C128, 23), (B.SV_C128, 13),
+                                  (B.SV_C64, 7)])
 def test_noalloc_matches_regular_readout_on_two_calls(svlib, cuda_dev, dt, n):
     import torch
     tdt = torch.complex64 if dt == B.SV_C64 else torch.complex128
-    tol = 1e-4 if dt == B.SV_C64 else 1e-11
     for call, seed in enumerate((1, 2)):  # two calls in a row share the fixed scratch
         gates = fused_layered_u3_cz(n, 3, seed=seed) if n >= 2 else random_circuit(n, 10, seed=seed)
         st = torch.empty(2 ** n, dtype=tdt, device="cuda")
@@ -34,7 +36,9 @@ def test_noalloc_matches_regular_readout_on_two_calls(svlib, cuda_dev, dt, n):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got)), call
-        assert np.max(np.abs(got - want)) < tol, (call, got, want)
+        # the same kernels on the same grid, summed in the same fixed order:
+        # the two read-outs agree bit for bit
+        assert np.array_equal(got, want), (call, got, want)
 
 
 def test_noalloc_rejects_bad_arguments(svlib, cuda_dev):
