@@ -158,13 +158,19 @@ sv_status sv_apply_circuit(void* state, int n_qubits, sv_dtype dtype, const sv_g
  *                   paper's form (Sec. 9.2)
  *   ops_per_pass    0: as many operations per pass over the state as fit a
  *                   tile; 1: one operation per pass (the plain per-gate path,
- *                   used as a baseline); other values cap the count */
+ *                   used as a baseline); other values cap the count
+ *   tile_qubits     0: the library picks the tile width (the qubits a pass
+ *                   gathers into shared memory) from the state size; 8..13
+ *                   (complex64) or 8..11 (complex128) forces it (capped at
+ *                   n_qubits); other values are SV_ERR_INVALID.  The results
+ *                   are the same up to rounding; the choice changes the passes
+ *                   and the kernel that runs them */
 typedef enum { SV_BLOCK_AUTO = 0, SV_BLOCK_DENSE = 1 } sv_block_mode;
 typedef struct sv_exec_opts {
   int32_t fuse_max_k;
   int32_t block_mode;
   int32_t ops_per_pass;
-  int32_t reserved;
+  int32_t tile_qubits;
 } sv_exec_opts;
 
 /* sv_apply_circuit with explicit options (opts NULL = all zero). */

@@ -63,7 +63,7 @@ class SvGate(ctypes.Structure):
 
 class SvExecOpts(ctypes.Structure):
     _fields_ = [("fuse_max_k", ctypes.c_int32), ("block_mode", ctypes.c_int32), ("ops_per_pass", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("tile_qubits", ctypes.c_int32)]
 
 
 SV_BLOCK_AUTO, SV_BLOCK_DENSE = 0, 1
@@ -280,17 +280,18 @@ def sv_apply_circuit(state, gates, param_values=None, fuse_max_k: int = 0, strea
                                    pp, npv, int(fuse_max_k), _stream(stream)))
 
 
-def _opts(fuse_max_k=0, block_mode=0, ops_per_pass=0):
+def _opts(fuse_max_k=0, block_mode=0, ops_per_pass=0, tile_qubits=0):
     o = SvExecOpts()
     o.fuse_max_k, o.block_mode, o.ops_per_pass = int(fuse_max_k), int(block_mode), int(ops_per_pass)
+    o.tile_qubits = int(tile_qubits)
     return o
 
 
 def sv_apply_circuit_ex(state, gates, param_values=None, fuse_max_k: int = 0, block_mode: int = 0,
-                        ops_per_pass: int = 0, stream=None):
+                        ops_per_pass: int = 0, stream=None, tile_qubits: int = 0):
     g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
-    o = _opts(fuse_max_k, block_mode, ops_per_pass)
+    o = _opts(fuse_max_k, block_mode, ops_per_pass, tile_qubits)
     _check(load().sv_apply_circuit_ex(ctypes.c_void_p(state.data_ptr()), _n_of(state), _dtype_of(state), g.arr, g.n,
                                       pp, npv, ctypes.byref(o), _stream(stream)))
 
@@ -325,13 +326,13 @@ def sv_expect_z_all(state, out=None, stream=None):
 
 
 def sv_plan_info(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, block_mode: int = 0,
-                 ops_per_pass: int = 0):
+                 ops_per_pass: int = 0, tile_qubits: int = 0):
     """(number of blocks, number of HBM passes, block start indices)."""
     g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     nb, ns = ctypes.c_int(), ctypes.c_int()
     starts = (ctypes.c_int * (g.n + 1))()
-    o = _opts(fuse_max_k, block_mode, ops_per_pass)
+    o = _opts(fuse_max_k, block_mode, ops_per_pass, tile_qubits)
     _check(load().sv_plan_info(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), ctypes.byref(nb), ctypes.byref(ns),
                                starts))
     return nb.value, ns.value, [starts[i] for i in range(nb.value + 1)]
@@ -367,13 +368,13 @@ def sv_sample(state, uniforms, out=None, stream=None) -> np.ndarray:
 
 
 def sv_emulate_apply(state: np.ndarray, n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0,
-                     block_mode: int = 0, ops_per_pass: int = 0) -> np.ndarray:
+                     block_mode: int = 0, ops_per_pass: int = 0, tile_qubits: int = 0) -> np.ndarray:
     """Runs the kernel programs the plan of `gates` builds for `dtype` on the
     host, in double precision, on a complex128 numpy state (in place)."""
     assert state.dtype == np.complex128 and state.size == 1 << n and state.flags.c_contiguous
     g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
-    o = _opts(fuse_max_k, block_mode, ops_per_pass)
+    o = _opts(fuse_max_k, block_mode, ops_per_pass, tile_qubits)
     _check(load().sv_emulate_apply(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o),
                                    ctypes.c_void_p(state.ctypes.data)))
     return state

@@ -56,7 +56,13 @@ AddrRangeFn addr_range_fn() {
 
 void set_last_error(const std::string& m) { g_last_error = m; }
 
-void sync_stream(cudaStream_t s) { cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize"); }
+void sync_stream(cudaStream_t s) {
+  cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  const int st = take_sweep_status(s);
+  if (st == SV_ERR_TIMEOUT)
+    fail(SV_ERR_TIMEOUT, "a pass kernel gave up waiting for its tile copies (bounded wait ran out); the state is not valid");
+  if (st != SV_OK) fail(SV_ERR_CUDA, "reading the pass kernels' device status failed");
+}
 
 void check_device_buffer(const void* p, size_t bytes, const char* what) {
   if (!p) fail(SV_ERR_INVALID, std::string(what) + " is NULL");
@@ -290,7 +296,7 @@ void run_programs(void* state, int n, const std::vector<SweepProgram<R>>& progs,
   const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << n);  // read + write the state
   for (const SweepProgram<R>& P : progs) {
     Prof pr(stream, "sweep", bytes);
-    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), P, stream), "sweep launch");
+    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), P, stream, &pr.family), "sweep launch");
     pr.done();
   }
 }

@@ -36,7 +36,8 @@ enum OpKind : uint8_t {
                     // slots present), four blocks of four coefficients at `coef`
   OPK_KROT = 7,     // register phase only: real rotations [[C, -S], [S, C]] on register slots (rmask =
                     // the slots present).  complex64: three shears, coef[s] = (tan(alpha/2), sin(alpha));
-                    // complex128: scaled form, coef[s].re = S/C (bit s of rval clear) or C/S (set)
+                    // complex128: scaled form, coef[s].re = S/C (bit s of rval clear) or C/S (set), the
+                    // factor max(C, S) carried by a phase table
   OPK_PHASE = 8,    // register phase only: amplitude j of the thread's 2^RQ is multiplied by
                     // coef[var * table_stride(RQ) + j]; var collects k selector bits, selector i being bit
                     // gq[i] of the thread's local bits (gq[i] < 64) or global bit gq[i] - 64 of the tile
@@ -232,8 +233,11 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
 // ----------------------------------------------------------------- launches
 // (sv_sweep.cu / sv_reduce.cu).  All return cudaError_t of the launch.
 
+// *kernel (if not NULL) names the pass kernel that ran: "sweep_tma" (TMA
+// tile movement) or "sweep" (cp.async).
 template <typename R>
-cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream);
+cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream,
+                         const char** kernel = nullptr);
 template <typename R>
 cudaError_t launch_init_basis(Cx<R>* state, int n, uint64_t index, cudaStream_t stream);
 // One CTA per small request (whole state in shared memory): request b runs
@@ -255,6 +259,10 @@ size_t expect_z_all_scratch_doubles(int n);
 size_t expect_terms_scratch_doubles(int n, int n_terms);
 
 int device_sm_count();
+
+// Reads and clears the status a pass kernel recorded on the device (SV_OK, or
+// SV_ERR_TIMEOUT when a bounded wait ran out); synchronizes `stream`.
+int take_sweep_status(cudaStream_t stream);
 
 // Kernel timing (sv_profile_*): Prof p(stream, "sweep", bytes); launch; p.done();
 struct Prof {

@@ -11,6 +11,7 @@
 //  * the tile scheduler: packs consecutive operations whose non-diagonal
 //    qubits fit one shared-memory tile into a single pass over HBM.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 
@@ -552,6 +553,8 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
   const int fuse_max_k = opts.fuse_max_k;
   if (opts.block_mode != SV_BLOCK_AUTO && opts.block_mode != SV_BLOCK_DENSE) fail(SV_ERR_INVALID, "unknown block_mode");
   if (opts.ops_per_pass < 0) fail(SV_ERR_INVALID, "ops_per_pass must be >= 0");
+  if (opts.tile_qubits != 0 && (opts.tile_qubits < 8 || opts.tile_qubits > (dtype == SV_C64 ? 13 : 11)))
+    fail(SV_ERR_INVALID, "tile_qubits must be 0, or 8..13 (complex64) / 8..11 (complex128)");
   if (n < 1 || n > SV_MAX_QUBITS) fail(SV_ERR_INVALID, "n_qubits out of range");
   if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
   if (fuse_max_k != 0 && (fuse_max_k < 2 || fuse_max_k > 5))
@@ -588,7 +591,9 @@ Plan make_plan(int n, sv_dtype dtype, const sv_gate* gates, size_t n_gates, cons
   };
   drop_identities(p.ops);
   int pool = dtype == SV_C64 ? SweepProgram<float>::kPool : SweepProgram<double>::kPool;
-  const int tile_q = tile_q_override > 0 ? tile_q_override : tile_qubits_for(dtype, n);
+  const int tile_q = tile_q_override > 0 ? tile_q_override
+                     : opts.tile_qubits > 0 ? std::min(opts.tile_qubits, n)
+                                            : tile_qubits_for(dtype, n);
   const int max_ops = opts.ops_per_pass > 0 ? std::min(opts.ops_per_pass, kMaxOps) : kMaxOps;
   p.sweeps = schedule_sweeps(n, p.ops, tile_q, low_qubits_for(dtype), pool, opts.ops_per_pass);
   if (opts.ops_per_pass != 1) {

@@ -540,8 +540,18 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
           for (int x = 0; x < nvar() * NT; x++)
             if ((x >> s2) & 1) tab[x] *= sp[s2].elam;  // bit s2 of x is bit s2 of j (NT = 2^rq)
           sc *= sp[s2].g;
-          if (sizeof(R) == 8) sc *= std::max(sp[s2].C, sp[s2].S);  // the scaled form's factor
         }
+        // complex128 takes the scaled form (two multiply-adds per component),
+        // which leaves every amplitude multiplied by max(C, S) per rotated
+        // slot, a factor the table carries; complex64 takes three shears (one
+        // packed FMA each, no factor).  The scaled form measured slower for
+        // complex64 on GB300 (6.00 against 5.65 ms per 30-qubit pass): its
+        // per-slot form test and extra temporaries cost more, at the kernel's
+        // 128-register budget, than the packed FMA per pair it saves.
+        const bool scaled = sizeof(R) == 8;
+        if (scaled)
+          for (int s2 = 0; s2 < rq; s2++)
+            if ((present >> s2) & 1u) sc *= std::max(sp[s2].C, sp[s2].S);
         if (tab_dep(present)) flush();
         Tmp k = blank(OPK_KROT);
         k.d.rmask = (uint8_t)present;
@@ -549,7 +559,7 @@ void build_program(const Plan& plan, const Sweep& sw, SweepProgram<R>& P, int rq
         for (int s2 = 0; s2 < rq; s2++) {
           if (!((present >> s2) & 1u)) continue;
           const double C = sp[s2].C, S = sp[s2].S;
-          if (sizeof(R) == 4) {  // three shears: (tan(alpha/2), sin(alpha))
+          if (!scaled) {         // three shears: (tan(alpha/2), sin(alpha))
             k.m[s2] = cplx(S / (1.0 + C), S);
           } else if (C >= S) {   // scaled form (a - t b, b + t a), t = S/C
             k.m[s2] = S / C;
@@ -728,8 +738,9 @@ void emulate_reg_op(const SweepProgram<R>& P, const DevOp& op, uint32_t code, in
         if (!((rm >> S) & 1u)) continue;
         const double t = (double)cf[S].re, sn = (double)cf[S].im;
         const bool cot = (rv >> S) & 1u;
+        const bool shears = sizeof(R) == 4;
         pairs(S, false, [&](zc& a, zc& b) {
-          if (sizeof(R) == 4) {
+          if (shears) {
             a -= t * b;
             b += sn * a;
             a -= t * b;

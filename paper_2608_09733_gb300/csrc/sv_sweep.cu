@@ -20,9 +20,12 @@
 // phase, with an XOR swizzle of 16-byte granules so the strided register
 // groups do not collide in banks.  Dense k >= 3 operations (the paper's fused
 // blocks) run group by group straight in shared memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdlib>
+#include <mutex>
 
 #include "sv_internal.h"
 
@@ -122,11 +125,11 @@ __device__ __forceinline__ void r_u1(Cx<R> (&v)[1 << RQ], const Cx<R>* cf) {
 }
 
 // Real rotation [[C, -S], [S, C]] on register slot S.
-//  - float (issue-bound): three in-place shears a -= t b; b += s a; a -= t b
-//    with coef = (t, s) = (tan(alpha/2), sin(alpha)); no temporaries, one
-//    packed FMA per shear.
-//  - double (FP64-pipe-bound): two FMAs per component in scaled form, the
-//    scale carried by a later phase table: coef.re = t and, with COT clear,
+//  - complex64 (issue-bound): three in-place shears a -= t b; b += s a;
+//    a -= t b with coef = (t, s) = (tan(alpha/2), sin(alpha)); no
+//    temporaries, one packed FMA per shear.
+//  - complex128 (FP64-pipe-bound): two FMAs per component in scaled form,
+//    the scale carried by a phase table: coef.re = t and, with COT clear,
 //    (a, b) -> (a - t b, b + t a) (scale C, t = S/C); with COT set,
 //    (a, b) -> (t a - b, a + t b) (scale S, t = C/S).
 // a += c * b for the real and imaginary parts at once: one packed two-lane
@@ -470,14 +473,27 @@ __device__ __forceinline__ void reg_store(const Cx<R> (&v)[1 << RQ], Cx<R>* s, u
 }
 
 // ---------------------------------------------------------------- shared-memory ops
+// The threads that share one tile: the whole CTA (bar == 0, __syncthreads),
+// or one group of a CTA that works on several tiles at once (named barrier `bar` over
+// `nthr` threads, a multiple of 32).  tid is the thread's index in the group.
+struct Grp {
+  uint32_t tid, nthr, bar;
+};
+__device__ __forceinline__ void grp_sync(const Grp& g) {
+  if (g.bar == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;\n" ::"r"(g.bar), "r"(g.nthr) : "memory");
+}
+
 
 template <typename R, int K>
-__device__ __forceinline__ void s_denseK(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf) {
+__device__ __forceinline__ void s_denseK(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, const Grp& gr) {
   constexpr int D = 1 << K;
   uint32_t bit[K];
 #pragma unroll
   for (int i = 0; i < K; i++) bit[i] = 1u << op.pos[i];
-  for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> K); g += blockDim.x) {
+  for (uint32_t g = gr.tid; g < (uint32_t)(tsz >> K); g += gr.nthr) {
     uint32_t b = g;
 #pragma unroll
     for (int i = 0; i < K; i++) b = ins0(b, op.spos[i]);
@@ -507,11 +523,12 @@ __device__ __forceinline__ void s_denseK(Cx<R>* s, int tsz, const DevOp& op, con
 }
 
 template <typename R>
-__device__ __forceinline__ void s_diag(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, uint64_t base) {
+__device__ __forceinline__ void s_diag(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, uint64_t base,
+                                       const Grp& gr) {
   uint32_t xi = 0;
   for (int i = 0; i < op.k; i++)
     if (op.pos[i] == 0xFF) xi |= (uint32_t)((base >> op.gq[i]) & 1ull) << i;
-  for (uint32_t a = threadIdx.x; a < (uint32_t)tsz; a += blockDim.x) {
+  for (uint32_t a = gr.tid; a < (uint32_t)tsz; a += gr.nthr) {
     if ((a & op.lmask) != op.lval) continue;
     const uint32_t pa = phys<R>(a);
     if (op.kind == OPK_SIGN) {
@@ -528,10 +545,10 @@ __device__ __forceinline__ void s_diag(Cx<R>* s, int tsz, const DevOp& op, const
 // Anti-diagonal and swap ops of a shared-memory phase (tiles too small for
 // register groups).
 template <typename R>
-__device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf) {
+__device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const Cx<R>* cf, const Grp& gr) {
   if (op.kind == OPK_ANTIDIAG) {
     const int p = op.pos[0];
-    for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 1); g += blockDim.x) {
+    for (uint32_t g = gr.tid; g < (uint32_t)(tsz >> 1); g += gr.nthr) {
       const uint32_t i0 = ins0(g, p);
       if ((i0 & op.lmask) != op.lval) continue;
       const uint32_t a = phys<R>(i0), b = phys<R>(i0 | (1u << p));
@@ -540,7 +557,7 @@ __device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const
       s[b] = cmul(cf[1], x);
     }
   } else {
-    for (uint32_t g = threadIdx.x; g < (uint32_t)(tsz >> 2); g += blockDim.x) {
+    for (uint32_t g = gr.tid; g < (uint32_t)(tsz >> 2); g += gr.nthr) {
       const uint32_t b = ins0(ins0(g, op.spos[0]), op.spos[1]);
       if ((b & op.lmask) != op.lval) continue;
       const uint32_t i01 = phys<R>(b | (1u << op.pos[0])), i10 = phys<R>(b | (1u << op.pos[1]));
@@ -556,25 +573,92 @@ __device__ __forceinline__ void s_perm(Cx<R>* s, int tsz, const DevOp& op, const
 // Runs every phase of a program on a tile that is already in shared memory.
 // KMAX: widest dense operation the program runs in shared memory; RQ: the
 // register qubits of its register phases.
-template <typename R, int KMAX, int RQ, int OPS>
+struct NoRelease {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// Global offset of local amplitude l of a tile: local bit i is global bit
+// tq[i] (without the tile's base).
+__device__ __forceinline__ uint64_t tile_offset(uint32_t l, const ProgramHeader& h) {
+  uint64_t off = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxTileQ; i++) {
+    if (i >= h.m) break;
+    if ((l >> i) & 1u) off |= 1ull << h.tq[i];
+  }
+  return off;
+}
+
+// Writes the thread's 2^RQ register amplitudes straight to the state: the
+// amplitude of register combination j is at g + (XOR of gs[i] over the set
+// bits i of j).  With local bit 0 in register slot 0, pairs (j, j+1) are
+// adjacent in the state and go out as one 16-byte store (complex64).
+template <typename R, int RQ>
+__device__ __forceinline__ void reg_store_global(const Cx<R> (&v)[1 << RQ], Cx<R>* __restrict__ state, uint64_t g,
+                                                 const uint64_t (&gs)[RQ], bool pairs) {
+  if (sizeof(Cx<R>) == 8 && pairs) {
+    uint64_t off[(1 << RQ) / 2];
+    off[0] = g;
+#pragma unroll
+    for (int j = 2; j < (1 << RQ); j += 2) {
+      const int low = j & -j;
+      const int i = low == 2 ? 1 : low == 4 ? 2 : low == 8 ? 3 : 4;
+      off[j / 2] = off[(j ^ low) / 2] ^ gs[i];
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << RQ); j += 2)
+      *reinterpret_cast<float4*>(state + off[j / 2]) =
+          make_float4((float)v[j].re, (float)v[j].im, (float)v[j + 1].re, (float)v[j + 1].im);
+  } else {
+    uint64_t off[1 << RQ];
+    off[0] = g;
+#pragma unroll
+    for (int j = 1; j < (1 << RQ); j++) {
+      const int low = j & -j;
+      const int i = low == 1 ? 0 : low == 2 ? 1 : low == 4 ? 2 : low == 8 ? 3 : 4;
+      off[j] = off[j ^ low] ^ gs[i];
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << RQ); j++) state[off[j]] = v[j];
+  }
+}
+
+// Runs every phase of a program on a tile that is already in shared memory.
+// KMAX: widest dense operation the program runs in shared memory; RQ: the
+// register qubits of its register phases.
+//
+// DIRECT (TMA pass): the tile goes back to the state from the last phase
+// instead of staying in shared memory.  A last register phase loads its
+// registers, meets the group's barrier, calls release() (the stage is free:
+// the caller refills it) and writes its results straight to `gstate` at the
+// tile's `base`; any other last phase is followed by a copy of the stage to
+// the state, a barrier and release().
+template <typename R, int KMAX, int RQ, int OPS, bool DIRECT = false, typename Release = NoRelease>
 __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, const Cx<R>* coef, Cx<R>* s, int tsz,
-                                           uint64_t base) {
+                                           uint64_t base, const Grp& gr, Cx<R>* gstate = nullptr,
+                                           const Release& release = Release()) {
   const ProgramHeader& h = P.h;
   for (int p = 0; p < h.nphases; p++) {
     const Phase& ph = P.ph[p];
+    const bool direct = DIRECT && p == h.nphases - 1 && ph.kind == PH_REG;
     if (ph.kind == PH_REG) {
-      if (threadIdx.x < (1u << ph.ntpos)) {
-        // thread bits: the thread index with zeros inserted at the register
-        // positions (rp[] ascending), i.e. deposited into tpos[]
-        uint32_t tb = threadIdx.x;
-        uint32_t m[RQ];
+      const bool active = gr.tid < (1u << ph.ntpos);
+      // thread bits: the thread index with zeros inserted at the register
+      // positions (rp[] ascending), i.e. deposited into tpos[]
+      uint32_t tb = gr.tid;
+      uint32_t m[RQ];
 #pragma unroll
-        for (int i = 0; i < RQ; i++) {
-          m[i] = 1u << ph.rp[i];
-          tb = ins0(tb, ph.rp[i]);
-        }
-        Cx<R> v[1 << RQ];
-        reg_load<R, RQ>(v, s, tb, m);
+      for (int i = 0; i < RQ; i++) {
+        m[i] = 1u << ph.rp[i];
+        tb = ins0(tb, ph.rp[i]);
+      }
+      Cx<R> v[1 << RQ];
+      if (active) reg_load<R, RQ>(v, s, tb, m);
+      if (direct) {
+        grp_sync(gr);  // every thread has its registers: the stage is free
+        release();
+      }
+      if (active) {
         // Sign flips commute with each other: a run of them becomes one mask of
         // the thread's amplitudes to negate, applied before the next other op.
         uint32_t neg = 0;
@@ -600,29 +684,46 @@ __device__ __forceinline__ void run_phases(const SweepProgram<R>& P, const Cx<R>
           apply_reg<R, RQ, OPS>(v, op, code, coef, tb, base);
         }
         if (neg) apply_neg<R, RQ>(v, neg);
-        reg_store<R, RQ>(v, s, tb, m);
+        if (direct) {
+          uint64_t gs[RQ];
+#pragma unroll
+          for (int i = 0; i < RQ; i++) gs[i] = 1ull << h.tq[ph.rp[i]];
+          reg_store_global<R, RQ>(v, gstate, base | tile_offset(tb, h), gs, m[0] == 1u);
+        } else {
+          reg_store<R, RQ>(v, s, tb, m);
+        }
       }
+      if (direct) return;
     } else {
       const DevOp& op = P.ops[ph.first];
       if ((base & op.xmask) == op.xval) {
         const Cx<R>* cf = coef + op.coef;
         switch (op.kind) {
           case OPK_DIAG:
-          case OPK_SIGN: s_diag<R>(s, tsz, op, cf, base); break;
+          case OPK_SIGN: s_diag<R>(s, tsz, op, cf, base, gr); break;
           case OPK_ANTIDIAG:
-          case OPK_SWAP: s_perm<R>(s, tsz, op, cf); break;
+          case OPK_SWAP: s_perm<R>(s, tsz, op, cf, gr); break;
           default:
             switch (op.k) {
-              case 1: s_denseK<R, 1>(s, tsz, op, cf); break;
-              case 2: s_denseK<R, 2>(s, tsz, op, cf); break;
-              case 3: if constexpr (KMAX >= 3) s_denseK<R, 3>(s, tsz, op, cf); break;
-              case 4: if constexpr (KMAX >= 4) s_denseK<R, 4>(s, tsz, op, cf); break;
-              default: if constexpr (KMAX >= 5) s_denseK<R, 5>(s, tsz, op, cf); break;
+              case 1: s_denseK<R, 1>(s, tsz, op, cf, gr); break;
+              case 2: s_denseK<R, 2>(s, tsz, op, cf, gr); break;
+              case 3: if constexpr (KMAX >= 3) s_denseK<R, 3>(s, tsz, op, cf, gr); break;
+              case 4: if constexpr (KMAX >= 4) s_denseK<R, 4>(s, tsz, op, cf, gr); break;
+              default: if constexpr (KMAX >= 5) s_denseK<R, 5>(s, tsz, op, cf, gr); break;
             }
         }
       }
     }
-    __syncthreads();
+    grp_sync(gr);
+  }
+  if constexpr (DIRECT) {  // the last phase was not a register phase: copy the stage out
+    constexpr int A = 16 / sizeof(Cx<R>);
+    for (uint32_t v = gr.tid; v < (uint32_t)(tsz / A); v += gr.nthr) {
+      const uint32_t l = v * A;
+      *reinterpret_cast<uint4*>(gstate + (base | tile_offset(l, h))) = *reinterpret_cast<const uint4*>(s + phys<R>(l));
+    }
+    grp_sync(gr);
+    release();
   }
 }
 
@@ -714,7 +815,7 @@ __global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
     }
     __syncthreads();  // ... and every thread's
     Cx<R>* s = buf[cur];
-    run_phases<R, KMAX, RQ, OPS>(P, scoef, s, tsz, base);
+    run_phases<R, KMAX, RQ, OPS>(P, scoef, s, tsz, base, Grp{threadIdx.x, blockDim.x, 0u});
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const uint32_t l = (uint32_t)(v * A);
       *reinterpret_cast<uint4*>(state + (base + (hi_off[l >> h.L] | (l & lowmask)))) =
@@ -722,6 +823,257 @@ __global__ void __launch_bounds__(RQ == 5 ? SV_RQ5_MAXT : 256,
     }
     __syncthreads();  // the buffer is free for the next copies
   }
+}
+
+// ---------------------------------------------------------------- TMA pass
+//
+// The same pass as k_sweep with the tile movement done by the tensor memory
+// accelerator.  One CTA per SM walks its tiles (tile = blockIdx.x + k *
+// gridDim.x) through a ring of `ns` shared-memory stages (tile k in stage
+// k mod ns):
+//   - a tile is 16 boxes of 2 KiB, each box the 2^(E+4) amplitudes of local
+//     bits 0..E+3, where 2^E amplitudes make one 128-byte row (E = 4 for
+//     complex64, 3 for complex128).  A five-dimensional tensor map per pass
+//     describes the state as [2^(n-q3)][2^(q3-q2)][2^(q2-q1)][2^(q1-E)][row],
+//     q1..q3 being the tile qubits at local positions E+1..E+3; a box takes
+//     two entries of each outer dimension.  The 128-byte swizzle of the copies
+//     places amplitude l at phys(l), the XOR layout the register phases read;
+//   - NC groups of 2^(m-RQ) threads each take every NC-th tile: wait for its
+//     stage to fill, run the program's phases on it (a named barrier per
+//     group), then thread 0 of the group stores the stage back with TMA, waits
+//     until the store has read shared memory, and refills the stage with the
+//     tile ns places further on.
+// So ns - NC tiles are loading while the groups compute, and no compute
+// thread spends instructions on addresses or 16-byte copies.  There is no
+// separate producer warp: a 17th warp would cap the compute threads' registers
+// at 96 (the register file is split between the SM's four schedulers).
+//
+// Every wait is bounded (one second of %globaltimer): a wait that runs out
+// records SV_ERR_TIMEOUT in g_sweep_status, the CTA's groups stop, and the
+// copies already issued are waited for (bounded) before the CTA exits.
+
+__device__ int g_sweep_status = 0;  // SV_OK, or the first error a pass kernel recorded
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of parity `parity` to complete, for at most
+// kWaitLimitNs.  Gives up early when another thread of the CTA has already
+// given up (*cta_flag != 0; pass NULL to wait regardless).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* cta_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; it++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 15u) == 0) {
+      if (cta_flag && *cta_flag) return false;
+      if (global_ns() - t0 > kWaitLimitNs) {
+        atomicCAS(&g_sweep_status, 0, (int)SV_ERR_TIMEOUT);
+        if (cta_flag) *cta_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const volatile uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32((const void*)p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(volatile uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;\n" ::"r"(smem_u32((const void*)p)), "r"(v) : "memory");
+}
+// Waits until *tag == want (read with acquire), for at most kWaitLimitNs
+// (give-up rules as mbar_wait_bounded).
+__device__ __forceinline__ bool tag_wait_bounded(const volatile uint32_t* tag, uint32_t want, volatile int* cta_flag) {
+  if (ld_acquire_u32(tag) == want) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; it++) {
+    if (ld_acquire_u32(tag) == want) return true;
+    if ((it & 15u) == 0) {
+      if (*cta_flag) return false;
+      if (global_ns() - t0 > kWaitLimitNs) {
+        atomicCAS(&g_sweep_status, 0, (int)SV_ERR_TIMEOUT);
+        *cta_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load5(uint32_t dst, const void* map, int c1, int c2, int c3, int c4,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+// Box geometry of a pass, passed beside its tensor map: the tile qubits at
+// local positions E+1..E+3 (q1..q3) and above E+3 (hq[], the box index bits).
+struct TmaBoxes {
+  int q1, q2, q3;
+  int nhq;
+  int hq[kMaxTileQ];
+};
+
+template <typename R>
+__device__ __forceinline__ void tma_coords(uint64_t g, const TmaBoxes& bx, int& c1, int& c2, int& c3, int& c4) {
+  constexpr int E = sizeof(Cx<R>) == 8 ? 4 : 3;
+  c1 = (int)((g >> E) & ((1ull << (bx.q1 - E)) - 1ull));
+  c2 = (int)((g >> bx.q1) & ((1ull << (bx.q2 - bx.q1)) - 1ull));
+  c3 = (int)((g >> bx.q2) & ((1ull << (bx.q3 - bx.q2)) - 1ull));
+  c4 = (int)(g >> bx.q3);
+}
+
+constexpr int kTmaBoxBytes = 2048;
+// Threads of a group: 2^(m - RQ), 128 for 12-qubit tiles with five register
+// qubits (32 amplitudes a thread).  Sixteen amplitudes a thread (256-thread
+// groups, 24 warps an SM at 80 registers) measured slower: 7.55 against 5.65
+// ms per 30-qubit pass, the per-phase work of a thread spread over half the
+// amplitudes and a third more phases.
+template <int RQ>
+constexpr int tma_group_threads() {
+  return RQ == 5 ? 128 : 256;
+}
+constexpr int kTmaMaxStages = 8;
+static_assert(kTmaMaxStages * 8 % 16 == 0 && 2 * kTmaMaxStages + 1 <= 20, "TMA pass shared-memory layout");
+
+template <typename R, int KMAX, int RQ, int OPS, int NC>
+__global__ void __launch_bounds__(NC * tma_group_threads<RQ>(), 1)
+    k_sweep_tma(Cx<R>* __restrict__ state, const __grid_constant__ CUtensorMap tmap,
+                const __grid_constant__ TmaBoxes bx, const __grid_constant__ SweepProgram<R> P, int ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ProgramHeader& h = P.h;
+  constexpr uint32_t T = tma_group_threads<RQ>();
+  const int tsz = 1 << h.m;
+  const uint32_t tile_bytes = (uint32_t)sizeof(Cx<R>) << h.m;
+  // stages from the first 1024-byte boundary (the swizzle pattern's period),
+  // then the coefficient pool, the stage barriers, the loads issued into each
+  // stage and the CTA's give-up flag
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  unsigned char* stages = smem_raw + pad;
+  Cx<R>* scoef = reinterpret_cast<Cx<R>*>(stages + (size_t)ns * tile_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(scoef + ((h.ncoef + 1) & ~1));
+  unsigned* issued = reinterpret_cast<unsigned*>(bars + kTmaMaxStages);
+  volatile uint32_t* stage_tile = reinterpret_cast<volatile uint32_t*>(issued + kTmaMaxStages);
+  volatile int* flag = reinterpret_cast<volatile int*>(stage_tile + kTmaMaxStages);
+  // per-CTA constants kept in shared memory rather than in every thread's
+  // registers: the deposit mask and steps, and the coordinate offsets of each
+  // box of a tile
+  // (bars is 16-byte aligned: the pool before it holds an even number of
+  // 8-byte complex64 entries or 16-byte complex128 ones; issued is 64 bytes
+  // further, cst 80 bytes after issued and boxc 32 after cst, all 16-aligned)
+  uint64_t* cst = reinterpret_cast<uint64_t*>(issued + 20);
+  int4* boxc = reinterpret_cast<int4*>(cst + 4);
+  const uint32_t full0 = smem_u32(bars), st0 = smem_u32(stages);
+  const uint64_t ntiles = 1ull << (h.n - h.m);
+  const uint64_t K = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // The base of tile t is t with zeros inserted at the tile qubits (its bits
+  // deposited into the other positions, mask M).  Deposits add without
+  // unpacking: dep(t + d) = ((dep(t) | ~M) + dep(d)) & M, the carries running
+  // through the tile positions set to one.
+  auto deposit = [&](uint64_t t) {
+    for (int i = 0; i < h.m; i++) t = ins0_64(t, h.tq[i]);
+    return t;
+  };
+  auto dep_add = [&](uint64_t a, uint64_t d) {
+    const uint64_t M = cst[0];
+    return ((a | ~M) + d) & M;
+  };
+  auto tile_base = [&](uint64_t k) { return deposit(blockIdx.x + k * gridDim.x); };
+  // Lane j < 2^nhq of a loading warp copies box j of a tile: its coordinates
+  // are those of the tile's base plus those of the box's own bits (the bit
+  // fields are disjoint, so the sum has no carries).
+  const uint32_t lane = threadIdx.x & 31u;
+  const int nbox = 1 << bx.nhq;
+  // One warp fills stage b with tile k (base `base`).  The stage's tag names
+  // the tile its barrier's current phase belongs to: groups take tiles
+  // round-robin, so a group can reach tile k + 2 ns while the load of tile
+  // k + ns into the same stage is still to come, and the barrier's phase
+  // parity alone would not tell those two apart.
+  auto load_tile = [&](uint32_t b, uint64_t k, uint64_t base) {
+    if (lane == 0) {
+      issued[b] += 1;
+      st_release_u32(stage_tile + b, (uint32_t)k);
+      mbar_expect_tx(full0 + 8 * b, tile_bytes);
+    }
+    __syncwarp();
+    if ((int)lane < nbox) {
+      int c1, c2, c3, c4;
+      tma_coords<R>(base, bx, c1, c2, c3, c4);
+      const int4 bc = boxc[lane];
+      tma_load5(st0 + b * tile_bytes + lane * kTmaBoxBytes, &tmap, c1 + bc.x, c2 + bc.y, c3 + bc.z, c4 + bc.w,
+                full0 + 8 * b);
+    }
+  };
+  for (int c = threadIdx.x; c < h.ncoef; c += blockDim.x) scoef[c] = P.coef[c];
+  if (threadIdx.x == 0) {
+    *flag = 0;
+    for (int b = 0; b < ns; b++) {
+      mbar_init(full0 + 8 * b, 1);
+      issued[b] = 0;
+      stage_tile[b] = 0xFFFFFFFFu;
+    }
+    cst[0] = deposit((1ull << (h.n - h.m)) - 1ull);
+    cst[1] = deposit((uint64_t)NC * gridDim.x);
+    cst[2] = deposit((uint64_t)ns * gridDim.x);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 32 && (int)threadIdx.x < nbox) {
+    uint64_t gb = 0;
+    for (int i = 0; i < bx.nhq; i++) gb |= (uint64_t)((threadIdx.x >> i) & 1u) << bx.hq[i];
+    int4 bc;
+    tma_coords<R>(gb, bx, bc.x, bc.y, bc.z, bc.w);
+    boxc[threadIdx.x] = bc;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32)  // first fill of the ring
+    for (uint64_t k = 0; k < K && k < (uint64_t)ns; k++) load_tile((uint32_t)k, k, tile_base(k));
+  const uint32_t g = threadIdx.x / T;
+  const Grp gr{threadIdx.x % T, T, 1u + g};
+  const bool loader = gr.tid < 32;  // warp 0 of the group refills the stages it frees
+  uint64_t base = tile_base(g);
+  for (uint64_t k = g; k < K; k += NC, base = dep_add(base, cst[1])) {
+    const uint32_t b = (uint32_t)(k % (uint64_t)ns);
+    // a wait that runs out sets the CTA's flag and the group carries on over
+    // whatever the stage holds: every thread keeps meeting the group's
+    // barriers, so nothing waits forever, and the status says the pass failed
+    if (tag_wait_bounded(stage_tile + b, (uint32_t)k, flag))
+      mbar_wait_bounded(full0 + 8 * b, (uint32_t)((k / ns) & 1), flag);
+    auto release = [&]() {
+      if (loader && k + ns < K && __all_sync(0xffffffffu, *flag == 0)) load_tile(b, k + ns, dep_add(base, cst[2]));
+    };
+    run_phases<R, KMAX, RQ, OPS, true>(P, scoef, reinterpret_cast<Cx<R>*>(stages + (size_t)b * tile_bytes), tsz,
+                                       base, gr, state, release);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *flag)  // stopped early: loads still in flight must land first
+    for (int b = 0; b < ns; b++)
+      if (issued[b]) mbar_wait_bounded(full0 + 8 * b, (issued[b] - 1) & 1u, nullptr);
 }
 
 // Packed small states (serving): CTA b simulates request b entirely in shared
@@ -741,7 +1093,7 @@ __global__ void __launch_bounds__(256) k_small_batch(const SweepProgram<R>* __re
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) s[phys<R>(a)] = Cx<R>{R(a == 0 ? 1 : 0), R(0)};
   __syncthreads();
   for (int p = first_prog[b]; p < first_prog[b + 1]; p++)
-    run_phases<R, 5, kRegQ, kOpsAll>(progs[p], progs[p].coef, s, tsz, 0ull);
+    run_phases<R, 5, kRegQ, kOpsAll>(progs[p], progs[p].coef, s, tsz, 0ull, Grp{threadIdx.x, blockDim.x, 0u});
   double acc = 0.0;
   for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
     const Cx<R> x = s[phys<R>(a)];
@@ -835,14 +1187,169 @@ static cudaError_t launch_sweep_rq(Cx<R>* state, const SweepProgram<R>& prog, cu
   return launch_sweep_k<R, 5, RQ, DBUF, kOpsAll>(state, prog, stream);
 }
 
+// ---- TMA pass: tensor maps and launch
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+
+// The five-dimensional map of one pass (see k_sweep_tma) and its box
+// geometry; false when this pass's tile cannot be described that way.
 template <typename R>
-cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream) {
+static bool tma_map_for(Cx<R>* state, const ProgramHeader& h, CUtensorMap& map, TmaBoxes& bx) {
+  constexpr int E = sizeof(Cx<R>) == 8 ? 4 : 3;  // 2^E amplitudes per 128-byte row
+  if (h.m < E + 4 || h.L < E + 1 || h.m - (E + 4) > 5 || h.n <= h.m) return false;
+  if ((uintptr_t)state % 256) return false;
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  bx.q1 = h.tq[E + 1];
+  bx.q2 = h.tq[E + 2];
+  bx.q3 = h.tq[E + 3];
+  bx.nhq = h.m - (E + 4);
+  for (int i = 0; i < kMaxTileQ; i++) bx.hq[i] = i < bx.nhq ? h.tq[E + 4 + i] : 0;
+  const cuuint64_t amp = sizeof(Cx<R>);
+  const cuuint64_t dims[5] = {128 / sizeof(R), 1ull << (bx.q1 - E), 1ull << (bx.q2 - bx.q1),
+                              1ull << (bx.q3 - bx.q2), 1ull << (h.n - bx.q3)};
+  const cuuint64_t strides[4] = {128, amp << bx.q1, amp << bx.q2, amp << bx.q3};
+  const cuuint32_t box[5] = {(cuuint32_t)(128 / sizeof(R)), 2, 2, 2, 2};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(&map, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5,
+                         (void*)state, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Groups of the TMA pass (tiles in work at once per SM): four of 128 threads
+// hold the SM's register file at 128 registers a thread.  Measured on the
+// 28-qubit layered circuit: three groups 1.65 ms per pass, four 1.44.
+constexpr int kTmaGroups = 4;
+// Shared memory of a TMA pass with ns stages.
+template <typename R>
+static size_t tma_smem_bytes(const ProgramHeader& h, int ns) {
+  return 1024 + (size_t)ns * (sizeof(Cx<R>) << h.m) + sizeof(Cx<R>) * (size_t)((h.ncoef + 1) & ~1) +
+         16 * (size_t)kTmaMaxStages + 16 + 32 + 16 * 32;
+}
+
+template <typename R, int KMAX, int RQ, int OPS>
+static cudaError_t launch_sweep_tma_k(Cx<R>* state, const SweepProgram<R>& prog, const CUtensorMap& map,
+                                      const TmaBoxes& bx, cudaStream_t stream) {
+  constexpr int NC = kTmaGroups;
+  int ns = kTmaMaxStages;  // as many stages as shared memory holds
+  while (ns > NC && tma_smem_bytes<R>(prog.h, ns) > 227 * 1024) ns--;
+  if (ns <= NC) return cudaErrorInvalidConfiguration;
+  const size_t smem = tma_smem_bytes<R>(prog.h, ns);
+  static size_t configured_bytes[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (smem > configured_bytes[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_tma<R, KMAX, RQ, OPS, NC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes[dev] = smem;
+  }
+  const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
+  uint64_t grid = (uint64_t)device_sm_count();
+  if (grid > ntiles) grid = ntiles;
+  k_sweep_tma<R, KMAX, RQ, OPS, NC>
+      <<<(unsigned)grid, NC * tma_group_threads<RQ>(), smem, stream>>>(state, map, bx, prog, ns);
+  return cudaGetLastError();
+}
+
+// Whether the TMA pass runs this program: complex64 states of at least 2^9
+// tiles whose tile groups are 128 threads (12-qubit tiles with five register
+// qubits), unless SV_SWEEP_TMA=0 in the environment selects the cp.async
+// kernel.  (complex128 passes are bound by the FP64 pipe, and at the 128
+// registers of four 128-thread groups per SM their register phases spill.)
+static bool tma_enabled() {
+  const char* e = std::getenv("SV_SWEEP_TMA");
+  return !(e && e[0] == '0');
+}
+
+template <typename R, int RQ>
+static cudaError_t launch_sweep_tma(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream, bool& used) {
+  used = false;
+  if (!tma_enabled() || prog.h.n - prog.h.m < 9 || (1 << (prog.h.m - RQ)) != tma_group_threads<RQ>())
+    return cudaSuccess;
+  CUtensorMap map;
+  TmaBoxes bx;
+  if (!tma_map_for<R>(state, prog.h, map, bx)) return cudaSuccess;
+  int kmax = 1;
+  bool perm = false, other = false;
+  for (int p = 0; p < prog.h.nphases; p++) {
+    const Phase& ph = prog.ph[p];
+    if (ph.kind != PH_SMEM) {
+      for (int o = ph.first; o < ph.first + ph.nops; o++) {
+        const uint32_t kind = prog.ops[o].pad & 15u;
+        if (kind == OPK_ANTIDIAG || kind == OPK_SWAP)
+          perm = true;
+        else if (kind != OPK_KROT && kind != OPK_PHASE && kind != OPK_SIGN)
+          other = true;
+      }
+      continue;
+    }
+    const DevOp& op = prog.ops[ph.first];
+    if ((op.kind == OPK_DENSE || op.kind == OPK_REAL) && op.k > kmax) kmax = op.k;
+  }
+  used = true;
+  if (kmax <= 2 && !other) {
+    if (!perm) return launch_sweep_tma_k<R, 2, RQ, kOpsRot>(state, prog, map, bx, stream);
+    return launch_sweep_tma_k<R, 2, RQ, kOpsPerm>(state, prog, map, bx, stream);
+  }
+  if (kmax <= 2) return launch_sweep_tma_k<R, 2, RQ, kOpsAll>(state, prog, map, bx, stream);
+  if (kmax == 3) return launch_sweep_tma_k<R, 3, RQ, kOpsAll>(state, prog, map, bx, stream);
+  return launch_sweep_tma_k<R, 5, RQ, kOpsAll>(state, prog, map, bx, stream);
+}
+
+template <typename R>
+cudaError_t launch_sweep(Cx<R>* state, const SweepProgram<R>& prog, cudaStream_t stream, const char** kernel) {
   // four register qubits with two tile buffers, or five with one (12-qubit
-  // complex64 tiles; complex128 tiles have 11 qubits)
-  if constexpr (sizeof(R) == 4)
-    if (prog.h.rq == 5) return launch_sweep_rq<R, 5, SV_RQ5_DBUF>(state, prog, stream);
+  // complex64 tiles; complex128 tiles have 11 qubits); large complex64 states
+  // take the TMA pass
+  bool used = false;
+  if (kernel) *kernel = "sweep";
+  if constexpr (sizeof(R) == 4) {
+    if (prog.h.rq == 5) {
+      cudaError_t e = launch_sweep_tma<R, 5>(state, prog, stream, used);
+      if (used && kernel) *kernel = "sweep_tma";
+      if (used || e != cudaSuccess) return e;
+      return launch_sweep_rq<R, 5, SV_RQ5_DBUF>(state, prog, stream);
+    }
+  }
   if (prog.h.rq != 4) return cudaErrorInvalidValue;
   return launch_sweep_rq<R, 4, true>(state, prog, stream);
+}
+
+// Reads and clears the status a pass kernel recorded (SV_OK if none); the
+// caller has synchronized the work it wants covered.
+int take_sweep_status(cudaStream_t stream) {
+  int st = 0, zero = 0;
+  if (cudaMemcpyFromSymbolAsync(&st, g_sweep_status, sizeof(int), 0, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    return (int)SV_ERR_CUDA;
+  }
+  if (st != 0) {
+    cudaMemcpyToSymbolAsync(g_sweep_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, stream);
+    cudaStreamSynchronize(stream);
+  }
+  return st;
 }
 
 template <typename R>
@@ -876,8 +1383,8 @@ template cudaError_t launch_small_batch<float>(const SweepProgram<float>*, const
                                                cudaStream_t);
 template cudaError_t launch_small_batch<double>(const SweepProgram<double>*, const int*, const int*, int, int, double*,
                                                 cudaStream_t);
-template cudaError_t launch_sweep<float>(Cx<float>*, const SweepProgram<float>&, cudaStream_t);
-template cudaError_t launch_sweep<double>(Cx<double>*, const SweepProgram<double>&, cudaStream_t);
+template cudaError_t launch_sweep<float>(Cx<float>*, const SweepProgram<float>&, cudaStream_t, const char**);
+template cudaError_t launch_sweep<double>(Cx<double>*, const SweepProgram<double>&, cudaStream_t, const char**);
 template cudaError_t launch_init_basis<float>(Cx<float>*, int, uint64_t, cudaStream_t);
 template cudaError_t launch_init_basis<double>(Cx<double>*, int, uint64_t, cudaStream_t);
 

@@ -110,3 +110,25 @@ def test_host_pointer_is_rejected_before_any_launch(svlib):
     buf = np.zeros(16, dtype=np.complex64)
     st = svlib.sv_init_basis(ctypes.c_void_p(buf.ctypes.data), 4, B.SV_C64, 0, None)
     assert st in (1, 4)  # SV_ERR_INVALID, or SV_ERR_CUDA when no driver is present
+
+
+def test_tile_width_option(svlib):
+    """sv_exec_opts.tile_qubits: 0 lets the library choose; 8..13 (complex64)
+    or 8..11 (complex128) forces the width; anything else is rejected before
+    any planning.  A narrower tile holds fewer qubits, so it never needs fewer
+    passes on the same circuit."""
+    n = 22
+    g = fused_layered_u3_cz(n, 6, seed=1)
+    _, auto, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5)
+    _, t13, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5, tile_qubits=13)
+    _, t12, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5, tile_qubits=12)
+    _, t8, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5, tile_qubits=8)
+    assert auto == t13 and t8 >= t12 >= t13 >= 1
+    _, c11, _ = B.sv_plan_info(n, B.SV_C128, g, fuse_max_k=5, tile_qubits=11)
+    assert c11 >= 1
+    for dt, bad in ((B.SV_C64, 7), (B.SV_C64, 14), (B.SV_C128, 12), (B.SV_C64, -1)):
+        with pytest.raises(B.SvError):
+            B.sv_plan_info(n, dt, g, fuse_max_k=5, tile_qubits=bad)
+    # capped at the state size: a 6-qubit state plans with any legal width
+    _, small, _ = B.sv_plan_info(6, B.SV_C64, fused_layered_u3_cz(6, 3, seed=2), fuse_max_k=5, tile_qubits=12)
+    assert small == 1
