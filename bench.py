@@ -67,6 +67,10 @@ def parse_args():
     ap.add_argument("--sweep-rates", type=str, default="25,50,100,200",
                     help="serving: extra sub-saturation rates (req/s), each run for --sweep-duration s")
     ap.add_argument("--sweep-duration", type=float, default=10.0)
+    ap.add_argument("--drain", type=float, default=30.0, help="serving: seconds after the last arrival before "
+                                                              "unfinished requests are counted")
+    ap.add_argument("--no-extras", action="store_true", help="gates workload: skip the adjoint, serving and "
+                                                              "complex128 figures of the default line")
     return ap.parse_args()
 
 
@@ -295,7 +299,7 @@ def bench_adjoint(args):
     peaks, src = measured_peaks()
     rev = prof.get("batch_sweep_rev", {"bytes": 0, "total_ms": float("nan"), "launches": 0})
     gbs = rev["bytes"] / (rev["total_ms"] / 1e3) / 1e9 if rev["launches"] else None
-    print(json.dumps({
+    return ({
         "metric": "adjoint grads/s (20q HEA, 400 params, batch %d, c64)" % args.batch, "value": args.steps * batch / t,
         "unit": "grads/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
@@ -304,7 +308,7 @@ def bench_adjoint(args):
         "roofline": {"bound": "hbm", "kernel": "k_batch_sweep<reverse>", "achieved": gbs,
                      "peak": float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)), "unit": "GB/s",
                      "frac": gbs / float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if gbs else None},
-        "kernels": prof}), flush=True)
+        "kernels": prof})
 
 
 def serving_cpu_baseline(stream, served, budget_s=15.0):
@@ -345,13 +349,13 @@ def bench_serving(args):
     warm = serving_stream(rate=200.0, duration=0.2, seed=99)
     srv = Server(sv.SV_C64, budget_bytes=150e9)
     srv.run(warm)
-    stats, reqs = srv.run(stream, time_limit=args.duration + 30.0)
+    stats, reqs = srv.run(stream, time_limit=args.duration + args.drain)
     seq_stream = [r for r in stream if r[0] < args.seq_duration]
     seq, _ = run_sequential(seq_stream, sv.SV_C64, time_limit=args.seq_duration + 30.0)
     sweep = []
     for rate in [float(x) for x in args.sweep_rates.split(",") if x.strip()]:
         st = serving_stream(rate=rate, duration=args.sweep_duration, seed=1)
-        s_stats, _ = Server(sv.SV_C64, budget_bytes=150e9).run(st, time_limit=args.sweep_duration + 60.0)
+        s_stats, _ = Server(sv.SV_C64, budget_bytes=150e9).run(st, time_limit=args.sweep_duration + args.drain)
         d = s_stats.as_dict()
         sweep.append({"rate": rate, **{k: d[k] for k in ("offered", "completed", "rejected", "unfinished",
                                                            "req_per_s", "p50_ms", "p99_ms")}})
@@ -362,8 +366,8 @@ def bench_serving(args):
                                         "budget_gb": 150},
         "served": stats.as_dict(), "sequential": seq.as_dict(), "rate_sweep": sweep}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = serving_cpu_baseline(stream, reqs)
-    print(json.dumps(line), flush=True)
+        line["cpu_baseline"] = serving_cpu_baseline(stream, reqs, budget_s=getattr(args, "serving_cpu_s", 15.0))
+    return line
 
 
 def bench_precision(args):
@@ -573,6 +577,86 @@ def bench_checkpoint(args):
         "policies": rows}), flush=True)
 
 
+# ------------------------------------------------------------------ figures beside the headline
+
+def bench_c128_30q(args):
+    """The same 30-qubit layered circuit on a complex128 state (16 GiB): per
+    pass time against the FP64 pipe and HBM, whole-step time."""
+    import torch
+    import paper_2608_09733_gb300 as sv
+    from workloads import fused_layered_u3_cz
+    n = args.n
+    glist = fused_layered_u3_cz(n, args.layers, seed=0)
+    gates = sv.Gates(glist)
+    _, npasses, _ = sv.sv_plan_info(n, sv.SV_C128, gates, fuse_max_k=args.fuse)
+    st = torch.empty(2 ** n, dtype=torch.complex128, device="cuda")
+    z = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+
+    def step():
+        sv.sv_init_basis(st, 0)
+        sv.sv_apply_circuit(st, gates, fuse_max_k=args.fuse)
+        sv.sv_expect_z_all(st, out=z)
+    step()
+    torch.cuda.synchronize()
+    sv.sv_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 2
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = sv.sv_profile_read(reset=True)
+    sv.sv_profile_enable(False)
+    ms = e0.elapsed_time(e1) / steps
+    sw = prof.get("sweep", {"launches": 0, "total_ms": float("nan"), "bytes": 0.0})
+    per_pass = sw["total_ms"] / max(1, sw["launches"])
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    # FP64 work of the gates: 14 real flops per amplitude per U3 (a dense
+    # 2x2 complex product), none for a CZ
+    flops = sum(14.0 for g in glist if g.name == "u3") * (2 ** n)
+    fp64 = flops * steps / (sw["total_ms"] / 1e3) / 1e12 if sw["launches"] else None
+    del st
+    torch.cuda.empty_cache()
+    return {"metric": "30q c128 fused layered circuit", "value": ms, "unit": "ms per step", "dtype": "c128",
+            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers_c128" % (n, args.layers),
+                       "passes_per_step": npasses, "steps": steps},
+            "ms_per_pass": per_pass,
+            "hbm": {"achieved": 2 * (2 ** n) * 16 / (per_pass / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": 2 * (2 ** n) * 16 / (per_pass / 1e3) / 1e9 / hbm, "peak_source": src + " hbm_gbs"},
+            "fp64": {"achieved": fp64, "peak": 1.25, "unit": "TFLOP/s", "frac": fp64 / 1.25 if fp64 else None,
+                     "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"},
+            "gates_per_s": len(glist) / (ms / 1e3)}
+
+
+def run_extras(args):
+    """The metric's other parts, each timed after the headline with its own
+    clock record: adjoint gradients (20q HEA, batch 64), the serving stream
+    (2000 req/s, bounded) with its sub-saturation sweep, and the 30-qubit
+    circuit in complex128."""
+    ex = {}
+    jobs = [("adjoint", bench_adjoint, dict(batch=64, steps=5, warmup=3)),
+            ("serving", bench_serving, dict(rate=2000.0, duration=10.0, seq_duration=5.0, sweep_duration=5.0,
+                                            sweep_rates="25,50,100,200", drain=5.0, serving_cpu_s=5.0)),
+            ("c128", bench_c128_30q, {})]
+    for name, fn, over in jobs:
+        a = argparse.Namespace(**vars(args))
+        for k, v in over.items():
+            setattr(a, k, v)
+        clocks = ClockSampler()
+        clocks.start()
+        t0 = time.perf_counter()
+        try:
+            line = fn(a)
+        except Exception as e:  # reported, never hides the headline
+            line = {"error": repr(e)}
+        line["wall_s"] = time.perf_counter() - t0
+        line["clocks"] = clocks.stop(None)
+        ex[name] = line
+    return ex
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -587,9 +671,17 @@ def main():
         from paper_2608_09733_gb300 import build as _build
         _build.build()
         if rank == 0:
-            {"adjoint": bench_adjoint, "serving": bench_serving, "precision": bench_precision,
-             "latency": bench_latency, "sampling": bench_sampling, "batchlayer": bench_batchlayer,
-             "checkpoint": bench_checkpoint}[args.workload](args)
+            fn = {"adjoint": bench_adjoint, "serving": bench_serving, "precision": bench_precision,
+                  "latency": bench_latency, "sampling": bench_sampling, "batchlayer": bench_batchlayer,
+                  "checkpoint": bench_checkpoint}[args.workload]
+            clocks = ClockSampler()
+            clocks.start()
+            line = fn(args)
+            if line is not None:
+                line["clocks"] = clocks.stop(None)
+                print(json.dumps(line), flush=True)
+            else:
+                clocks.stop(None)
         return
 
     import numpy as np
@@ -702,6 +794,12 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(n, gates, args.cpu_sample_gates or 24, None)
 
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras and n == 30 and args.dtype == "c64":
+        del state
+        torch.cuda.empty_cache()
+        extras = run_extras(args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -728,6 +826,10 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if extras is not None:
+            line["adjoint"] = extras["adjoint"]
+            line["serving"] = extras["serving"]
+            line["c128"] = extras["c128"]
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
