@@ -517,9 +517,10 @@ def bench_batchlayer(args):
             gates += [Gate("ry", [q], slots=[slot]), Gate("rz", [q], slots=[slot + 1])]
             slot += 2
         gates += [Gate("x", [(q + 1) % n], controls=[q]) for q in range(n)]
-    layer = sv.BatchLayer(gates, n, n_data=n, n_weights=slot - n, dtype=sv.SV_C64)
-    x = torch.tensor(np.random.default_rng(0).uniform(0, np.pi, size=(batch, n)), requires_grad=True)
-    target = torch.tensor(np.random.default_rng(1).normal(size=(batch, n)))
+    layer = sv.BatchLayer(gates, n, n_data=n, n_weights=slot - n, dtype=sv.SV_C64).cuda()
+    x = torch.tensor(np.random.default_rng(0).uniform(0, np.pi, size=(batch, n)), device="cuda",
+                     requires_grad=True)
+    target = torch.tensor(np.random.default_rng(1).normal(size=(batch, n)), device="cuda")
 
     def step():
         layer.zero_grad()
@@ -534,11 +535,12 @@ def bench_batchlayer(args):
         step()
     torch.cuda.synchronize()
     t = (time.perf_counter() - t0) / args.steps
-    print(json.dumps({
+    return {
         "metric": "BatchLayer rows/s, forward + backward (16q, 4 layers, batch 256, c64)", "value": batch / t,
         "unit": "rows/s", "n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": "batchlayer_16q_4layers_batch256", "parameters": slot}, "ms_per_step": t * 1e3}),
-        flush=True)
+        "config": {"workload": "batchlayer_16q_4layers_batch256", "parameters": slot,
+                   "tensors": "inputs, weights, targets and gradients on the GPU (device-array entry points)"},
+        "ms_per_step": t * 1e3}
 
 
 def bench_checkpoint(args):

@@ -270,8 +270,11 @@ sv_status sv_emulate_apply(int n_qubits, sv_dtype dtype, const sv_gate* gates, s
  * derivative of Sec. 4.2).  At each checkpoint the reverse pass replaces psi
  * by the stored forward state, which bounds the complex64 uncompute drift.
  *   gates            template; parameterised gates (param_slot[0] >= 0) must
- *                    be RX, RY, RZ, P, RXX, RYY, RZZ or EXC1 (else
- *                    SV_ERR_UNSUPPORTED); every gate has <= 2 targets
+ *                    be RX, RY, RZ, P, RXX, RYY, RZZ, EXC1 or EXC2 (else
+ *                    SV_ERR_UNSUPPORTED); every gate has <= 2 targets except
+ *                    double excitations (EXC2, 4 targets, at most 2
+ *                    controls), which the adjoint runs as a controlled RY
+ *                    between fixed CNOT/X permutations
  *   params           host, batch x n_params doubles, row-major; row b binds
  *                    the slots of state b
  *   terms            H = sum_j coeff_j P_j, 1..4096 terms
@@ -338,6 +341,31 @@ sv_status sv_adjoint_grad_rows(int n_qubits, sv_dtype dtype, const sv_gate* gate
  * The call waits for the result.  1 <= n_qubits <= 30, 1 <= batch <= 65535. */
 sv_status sv_batch_expect_z(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
                             const double* params, int batch, int n_params, double* out_z, void* stream);
+
+/* sv_adjoint_grad / sv_adjoint_grad_rows with every array in device memory:
+ * the step of a training loop whose parameters, upstream gradients and
+ * results stay on the GPU (Sec. 5.4 BatchLayer; Sec. 8.2 batched QML).  The
+ * per-state gate matrices are built on the device from `params` (double
+ * precision, narrowed once), so no parameter value crosses to the host; the
+ * call only enqueues work on `stream` and returns.
+ *   params      device, batch x n_params doubles (values are not checked on
+ *               the host: a non-finite parameter gives non-finite results)
+ *   row_coeffs  device, batch x n_terms doubles (H_b as in
+ *               sv_adjoint_grad_rows, with its tile rule on X-masks), or NULL
+ *               for H = sum_j terms[j].coeff P_j for every state
+ *   out_grad    device, batch x n_params doubles, or NULL: values only (the
+ *               forward pass and H psi, no reverse pass)
+ *   out_value   device, batch doubles
+ * Other arguments and errors as sv_adjoint_grad. */
+sv_status sv_adjoint_grad_device(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                 const double* params, int batch, int n_params, const sv_pauli_term* terms,
+                                 size_t n_terms, const double* row_coeffs, int checkpoint_every, double* out_grad,
+                                 double* out_value, void* stream);
+
+/* sv_batch_expect_z with device arrays (params as sv_adjoint_grad_device;
+ * out_z device, batch x (n_qubits + 1) doubles); only enqueues work. */
+sv_status sv_batch_expect_z_device(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                   const double* params, int batch, int n_params, double* out_z, void* stream);
 
 /* ---- serving: packed small states -------------------------------------------
  * Runs many small independent circuits in ONE kernel launch: request b gets one

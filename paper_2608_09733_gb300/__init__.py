@@ -15,9 +15,11 @@ from .binding import (  # noqa: F401
     load,
     pauli_terms,
     sv_adjoint_grad,
+    sv_adjoint_grad_device,
     sv_adjoint_grad_ex,
     sv_adjoint_grad_rows,
     sv_batch_expect_z,
+    sv_batch_expect_z_device,
     sv_apply_circuit,
     sv_apply_circuit_ex,
     SV_BLOCK_AUTO,

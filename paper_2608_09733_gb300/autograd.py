@@ -1,11 +1,15 @@
-"""torch.autograd.Function around sv_adjoint_grad.
+"""torch.autograd.Function around the adjoint gradient.
 
 Forward returns f_b = <0|U^dag(theta_b) H U(theta_b)|0> for each row of a
-(batch, n_params) parameter tensor; the library computes the gradients in the
-same call (adjoint sweep, no tape), and backward scales them by the upstream
-gradient: d loss / d theta_b = (d loss / d f_b) * grad_b.  This is the
-batched-template, per-parameter-gradient path of the paper's QML layers
-(Sec. 8.2), with the adjoint in place of autograd through every gate.
+(batch, n_params) parameter tensor.  When the parameters need a gradient the
+library computes it in the same call (adjoint sweep, no tape) and backward
+scales it by the upstream gradient: d loss / d theta_b = (d loss / d f_b) *
+grad_b; otherwise only the values are computed (forward pass and H psi, no
+reverse pass).  CUDA parameter tensors go through the device-array entry
+points: parameters, gradients and values stay on the GPU, and no host copy
+sits on the step.  This is the batched-template, per-parameter-gradient path
+of the paper's QML layers (Sec. 8.2), with the adjoint in place of autograd
+through every gate.
 """
 
 from __future__ import annotations
@@ -21,10 +25,18 @@ from . import binding as B
 class AdjointExpectation(torch.autograd.Function):
     @staticmethod
     def forward(ctx, params, n, dtype, gates, terms, checkpoint_every):
-        p = params.detach().to("cpu", torch.float64).numpy()
-        val, grad = B.sv_adjoint_grad(n, dtype, gates, p, terms, checkpoint_every)
-        ctx.save_for_backward(torch.from_numpy(grad).to(params.device, params.dtype))
-        return torch.from_numpy(val).to(params.device, params.dtype)
+        want_grad = ctx.needs_input_grad[0]
+        if params.is_cuda:
+            p = params.detach().to(torch.float64).contiguous()
+            val, grad = B.sv_adjoint_grad_device(n, dtype, gates, p, terms, checkpoint_every=checkpoint_every,
+                                                 values_only=not want_grad)
+        else:
+            p = params.detach().to(torch.float64).numpy()
+            v, g = B.sv_adjoint_grad(n, dtype, gates, p, terms, checkpoint_every)
+            val, grad = torch.from_numpy(v), torch.from_numpy(g)
+        if want_grad:
+            ctx.save_for_backward(grad.to(params.dtype))
+        return val.to(params.dtype)
 
     @staticmethod
     def backward(ctx, gout):
@@ -53,23 +65,32 @@ class _BatchLayerFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, x, w, n, dtype, gates, checkpoint_every):
-        xb = x.detach().to("cpu", torch.float64)
-        wb = w.detach().to("cpu", torch.float64).reshape(1, -1).expand(xb.shape[0], -1)
-        params = torch.cat([xb, wb], dim=1).contiguous().numpy()
-        z = B.sv_batch_expect_z(n, dtype, gates, params)[:, :n]
+        dev = x.device if x.is_cuda else torch.device("cpu")
+        xb = x.detach().to(dev, torch.float64)
+        wb = w.detach().to(dev, torch.float64).reshape(1, -1).expand(xb.shape[0], -1)
+        params = torch.cat([xb, wb], dim=1).contiguous()
+        if params.is_cuda:  # the parameters stay on the device
+            z = B.sv_batch_expect_z_device(n, dtype, gates, params)[:, :n]
+        else:
+            z = torch.from_numpy(B.sv_batch_expect_z(n, dtype, gates, params.numpy())[:, :n])
         ctx.params, ctx.n, ctx.dtype, ctx.gates, ctx.ckpt = params, n, dtype, gates, checkpoint_every
         ctx.n_data = x.shape[1]
         ctx.devices = (x.device, x.dtype, w.device, w.dtype)
-        return torch.from_numpy(z).to(x.device, x.dtype)
+        return z.to(x.device, x.dtype)
 
     @staticmethod
     def backward(ctx, gz):
         n = ctx.n
         terms = B.pauli_terms([_Term("Z", [q], 1.0) for q in range(n)])
-        coeffs = gz.detach().to("cpu", torch.float64).contiguous().numpy()
-        _, grad = B.sv_adjoint_grad_rows(n, ctx.dtype, ctx.gates, ctx.params, terms, coeffs, ctx.ckpt)
         xdev, xdt, wdev, wdt = ctx.devices
-        g = torch.from_numpy(grad)
+        if ctx.params.is_cuda:  # upstream gradient, gradients and the weight sum on the device
+            coeffs = gz.detach().to(ctx.params.device, torch.float64).contiguous()
+            _, g = B.sv_adjoint_grad_device(n, ctx.dtype, ctx.gates, ctx.params, terms, row_coeffs=coeffs,
+                                            checkpoint_every=ctx.ckpt)
+        else:
+            coeffs = gz.detach().to("cpu", torch.float64).contiguous().numpy()
+            _, grad = B.sv_adjoint_grad_rows(n, ctx.dtype, ctx.gates, ctx.params.numpy(), terms, coeffs, ctx.ckpt)
+            g = torch.from_numpy(grad)
         dx = g[:, :ctx.n_data].to(xdev, xdt)
         dw = g[:, ctx.n_data:].sum(dim=0).to(wdev, wdt)
         return dx, dw, None, None, None, None
@@ -81,8 +102,9 @@ class BatchLayer(torch.nn.Module):
     slots n_data .. n_data+n_weights-1 the layer's trainable weights; the
     output is <Z_q> for every qubit of every row, (batch, n).  All rows run
     as one batched state; backward is one batched adjoint pass (no
-    parameter-shift loop).  Parameterised gates must be one-parameter
-    rotations (RX, RY, RZ, P, RXX, RYY, RZZ)."""
+    parameter-shift loop).  With CUDA inputs (and the layer on the GPU) the
+    whole step stays in device memory.  Parameterised gates must be
+    one-parameter rotations (RX, RY, RZ, P, RXX, RYY, RZZ, EXC1, EXC2)."""
 
     def __init__(self, gates, n_qubits: int, n_data: int, n_weights: int, dtype: int = B.SV_C64,
                  checkpoint_every: int = 0, init_scale: float = 0.1, seed: int = 0):

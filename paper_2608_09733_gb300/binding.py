@@ -37,7 +37,7 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
            "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample", "sv_adjoint_grad_rows",
-           "sv_batch_expect_z", "sv_adjoint_grad_ex"]
+           "sv_batch_expect_z", "sv_adjoint_grad_ex", "sv_adjoint_grad_device", "sv_batch_expect_z_device"]
 
 
 class SvError(RuntimeError):
@@ -125,6 +125,9 @@ def load():
             "sv_run_batch_small": ([ci, ci, P(ci), P(P(SvGate)), P(sz), vp, ci, vp], ci),
             "sv_expect_z_all_noalloc": ([vp, ci, ci, vp, vp], ci),
             "sv_profile_read": ([P(SvProfileEntry), ci, P(ci), ci], ci),
+            "sv_adjoint_grad_device": ([ci, ci, P(SvGate), sz, vp, ci, ci, P(SvPauliTerm), sz, vp, ci, vp, vp, vp],
+                                       ci),
+            "sv_batch_expect_z_device": ([ci, ci, P(SvGate), sz, vp, ci, ci, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -523,6 +526,51 @@ def sv_batch_expect_z(n: int, dtype: int, gates, params, stream=None) -> np.ndar
     dp = ctypes.POINTER(ctypes.c_double)
     _check(load().sv_batch_expect_z(n, dtype, g.arr, g.n, pv.ctypes.data_as(dp), batch, npar, out.ctypes.data_as(dp),
                                     st))
+    return out
+
+
+def _dev_ptr(t, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sv_adjoint_grad_device(n: int, dtype: int, gates, params, terms, row_coeffs=None, checkpoint_every: int = 0,
+                           out_grad=None, out_value=None, values_only: bool = False, stream=None):
+    """Device-array adjoint (nothing is copied to the host; asynchronous on
+    `stream`).  params: (batch, n_params) float64 CUDA tensor; row_coeffs:
+    (batch, n_terms) CUDA tensor or None.  Returns (values, gradients) as CUDA
+    tensors; gradients is None when values_only."""
+    import torch
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    p = params if params.dim() == 2 else params.reshape(1, -1)
+    batch, npar = p.shape
+    arr = terms if isinstance(terms, ctypes.Array) else pauli_terms(terms)
+    if out_value is None:
+        out_value = torch.empty(batch, dtype=torch.float64, device=p.device)
+    if out_grad is None and not values_only:
+        out_grad = torch.empty((batch, npar), dtype=torch.float64, device=p.device)
+    rc = _dev_ptr(row_coeffs, "row_coeffs") if row_coeffs is not None else ctypes.c_void_p(0)
+    og = _dev_ptr(out_grad, "out_grad") if not values_only else ctypes.c_void_p(0)
+    st = _stream(stream) if stream is not None else _stream(torch.cuda.current_stream())
+    _check(load().sv_adjoint_grad_device(n, dtype, g.arr, g.n, _dev_ptr(p, "params"), batch, npar, arr, len(arr), rc,
+                                         int(checkpoint_every), og, _dev_ptr(out_value, "out_value"), st))
+    return out_value, (None if values_only else out_grad)
+
+
+def sv_batch_expect_z_device(n: int, dtype: int, gates, params, out=None, stream=None):
+    """(batch, n + 1) CUDA tensor: <Z_q> of U(params_b)|0..0> per qubit, then
+    their sum; params a (batch, n_params) float64 CUDA tensor (asynchronous)."""
+    import torch
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    p = params if params.dim() == 2 else params.reshape(1, -1)
+    batch, npar = p.shape
+    if out is None:
+        out = torch.empty((batch, n + 1), dtype=torch.float64, device=p.device)
+    st = _stream(stream) if stream is not None else _stream(torch.cuda.current_stream())
+    _check(load().sv_batch_expect_z_device(n, dtype, g.arr, g.n, _dev_ptr(p, "params"), batch, npar,
+                                           _dev_ptr(out, "out"), st))
     return out
 
 

@@ -1215,7 +1215,91 @@ cudaError_t launch_grad_finish(const double* gscratch, int batch, int ngrad, int
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- device-side tables
+
+namespace {
+
+// One thread per (parameterised gate, state): the gate's matrix at the
+// state's parameter value, in double precision (sincos), narrowed once, in
+// the layout the host builds (d diagonal entries, or d x d row-major).
+template <typename R>
+__global__ void k_build_tables(const double* __restrict__ params, int npar, int batch,
+                               const TableGate* __restrict__ gates, int ngates, Cx<R>* __restrict__ table) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ngates * batch) return;
+  const int pidx = (int)(i / batch), b = (int)(i % batch);
+  const TableGate tg = gates[pidx];
+  const double th = params[(size_t)b * npar + tg.slot];
+  double s, c;
+  sincos(0.5 * th, &s, &c);
+  Cx<R>* row = table + (size_t)i * kTableStride;
+  auto put = [&](int e, double re, double im) { row[e] = Cx<R>{(R)re, (R)im}; };
+  switch (tg.type) {
+    case SV_GATE_RX: put(0, c, 0); put(1, 0, -s); put(2, 0, -s); put(3, c, 0); break;
+    case SV_GATE_RY: put(0, c, 0); put(1, -s, 0); put(2, s, 0); put(3, c, 0); break;
+    case SV_GATE_RZ: put(0, c, -s); put(1, c, s); break;  // diagonal
+    case SV_GATE_P: {                                      // diagonal
+      double s1, c1;
+      sincos(th, &s1, &c1);
+      put(0, 1, 0);
+      put(1, c1, s1);
+      break;
+    }
+    case SV_GATE_RZZ: put(0, c, -s); put(1, c, s); put(2, c, s); put(3, c, -s); break;  // diagonal
+    case SV_GATE_RXX:
+    case SV_GATE_RYY: {  // cos I - i sin P(x)P; YY has -1 on its outer anti-diagonal corners
+      const double outer = tg.type == SV_GATE_RXX ? 1.0 : -1.0;
+      for (int e = 0; e < 16; e++) put(e, (e % 5 == 0) ? c : 0.0, 0.0);
+      put(0 * 4 + 3, 0, -s * outer);
+      put(3 * 4 + 0, 0, -s * outer);
+      put(1 * 4 + 2, 0, -s);
+      put(2 * 4 + 1, 0, -s);
+      break;
+    }
+    case SV_GATE_EXC1: {  // identity except [[c, -s], [s, c]] on indices (1, 2)
+      for (int e = 0; e < 16; e++) put(e, (e % 5 == 0) ? 1.0 : 0.0, 0.0);
+      put(1 * 4 + 1, c, 0);
+      put(1 * 4 + 2, -s, 0);
+      put(2 * 4 + 1, s, 0);
+      put(2 * 4 + 2, c, 0);
+      break;
+    }
+    default: break;
+  }
+}
+
+// out[b, p] = sum of g[b, pidx] over the parameterised gates pidx bound to
+// slot p (in gate order, so the sums do not depend on scheduling).
+__global__ void k_scatter_grad(const double* __restrict__ g, int batch, int ngrad, const int* __restrict__ slot,
+                               int npar, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double* o = out + (size_t)b * npar;
+  for (int p = 0; p < npar; p++) o[p] = 0.0;
+  for (int k = 0; k < ngrad; k++) o[slot[k]] += g[(size_t)b * ngrad + k];
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_build_tables(const double* params, int npar, int batch, const TableGate* gates, int ngates,
+                                Cx<R>* table, cudaStream_t stream) {
+  const long long n = (long long)ngates * batch;
+  if (n == 0) return cudaSuccess;
+  k_build_tables<R><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(params, npar, batch, gates, ngates, table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_grad(const double* g, int batch, int ngrad, const int* slot, int npar, double* out,
+                                cudaStream_t stream) {
+  if (batch == 0 || npar == 0) return cudaSuccess;
+  k_scatter_grad<<<(batch + 127) / 128, 128, 0, stream>>>(g, batch, ngrad, slot, npar, out);
+  return cudaGetLastError();
+}
+
 #define SV_INST(R)                                                                                                \
+  template cudaError_t launch_build_tables<R>(const double*, int, int, const TableGate*, int, Cx<R>*,              \
+                                              cudaStream_t);                                                      \
   template cudaError_t launch_batch_sweep<R>(Cx<R>*, Cx<R>*, const Cx<R>*, double*, int, const BatchProgram<R>&, \
                                              bool, cudaStream_t);                                                 \
   template cudaError_t launch_batch_init<R>(Cx<R>*, int, int, cudaStream_t);                                      \

@@ -97,4 +97,19 @@ size_t batch_dot_scratch_doubles(int batch);
 // out[b * ngrad + g] = sum over grid_x of gscratch[(b * ngrad + g) * grid_x + c]
 cudaError_t launch_grad_finish(const double* gscratch, int batch, int ngrad, int grid_x, double* out,
                                cudaStream_t stream);
+
+// A parameterised gate of a template, for tables built on the device: its
+// family (one-parameter rotation) and the parameter slot it reads.
+struct TableGate {
+  int32_t type;
+  int32_t slot;
+};
+// table[(g * batch + b) * kTableStride ..] = the matrix of gate g at
+// params[b * npar + gates[g].slot] (device arrays), as the host would build it.
+template <typename R>
+cudaError_t launch_build_tables(const double* params, int npar, int batch, const TableGate* gates, int ngates,
+                                Cx<R>* table, cudaStream_t stream);
+// out[b * npar + p] = sum over k with slot[k] == p of g[b * ngrad + k] (device).
+cudaError_t launch_scatter_grad(const double* g, int batch, int ngrad, const int* slot, int npar, double* out,
+                                cudaStream_t stream);
 }  // namespace sv

@@ -68,7 +68,58 @@ struct AGate {
   int slot = -1;
   int pidx = -1;        // index among the parameterised gates
   std::vector<cplx> gen;
+  sv_gate rec;          // the record its matrix is built from
 };
+
+// The adjoint takes gates of at most two targets.  A double excitation
+// EXC2(theta) on (t0, t1, t2, t3) rotates the pair of basis states t0 t1 set /
+// t2 t3 set (matrix indices 3 and 12) and leaves the rest alone.  The
+// permutation C = X(t0) CNOT(t0 -> t2) CNOT(t2 -> t3) CNOT(t0 -> t1) (the
+// rightmost first) sends that pair to the two states with t1 = 0, t2 = 1,
+// t3 = 0 that differ in t0 (index 3 to t0 = 0, index 12 to t0 = 1) and no
+// other state there, so
+//   EXC2(theta) = C^dag RY(theta)[t0 | t1 = 0, t2 = 1, t3 = 0] C,
+// a controlled one-qubit rotation with generator Y whose gradient term the
+// adjoint already takes (the EXC2's own controls join the rotation's).
+// Appends the lowering of g to `out`; false when the rotation would need more
+// than SV_MAX_CONTROLS controls.
+bool expand_gate(const sv_gate& g, std::vector<sv_gate>& out) {
+  if (g.type != SV_GATE_EXC2) {
+    out.push_back(g);
+    return true;
+  }
+  if (g.n_controls + 3 > SV_MAX_CONTROLS) return false;
+  const int t0 = g.targets[0], t1 = g.targets[1], t2 = g.targets[2], t3 = g.targets[3];
+  auto fixed = [](int type, int target, int control) {
+    sv_gate f;
+    std::memset(&f, 0, sizeof(f));
+    f.type = type;
+    f.n_targets = 1;
+    f.targets[0] = target;
+    if (control >= 0) {
+      f.n_controls = 1;
+      f.controls[0] = control;
+    }
+    f.param_slot[0] = f.param_slot[1] = f.param_slot[2] = -1;
+    return f;
+  };
+  const sv_gate perm[4] = {fixed(SV_GATE_X, t1, t0), fixed(SV_GATE_X, t3, t2), fixed(SV_GATE_X, t2, t0),
+                           fixed(SV_GATE_X, t0, -1)};
+  for (int k = 0; k < 4; k++) out.push_back(perm[k]);
+  sv_gate ry = g;
+  ry.type = SV_GATE_RY;
+  ry.n_targets = 1;
+  ry.targets[0] = t0;
+  ry.n_controls = 3 + g.n_controls;
+  ry.controls[0] = t1;
+  ry.controls[1] = t2;
+  ry.controls[2] = t3;
+  for (int c = 0; c < g.n_controls; c++) ry.controls[3 + c] = g.controls[c];
+  ry.control_zero_mask = 1u | 4u | (g.control_zero_mask << 3);  // t1 = 0, t2 = 1, t3 = 0
+  out.push_back(ry);
+  for (int k = 3; k >= 0; k--) out.push_back(perm[k]);
+  return true;
+}
 
 template <typename R>
 void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, const Sweep& sw, int n, int batch,
@@ -244,26 +295,46 @@ template <typename R>
 // stored: how many of the segment-start states to keep (-1: all of them);
 // the others are recomputed in the reverse pass by applying the gates again
 // from the nearest kept state below (or |0..0>).
+// dev: params, row_coeffs, out_grad, out_value and out_z are device arrays,
+// the gate tables are built on the device and nothing is copied to the host
+// (the call only enqueues work).  values_only: no reverse pass (out_grad
+// unused).
 void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const double* params, int batch, int npar,
                  const sv_pauli_term* terms, size_t nterms, int ckpt, int stored, double* out_grad,
-                 double* out_value, const double* row_coeffs, double* out_z, cudaStream_t stream) {
-  // ---- lower the template
-  std::vector<AGate> ag(ng);
-  int npg = 0;
+                 double* out_value, const double* row_coeffs, double* out_z, cudaStream_t stream, bool dev = false,
+                 bool values_only = false) {
+  // ---- lower the template: gate i becomes ag[start[i]] .. ag[start[i+1]-1]
+  // (one gate, or the nine of a double excitation); segments and checkpoints
+  // count the caller's gates
+  std::vector<sv_gate> eg;
+  std::vector<size_t> start(ng + 1, 0);
+  eg.reserve(ng);
   for (size_t i = 0; i < ng; i++) {
-    const sv_gate& g = gates[i];
+    start[i] = eg.size();
+    if (!expand_gate(gates[i], eg))
+      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) + ": a double excitation in the adjoint takes at most " +
+                                   std::to_string(SV_MAX_CONTROLS - 3) + " controls");
+  }
+  start[ng] = eg.size();
+  std::vector<AGate> ag(eg.size());
+  int npg = 0;
+  for (size_t i = 0; i < eg.size(); i++) {
+    const sv_gate& g = eg[i];
+    ag[i].rec = g;
     bool any_slot = false;
     const int nang = g.type == SV_GATE_U3 ? 3 : g.type == SV_GATE_U2 ? 2 : is_rotation(g.type) ? 1 : 0;
     for (int a = 0; a < nang; a++)
       if (g.param_slot[a] >= 0) any_slot = true;
+    const size_t src = (size_t)(std::upper_bound(start.begin(), start.end(), i) - start.begin()) - 1;
     if (g.n_targets > 2)
-      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) + ": the adjoint path takes gates of <= 2 targets");
+      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(src) + ": the adjoint path takes gates of <= 2 targets "
+                                                               "(double excitations aside)");
     AGate& a = ag[i];
     if (any_slot) {
       if (!is_rotation(g.type) || g.param_slot[0] < 0)
-        fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) +
+        fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(src) +
                                      ": a parameterised gate needs a generator, exp(-i theta G / 2) "
-                                     "(RX, RY, RZ, P, RXX, RYY, RZZ, EXC1)");
+                                     "(RX, RY, RZ, P, RXX, RYY, RZZ, EXC1, EXC2)");
       a.param = true;
       a.slot = g.param_slot[0];
       a.pidx = npg++;
@@ -285,22 +356,27 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
       op.need = op.kind == OPK_DIAG ? 0 : tm;
       op.m.assign(op.kind == OPK_DIAG ? (1 << op.k) : (1 << (2 * op.k)), 0.0);  // sizes the pool use
     } else {
-      a.op = lower_gate(g, nullptr, (int)i);
+      a.op = lower_gate(g, nullptr, (int)src);
       if (a.op.kind == OPK_REAL) a.op.kind = OPK_DENSE;
     }
-    a.op.first_gate = (int)i;
+    a.op.first_gate = (int)src;
   }
 
   // ---- per-state tables of the parameterised gates (double, then narrowed)
   const size_t N = 1ull << n;
   const size_t sbytes = sizeof(Cx<R>) * N * (size_t)batch;
-  std::vector<Cx<R>> table((size_t)std::max(npg, 1) * batch * kTableStride);
-  for (size_t i = 0; i < ng; i++) {
+  std::vector<Cx<R>> table(dev ? 0 : (size_t)std::max(npg, 1) * batch * kTableStride);
+  std::vector<TableGate> tgates;
+  std::vector<int> pslot;
+  for (size_t i = 0; i < ag.size(); i++) {
     if (!ag[i].param) continue;
+    tgates.push_back(TableGate{ag[i].rec.type, ag[i].slot});
+    pslot.push_back(ag[i].slot);
+    if (dev) continue;
     for (int b = 0; b < batch; b++) {
-      std::vector<cplx> U = gate_matrix(gates[i], params + (size_t)b * npar);
+      std::vector<cplx> U = gate_matrix(ag[i].rec, params + (size_t)b * npar);
       Cx<R>* row = &table[((size_t)ag[i].pidx * batch + b) * kTableStride];
-      int d = 1 << gates[i].n_targets;
+      int d = 1 << ag[i].rec.n_targets;
       if (ag[i].op.kind == OPK_DIAG)
         for (int r = 0; r < d; r++) row[r] = {(R)U[r * d + r].real(), (R)U[r * d + r].imag()};
       else
@@ -324,13 +400,31 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   int nkeep = stored < 0 ? nck : std::min(stored, nck);
   for (int i = 0; i < nkeep; i++) slot_of[(int)(((long long)(i + 1) * nck) / nkeep)] = i;  // evenly spaced
   Cx<R>* ck = nkeep ? (Cx<R>*)scratch_buffer(stream, "adj_ckpt", sbytes * nkeep) : nullptr;
-  Cx<R>* dtab = (Cx<R>*)scratch_buffer(stream, "adj_table", table.size() * sizeof(Cx<R>));
+  Cx<R>* dtab = (Cx<R>*)scratch_buffer(stream, "adj_table", sizeof(Cx<R>) * (size_t)std::max(npg, 1) * batch *
+                                                                   kTableStride);
   double* gscr = (double*)scratch_buffer(stream, "adj_gscratch", sizeof(double) * (size_t)batch * std::max(npg, 1) * grid_x);
   double* gout = (double*)scratch_buffer(stream, "adj_gout", sizeof(double) * (size_t)batch * std::max(npg, 1));
   double* dots = (double*)scratch_buffer(stream, "adj_dot", sizeof(double) * batch_dot_scratch_doubles(batch));
   double* vout = (double*)scratch_buffer(stream, "adj_val", sizeof(double) * batch);
-  cuda_check(cudaMemcpyAsync(dtab, table.data(), table.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice, stream),
-             "table upload");
+  int* dslot = nullptr;
+  if (dev) {  // the gate list and slots go up (small); the matrices are built where the parameters are
+    TableGate* dg = (TableGate*)scratch_buffer(stream, "adj_tgates", sizeof(TableGate) * std::max<size_t>(npg, 1));
+    dslot = (int*)scratch_buffer(stream, "adj_pslot", sizeof(int) * std::max<size_t>(npg, 1));
+    if (npg) {
+      Pinned& pin = pinned_buffer(stream, "adj_tgates", sizeof(TableGate) * npg + sizeof(int) * npg);
+      std::memcpy(pin.p, tgates.data(), sizeof(TableGate) * npg);
+      std::memcpy((char*)pin.p + sizeof(TableGate) * npg, pslot.data(), sizeof(int) * npg);
+      cuda_check(cudaMemcpyAsync(dg, pin.p, sizeof(TableGate) * npg, cudaMemcpyHostToDevice, stream), "gate list");
+      cuda_check(cudaMemcpyAsync(dslot, (char*)pin.p + sizeof(TableGate) * npg, sizeof(int) * npg,
+                                 cudaMemcpyHostToDevice, stream),
+                 "slot list");
+      cuda_check(cudaEventRecord(pin.ready, stream), "cudaEventRecord");
+    }
+    cuda_check(launch_build_tables<R>(params, npar, batch, dg, npg, dtab, stream), "gate tables");
+  } else {
+    cuda_check(cudaMemcpyAsync(dtab, table.data(), table.size() * sizeof(Cx<R>), cudaMemcpyHostToDevice, stream),
+               "table upload");
+  }
 
   std::unique_ptr<BatchProgram<R>> prog(new BatchProgram<R>());
   const int pool_cap = BatchProgram<R>::kPool / 2;
@@ -343,7 +437,7 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
       const size_t b = std::min(g1, a + c);
       std::vector<int> order;
       std::vector<LOp> ops;
-      for (size_t i = a; i < b; i++) {
+      for (size_t i = start[a]; i < start[b]; i++) {
         order.push_back((int)i);
         ops.push_back(ag[i].op);
       }
@@ -367,11 +461,12 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   if (out_z) {
     const size_t zn = (size_t)n + 1;
     double* zscr = (double*)scratch_buffer(stream, "adj_zscratch", sizeof(double) * expect_z_all_scratch_doubles(n));
-    double* zdev = (double*)scratch_buffer(stream, "adj_zout", sizeof(double) * zn * batch);
+    double* zdev = dev ? out_z : (double*)scratch_buffer(stream, "adj_zout", sizeof(double) * zn * batch);
     for (int b = 0; b < batch; b++)
       cuda_check(launch_expect_z_all<R>(psi + (size_t)b * N, n, zscr, expect_z_all_scratch_doubles(n),
                                         zdev + (size_t)b * zn, stream),
                  "per-state <Z>");
+    if (dev) return;
     cuda_check(cudaMemcpyAsync(out_z, zdev, sizeof(double) * zn * batch, cudaMemcpyDeviceToHost, stream),
                "<Z> copy");
     cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
@@ -380,11 +475,14 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
 
   // ---- lambda = H psi (tiles that hold whole X-masks); f = Re <psi|lambda>
   {
-    double* rowc = nullptr;
-    if (row_coeffs) {
-      rowc = (double*)scratch_buffer(stream, "adj_rowc", sizeof(double) * nterms * batch);
-      cuda_check(cudaMemcpyAsync(rowc, row_coeffs, sizeof(double) * nterms * batch, cudaMemcpyHostToDevice, stream),
+    const double* rowc = nullptr;
+    if (row_coeffs && dev) {
+      rowc = row_coeffs;
+    } else if (row_coeffs) {
+      double* up = (double*)scratch_buffer(stream, "adj_rowc", sizeof(double) * nterms * batch);
+      cuda_check(cudaMemcpyAsync(up, row_coeffs, sizeof(double) * nterms * batch, cudaMemcpyHostToDevice, stream),
                  "row coefficients upload");
+      rowc = up;
     }
     Prof pr(stream, "pauli_accum", 2.0 * (double)sbytes);
     const cudaError_t e = launch_pauli_tiles<R>(psi, lam, n, batch, terms, (int)nterms, false, rowc, stream);
@@ -395,6 +493,17 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
     pr.done();
     cuda_check(launch_batch_dot<R>(psi, lam, n, batch, dots, vout, stream), "value");
   }
+  if (values_only) {
+    if (dev) {
+      cuda_check(cudaMemcpyAsync(out_value, vout, sizeof(double) * batch, cudaMemcpyDeviceToDevice, stream),
+                 "value copy");
+    } else {
+      cuda_check(cudaMemcpyAsync(out_value, vout, sizeof(double) * batch, cudaMemcpyDeviceToHost, stream),
+                 "value copy");
+      cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    }
+    return;
+  }
 
   // ---- reverse, segment by segment, re-anchoring psi at checkpoints
   int nseg = ng ? (int)((ng + c - 1) / c) : 0;
@@ -402,7 +511,7 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
     size_t g0 = (size_t)seg * c, g1 = std::min(ng, g0 + c);
     std::vector<int> order;
     std::vector<LOp> ops;
-    for (size_t i = g1; i-- > g0;) {
+    for (size_t i = start[g1]; i-- > start[g0];) {
       order.push_back((int)i);
       ops.push_back(ag[i].op);
     }
@@ -432,6 +541,16 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
     }
   }
   if (npg) cuda_check(launch_grad_finish(gscr, batch, npg, grid_x, gout, stream), "gradient reduce");
+  if (dev) {  // slots shared by several gates add up, on the device
+    if (npg) {
+      cuda_check(launch_scatter_grad(gout, batch, npg, dslot, npar, out_grad, stream), "gradient scatter");
+    } else if (npar) {
+      cuda_check(cudaMemsetAsync(out_grad, 0, sizeof(double) * (size_t)batch * npar, stream), "gradient clear");
+    }
+    cuda_check(cudaMemcpyAsync(out_value, vout, sizeof(double) * batch, cudaMemcpyDeviceToDevice, stream),
+               "value copy");
+    return;
+  }
 
   // ---- results to the host; slots shared by several gates add up
   std::vector<double> gh((size_t)batch * std::max(npg, 1), 0.0);
@@ -441,7 +560,7 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   cuda_check(cudaMemcpyAsync(out_value, vout, sizeof(double) * batch, cudaMemcpyDeviceToHost, stream), "value copy");
   cuda_check(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
   std::fill(out_grad, out_grad + (size_t)batch * npar, 0.0);
-  for (size_t i = 0; i < ng; i++) {
+  for (size_t i = 0; i < ag.size(); i++) {
     if (!ag[i].param) continue;
     for (int b = 0; b < batch; b++) out_grad[(size_t)b * npar + ag[i].slot] += gh[(size_t)b * npg + ag[i].pidx];
   }
@@ -479,15 +598,28 @@ void check_terms(int n_qubits, const sv_pauli_term* terms, size_t n_terms) {
 void adjoint_dispatch(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
                       int batch, int n_params, const sv_pauli_term* terms, size_t n_terms, int checkpoint_every,
                       double* out_grad, double* out_value, const double* row_coeffs, double* out_z, void* stream,
-                      int stored = -1) {
+                      int stored = -1, bool dev = false, bool values_only = false) {
   static double dummy_grad;
   double* og = n_params > 0 && out_grad ? out_grad : &dummy_grad;
   if (dtype == SV_C64)
     run_adjoint<float>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
-                       stored, og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
+                       stored, og, out_value, row_coeffs, out_z, (cudaStream_t)stream, dev, values_only);
   else
     run_adjoint<double>(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
-                        stored, og, out_value, row_coeffs, out_z, (cudaStream_t)stream);
+                        stored, og, out_value, row_coeffs, out_z, (cudaStream_t)stream, dev, values_only);
+}
+
+// As check_adjoint_args for device-resident parameters (their values are not
+// read on the host).
+void check_adjoint_args_dev(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* params,
+                            int batch, int n_params, int checkpoint_every) {
+  if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+  if (n_qubits < 1 || n_qubits > 30) fail(SV_ERR_INVALID, "n_qubits must be in 1..30 for the adjoint");
+  if (batch < 1 || batch > 65535) fail(SV_ERR_INVALID, "batch must be in 1..65535");
+  if (n_params < 0) fail(SV_ERR_INVALID, "n_params must be >= 0");
+  if (checkpoint_every < 0) fail(SV_ERR_INVALID, "checkpoint_every must be >= 0");
+  if (n_params > 0) check_device_buffer(params, sizeof(double) * (size_t)batch * n_params, "params");
+  validate_gates(n_qubits, gates, n_gates, (size_t)n_params);
 }
 
 }  // namespace
@@ -555,5 +687,33 @@ extern "C" sv_status sv_adjoint_grad_ex(int n_qubits, sv_dtype dtype, const sv_g
     }
     adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms,
                      opts->checkpoint_every, out_grad, out_value, nullptr, nullptr, stream, stored);
+  });
+}
+
+extern "C" sv_status sv_adjoint_grad_device(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                            const double* params, int batch, int n_params,
+                                            const sv_pauli_term* terms, size_t n_terms, const double* row_coeffs,
+                                            int checkpoint_every, double* out_grad, double* out_value,
+                                            void* stream) {
+  return guarded([&] {
+    check_adjoint_args_dev(n_qubits, dtype, gates, n_gates, params, batch, n_params, checkpoint_every);
+    check_terms(n_qubits, terms, n_terms);
+    if (row_coeffs) check_device_buffer(row_coeffs, sizeof(double) * (size_t)batch * n_terms, "row_coeffs");
+    if (out_grad && n_params > 0) check_device_buffer(out_grad, sizeof(double) * (size_t)batch * n_params, "out_grad");
+    check_device_buffer(out_value, sizeof(double) * (size_t)batch, "out_value");
+    adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, terms, n_terms, checkpoint_every,
+                     out_grad, out_value, row_coeffs, nullptr, stream, -1, true, out_grad == nullptr);
+  });
+}
+
+extern "C" sv_status sv_batch_expect_z_device(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                              const double* params, int batch, int n_params, double* out_z,
+                                              void* stream) {
+  return guarded([&] {
+    check_adjoint_args_dev(n_qubits, dtype, gates, n_gates, params, batch, n_params, 0);
+    check_device_buffer(out_z, sizeof(double) * (size_t)batch * (n_qubits + 1), "out_z");
+    static const sv_pauli_term z0 = {0, 1, 1.0};  // unused: forward only
+    adjoint_dispatch(n_qubits, dtype, gates, n_gates, params, batch, n_params, &z0, 1, 0, nullptr, nullptr, nullptr,
+                     out_z, stream, -1, true);
   });
 }

@@ -150,15 +150,8 @@ void* scratch_buffer(cudaStream_t stream, const char* name, size_t bytes) {
 }
 
 namespace {
-
-// Pinned host staging per (device, stream, name), grow-only; `ready` is
-// recorded after the last copy out of it, so a rewrite waits for that copy.
-struct Pinned {
-  void* p = nullptr;
-  size_t cap = 0;
-  cudaEvent_t ready = nullptr;
-};
 std::map<std::tuple<int, cudaStream_t, std::string>, Pinned> g_pinned;
+}  // namespace
 
 Pinned& pinned_buffer(cudaStream_t stream, const char* name, size_t bytes) {
   int dev = 0;
@@ -180,6 +173,8 @@ Pinned& pinned_buffer(cudaStream_t stream, const char* name, size_t bytes) {
   }
   return pb;
 }
+
+namespace {
 
 // ----------------------------------------------------------- kernel timing
 

@@ -199,6 +199,15 @@ sv_status guarded(F&& f) {
 void check_device_buffer(const void* p, size_t bytes, const char* what);
 void* scratch_buffer(cudaStream_t stream, const char* name, size_t bytes);
 
+// Pinned host staging per (device, stream, name), grow-only; `ready` is
+// recorded after the last copy out of it, so a rewrite waits for that copy.
+struct Pinned {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ready = nullptr;
+};
+Pinned& pinned_buffer(cudaStream_t stream, const char* name, size_t bytes);
+
 // Lowering (gate records -> double-precision matrices), the paper's greedy
 // fusion, and the tile scheduler.  Throw sv::Error on invalid input.
 void validate_gates(int n, const sv_gate* gates, size_t n_gates, size_t n_param_values);

@@ -132,3 +132,23 @@ def test_tile_width_option(svlib):
     # capped at the state size: a 6-qubit state plans with any legal width
     _, small, _ = B.sv_plan_info(6, B.SV_C64, fused_layered_u3_cz(6, 3, seed=2), fuse_max_k=5, tile_qubits=12)
     assert small == 1
+
+
+def test_double_excitation_lowering_identity():
+    """The adjoint runs a double excitation EXC2(theta) on (t0, t1, t2, t3) as
+    C^dag RY(theta)[t0 | t1 = 0, t2 = 1, t3 = 0] C with C = X(t0) CNOT(t0->t2)
+    CNOT(t2->t3) CNOT(t0->t1) (rightmost first).  The oracle confirms the
+    identity on random states, with and without an extra control."""
+    n = 6
+    rng = np.random.default_rng(3)
+    for t, ctrl in (([0, 1, 2, 3], []), ([4, 0, 5, 2], []), ([1, 3, 5, 0], [4]), ([2, 5, 0, 4], [3])):
+        th = float(rng.uniform(0, 2 * np.pi))
+        for cs in ([1] * len(ctrl), [0] * len(ctrl)):
+            init = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+            init /= np.linalg.norm(init)
+            direct = oracle.run(n, [Gate("exc2", t, ctrl, cs, params=[th])], init=init.copy())
+            t0, t1, t2, t3 = t
+            perm = [Gate("x", [t1], [t0]), Gate("x", [t3], [t2]), Gate("x", [t2], [t0]), Gate("x", [t0])]
+            ry = Gate("ry", [t0], [t1, t2, t3] + ctrl, [0, 1, 0] + cs, params=[th])
+            lowered = oracle.run(n, perm + [ry] + perm[::-1], init=init.copy())
+            assert np.abs(direct - lowered).max() < 1e-13
