@@ -382,6 +382,47 @@ sv_status sv_batch_expect_z_device(int n_qubits, sv_dtype dtype, const sv_gate* 
 sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits, const sv_gate* const* gates,
                              const size_t* n_gates, double* out_sum_z, int out_on_device, void* stream);
 
+/* ---- serving sessions: a resident packed kernel -------------------------------
+ * A session keeps one kernel resident on `n_ctas` SMs (0: a sixteenth of the
+ * SMs, at least 2) whose CTAs take small requests from a work queue while it
+ * runs: the host publishes a request (its programs uploaded, its queue entry
+ * written to pinned host memory mapped into the device), a free CTA claims it,
+ * runs its circuit from |0..0> on a state held in shared memory (as
+ * sv_run_batch_small does) and writes sum_q <Z_q> and a done word back to
+ * mapped memory.  A request costs no kernel launch (Sec. 9.3: small states
+ * were launch-bound on the NPU).  Requests up to SV_SESSION_MAX_QUBITS qubits
+ * (complex64; 12 for complex128), gates without parameter slots.
+ * Every device-side wait is bounded: a CTA that finds no published request
+ * for wait_limit_s seconds records SV_ERR_TIMEOUT and ends; the next submit
+ * relaunches the kernel, and sv_small_session_stop reports the timeout.
+ * A device-wide synchronization (cudaDeviceSynchronize, cudaFree,
+ * cudaFreeHost ...) waits for the resident kernel, that is until its CTAs
+ * have found no work for wait_limit_s: keep the limit short (tens of
+ * milliseconds) where such calls can happen while a session is live.
+ * While a session is live, apply calls on the same device use the pass kernel
+ * of 4 CTAs per SM (the TMA pass needs whole SMs).  A session belongs to the
+ * device current at start; its calls are thread-safe. */
+#define SV_SESSION_MAX_QUBITS 13
+typedef struct sv_small_session sv_small_session;
+/* capacity: requests in flight at most (1..2^20); arena_programs: pass
+ * programs held for them (1..65536, about 32 KB each on the device). */
+sv_status sv_small_session_start(sv_dtype dtype, int capacity, int arena_programs, double wait_limit_s, int n_ctas,
+                                 sv_small_session** out);
+/* Plans and publishes n_requests requests (host arrays as sv_run_batch_small);
+ * tickets[b] identifies request b.  SV_ERR_OOM when the session holds
+ * `capacity` requests in flight or its program arena is full: poll, then
+ * submit again. */
+sv_status sv_small_session_submit(sv_small_session* s, int n_requests, const int* n_qubits,
+                                  const sv_gate* const* gates, const size_t* n_gates, int64_t* tickets);
+/* *done = 1 and *result = sum_q <Z_q> once the ticket is done, else *done = 0
+ * (never waits).  A ticket older than `capacity` later ones is SV_ERR_INVALID. */
+sv_status sv_small_session_poll(sv_small_session* s, int64_t ticket, double* result, int* done);
+/* Asks the kernel to end once no published request is left, waits for it and
+ * frees the session.  SV_ERR_TIMEOUT if any of its waits ran out (the session
+ * sat idle past its limit, or was never given work); results of done
+ * tickets are valid either way. */
+sv_status sv_small_session_stop(sv_small_session* s);
+
 /* End-to-end call on HOST buffers: copies `state_in` (host, 2^n amplitudes of
  * dtype; NULL means |0..0>) to a library-owned device buffer, applies the
  * circuit as sv_apply_circuit does, evaluates <Z_q> for all qubits into

@@ -37,7 +37,8 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_plan_info", "sv_run_host", "sv_alloc", "sv_free", "sv_state_ptr", "sv_set_state", "sv_get_state",
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
            "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample", "sv_adjoint_grad_rows",
-           "sv_batch_expect_z", "sv_adjoint_grad_ex", "sv_adjoint_grad_device", "sv_batch_expect_z_device"]
+           "sv_batch_expect_z", "sv_adjoint_grad_ex", "sv_adjoint_grad_device", "sv_batch_expect_z_device",
+           "sv_small_session_start", "sv_small_session_submit", "sv_small_session_poll", "sv_small_session_stop"]
 
 
 class SvError(RuntimeError):
@@ -128,6 +129,10 @@ def load():
             "sv_adjoint_grad_device": ([ci, ci, P(SvGate), sz, vp, ci, ci, P(SvPauliTerm), sz, vp, ci, vp, vp, vp],
                                        ci),
             "sv_batch_expect_z_device": ([ci, ci, P(SvGate), sz, vp, ci, ci, vp, vp], ci),
+            "sv_small_session_start": ([ci, ci, ci, cd, ci, P(vp)], ci),
+            "sv_small_session_submit": ([vp, ci, P(ci), P(P(SvGate)), P(sz), P(ctypes.c_int64)], ci),
+            "sv_small_session_poll": ([vp, ctypes.c_int64, P(cd), P(ci)], ci),
+            "sv_small_session_stop": ([vp], ci),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -572,6 +577,45 @@ def sv_batch_expect_z_device(n: int, dtype: int, gates, params, out=None, stream
     _check(load().sv_batch_expect_z_device(n, dtype, g.arr, g.n, _dev_ptr(p, "params"), batch, npar,
                                            _dev_ptr(out, "out"), st))
     return out
+
+
+SV_SESSION_MAX_QUBITS = 13
+
+
+class SmallSession:
+    """A resident packed kernel fed from a work queue (sv_small_session_*):
+    submit small requests (n <= 13 complex64, 12 complex128), poll tickets,
+    stop.  ``stop`` raises SvError(SV_ERR_TIMEOUT) when a device-side wait of
+    the session ran out (it sat idle past ``wait_limit_s``)."""
+
+    def __init__(self, dtype: int = SV_C64, capacity: int = 16384, arena_programs: int = 8192,
+                 wait_limit_s: float = 0.05, n_ctas: int = 0):
+        self.h = ctypes.c_void_p()
+        self.dtype = dtype
+        _check(load().sv_small_session_start(dtype, capacity, arena_programs, float(wait_limit_s), n_ctas,
+                                             ctypes.byref(self.h)))
+
+    def submit(self, n_qubits, gate_sets):
+        """Plans and publishes the requests; returns their tickets."""
+        nreq = len(gate_sets)
+        gs = [g if isinstance(g, (Gates, GateArray)) else Gates(g) for g in gate_sets]
+        nq = (ctypes.c_int * nreq)(*[int(v) for v in n_qubits])
+        ptrs = (ctypes.POINTER(SvGate) * nreq)(*[g.arr for g in gs])
+        ngs = (ctypes.c_size_t * nreq)(*[g.n for g in gs])
+        tk = (ctypes.c_int64 * nreq)()
+        _check(load().sv_small_session_submit(self.h, nreq, nq, ptrs, ngs, tk))
+        return [int(t) for t in tk]
+
+    def poll(self, ticket: int):
+        """(done, sum_q <Z_q>) of a ticket; never waits."""
+        r, d = ctypes.c_double(), ctypes.c_int()
+        _check(load().sv_small_session_poll(self.h, int(ticket), ctypes.byref(r), ctypes.byref(d)))
+        return bool(d.value), float(r.value)
+
+    def stop(self):
+        if self.h:
+            h, self.h = self.h, ctypes.c_void_p()
+            _check(load().sv_small_session_stop(h))
 
 
 def sv_run_batch_small(n_qubits, gate_sets, dtype: int = SV_C64, out=None, stream=None):

@@ -21,8 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsv.so")
 
-SOURCES = ["sv_plan.cpp", "sv_program.cpp", "sv_api.cpp", "sv_adjoint_host.cpp", "sv_sweep.cu", "sv_reduce.cu", "sv_adjoint.cu",
-           "sv_batch.cu", "sv_noalloc.cu", "sv_sample.cu"]
+SOURCES = ["sv_plan.cpp", "sv_program.cpp", "sv_api.cpp", "sv_adjoint_host.cpp", "sv_serve.cpp", "sv_sweep.cu",
+           "sv_reduce.cu", "sv_adjoint.cu", "sv_noalloc.cu", "sv_sample.cu"]
 HEADERS = ["sv_internal.h", "sv_adjoint.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -255,6 +255,35 @@ template <typename R>
 cudaError_t launch_small_batch(const SweepProgram<R>* progs, const int* first_prog, const int* nq, int n_requests,
                                int max_n, double* out, cudaStream_t stream);
 
+// Persistent packed small states (serving sessions, sv_serve.cpp).  The
+// entries, published count, exit flag, results and done words are pinned host
+// memory mapped into the device; head and status are device memory.
+struct SmallEntry {
+  int32_t first_prog, last_prog;  // the request's programs in the session's program arena
+  int32_t n_qubits, slot;         // state size; result slot (results[slot], done[slot])
+};
+struct SmallSessionDev {
+  const SmallEntry* entries;      // ring of `capacity` entries; ticket t uses entries[t % capacity]
+  const long long* tail;          // tickets published so far (written by the host)
+  const int* exit_flag;           // nonzero: end the session once no published ticket is left
+  unsigned long long* head;       // next ticket to claim (device)
+  double* results;                // sum_q <Z_q> per slot
+  long long* done;                // done[slot] = ticket + 1 once results[slot] is written
+  int* status;                    // SV_OK, or SV_ERR_TIMEOUT when a wait ran out (device)
+  long long capacity;
+  uint64_t limit_ns;              // longest wait for a ticket
+};
+template <typename R>
+cudaError_t launch_small_session(const SmallSessionDev& d, const SweepProgram<R>* progs, int max_n, int grid,
+                                 cudaStream_t stream);
+// Live sessions per device.  A session's resident CTAs hold their SMs, so
+// while one is live the pass kernels avoid the TMA kernel (one CTA per SM, a
+// fixed share of tiles each) for the cp.async one, whose many small CTAs fill
+// what the session leaves free.
+void session_opened(int device);
+void session_closed(int device);
+bool session_live(int device);
+
 // Reductions write fixed-order per-block partials into `scratch` and a final
 // kernel folds them into `out` (device doubles).
 template <typename R>

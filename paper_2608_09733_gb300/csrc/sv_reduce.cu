@@ -271,7 +271,13 @@ __global__ void k_finish_terms(const double* __restrict__ partials, int nblocks,
 
 }  // namespace
 
-size_t expect_z_all_scratch_doubles(int n) { return (size_t)red_grid() * (n + 1); }
+// Sized for the largest state whatever n is, so the per-stream scratch never
+// regrows: regrowing frees the old buffer, and cudaFree synchronizes the whole
+// device (it would wait for a resident serving kernel).
+size_t expect_z_all_scratch_doubles(int n) {
+  (void)n;
+  return (size_t)red_grid() * (SV_MAX_QUBITS + 1);
+}
 size_t expect_terms_scratch_doubles(int n, int n_terms) {
   (void)n;
   (void)n_terms;

@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdlib>
 #include <mutex>
@@ -868,9 +869,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -1110,6 +1108,100 @@ __global__ void __launch_bounds__(256) k_small_batch(const SweepProgram<R>* __re
   }
 }
 
+// Persistent packed small states (serving): a session kernel whose CTAs take
+// requests from a work queue the host fills while it runs.  The queue, its
+// published count and the exit flag live in pinned host memory mapped into the
+// device; the programs in device memory.  CTA loop: claim the next ticket
+// (atomicAdd on the device-side head), wait until the host has published it
+// or asked the session to end, run the request's programs on its state in
+// shared memory from |0..0>, write sum_q <Z_q> and then the ticket's done word
+// (system-scope fence between them).  The wait is bounded by `limit_ns` of
+// %globaltimer: when it runs out the CTA records SV_ERR_TIMEOUT in *status
+// and returns (an idle session ends this way too).
+template <typename R>
+__device__ __forceinline__ void run_small_request(const SweepProgram<R>* progs, int first, int last, int n,
+                                                  Cx<R>* s, double* red, double& result) {
+  const int tsz = 1 << n;
+  for (int a = threadIdx.x; a < tsz; a += blockDim.x) s[phys<R>(a)] = Cx<R>{R(a == 0 ? 1 : 0), R(0)};
+  __syncthreads();
+  const Grp gr{threadIdx.x, blockDim.x, 0u};
+  for (int p = first; p < last; p++) {
+    if (progs[p].h.rq == 5) {
+      if constexpr (sizeof(R) == 4) run_phases<R, 5, 5, kOpsAll>(progs[p], progs[p].coef, s, tsz, 0ull, gr);
+    } else {
+      run_phases<R, 5, kRegQ, kOpsAll>(progs[p], progs[p].coef, s, tsz, 0ull, gr);
+    }
+  }
+  double acc = 0.0;
+  for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
+    const Cx<R> x = s[phys<R>(a)];
+    acc += (double)(x.re * x.re + x.im * x.im) * (double)(n - 2 * __popc(a));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    result = t;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_small_session(SmallSessionDev d, const SweepProgram<R>* __restrict__ progs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
+  __shared__ double red[8];
+  __shared__ long long s_ticket;
+  __shared__ int s_stop;
+  __shared__ double s_result;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long t = (long long)atomicAdd(d.head, 1ull);
+      int stop = 0;
+      const uint64_t t0 = global_ns();
+      for (uint32_t it = 0;; it++) {
+        long long pub;
+        asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(pub) : "l"(d.tail) : "memory");
+        if (t < pub) break;
+        int ex;
+        asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(ex) : "l"(d.exit_flag) : "memory");
+        if (ex) {
+          stop = 1;
+          break;
+        }
+        if ((it & 15u) == 15u && global_ns() - t0 > d.limit_ns) {
+          atomicCAS(d.status, 0, (int)SV_ERR_TIMEOUT);
+          stop = 1;
+          break;
+        }
+        __nanosleep(2000);
+      }
+      s_ticket = t;
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const long long t = s_ticket;
+    const SmallEntry* e = d.entries + (t % d.capacity);
+    int first, last, n, slot;
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(first) : "l"(&e->first_prog) : "memory");
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(last) : "l"(&e->last_prog) : "memory");
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(n) : "l"(&e->n_qubits) : "memory");
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(slot) : "l"(&e->slot) : "memory");
+    double result = 0.0;
+    run_small_request<R>(progs, first, last, n, s, red, s_result);
+    if (threadIdx.x == 0) {
+      result = s_result;
+      d.results[slot] = result;
+      __threadfence_system();  // the result is visible before the done word (also a release store)
+      asm volatile("st.release.sys.global.s64 [%0], %1;" ::"l"(d.done + slot), "l"(t + 1) : "memory");
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __global__ void k_init_basis(Cx<R>* __restrict__ state, uint64_t N, uint64_t index) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -1274,12 +1366,25 @@ static cudaError_t launch_sweep_tma_k(Cx<R>* state, const SweepProgram<R>& prog,
 
 // Whether the TMA pass runs this program: complex64 states of at least 2^9
 // tiles whose tile groups are 128 threads (12-qubit tiles with five register
-// qubits), unless SV_SWEEP_TMA=0 in the environment selects the cp.async
-// kernel.  (complex128 passes are bound by the FP64 pipe, and at the 128
+// qubits), unless a serving session is live on the device or SV_SWEEP_TMA=0
+// in the environment selects the cp.async kernel.  (complex128 passes are bound by the FP64 pipe, and at the 128
 // registers of four 128-thread groups per SM their register phases spill.)
+static std::atomic<int> g_live_sessions[64];
+
+void session_opened(int device) {
+  if (device >= 0 && device < 64) g_live_sessions[device]++;
+}
+void session_closed(int device) {
+  if (device >= 0 && device < 64) g_live_sessions[device]--;
+}
+bool session_live(int device) { return device >= 0 && device < 64 && g_live_sessions[device].load() > 0; }
+
 static bool tma_enabled() {
   const char* e = std::getenv("SV_SWEEP_TMA");
-  return !(e && e[0] == '0');
+  if (e && e[0] == '0') return false;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return !session_live(dev);
 }
 
 template <typename R, int RQ>
@@ -1379,6 +1484,27 @@ cudaError_t launch_small_batch(const SweepProgram<R>* progs, const int* first_pr
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_small_session(const SmallSessionDev& d, const SweepProgram<R>* progs, int max_n, int grid,
+                                 cudaStream_t stream) {
+  const int smem = (int)sizeof(Cx<R>) << max_n;
+  static int configured_bytes[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (smem > 48 * 1024 && smem > configured_bytes[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_small_session<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes[dev] = smem;
+  }
+  k_small_session<R><<<grid, 256, smem, stream>>>(d, progs);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_small_session<float>(const SmallSessionDev&, const SweepProgram<float>*, int, int,
+                                                 cudaStream_t);
+template cudaError_t launch_small_session<double>(const SmallSessionDev&, const SweepProgram<double>*, int, int,
+                                                  cudaStream_t);
 template cudaError_t launch_small_batch<float>(const SweepProgram<float>*, const int*, const int*, int, int, double*,
                                                cudaStream_t);
 template cudaError_t launch_small_batch<double>(const SweepProgram<double>*, const int*, const int*, int, int, double*,

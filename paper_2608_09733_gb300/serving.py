@@ -4,19 +4,28 @@ Requests (arrival time, n qubits, depth, seed) each ask for sum_q <Z_q> of a
 layered U3 + CNOT-ladder circuit.  The loop admits them as they arrive and
 keeps many on the device at once:
 
-* small requests (n <= SV_SMALL_MAX_QUBITS) are packed into one launch of
-  ``sv_run_batch_small``: one CTA per request, the whole state in shared
-  memory, so they never touch HBM and cost one launch per batch;
-* large requests run on a pool of worker threads, each with its own CUDA
-  stream and device state buffer: ``sv_init_basis`` + ``sv_apply_circuit`` +
-  ``sv_expect_z_all``.  A request is admitted only while the states in flight
-  fit the HBM budget (its 2^n amplitudes count against it until its result is
-  read); the worker threads plan in the C library with the GIL released, so
-  their work overlaps on the device.
+* small requests (n <= 13 for complex64, 12 for complex128) go to a serving
+  session (``SmallSession``): one kernel stays resident on a few SMs and its
+  CTAs take requests from a work queue in mapped host memory, each running a
+  whole circuit on a state held in shared memory.  The loop submits the
+  requests that arrived since its last turn in one batch and polls their done
+  words; no request costs a kernel launch.  The session's CTAs end after
+  ``session_wait_s`` without work (the next submit relaunches them), which
+  also bounds how long a device-wide synchronization waits for them.  (``small_mode="packed"`` uses the
+  one-launch-per-batch ``sv_run_batch_small`` instead, for n <= 12.)
+* large requests are admitted against the HBM budget: an admitted request
+  gets its own device state (2^n amplitudes), which counts against the budget
+  until its result has been read, and waits on the device for one of the
+  worker threads.  Each worker has its own CUDA stream and runs
+  ``sv_init_basis`` + ``sv_apply_circuit`` + ``sv_expect_z_all`` on it; the
+  workers plan in the C library with the GIL released, so their work overlaps
+  on the device.  A request that does not fit yet waits in the host queue.
 
-Requests that arrive while the queue already holds ``max_queue`` are
-rejected; a request larger than the whole budget is rejected at admission.
-Latency is completion time minus arrival time on the host clock.
+Rejections, by cause: ``over_budget`` (one state larger than the whole
+budget) and ``queue_full`` (the host queue already holds ``max_queue``
+requests).  Latency is completion time minus arrival time on the host clock.
+``peak_resident_bytes`` is the most device memory the admitted states held at
+once.
 
 The paper has no serving layer; its nearest parts are the batched state
 (Sec. 4.1 BatchSV) and task parallelism across devices (Sec. 7.4).
@@ -47,6 +56,8 @@ class Request:
     result: Optional[float] = None
     path: str = ""
     error: Optional[str] = None
+    state: object = None
+    ticket: int = -1
 
 
 @dataclass
@@ -64,7 +75,8 @@ class ServeStats:
     small: int = 0
     large: int = 0
     small_batches: int = 0
-    peak_inflight_bytes: int = 0
+    peak_resident_bytes: int = 0
+    rejected_by: Dict[str, int] = field(default_factory=dict)
     extra: Dict[str, float] = field(default_factory=dict)
 
     def as_dict(self):
@@ -83,11 +95,11 @@ def request_gates(r: Request):
 
 
 class Server:
-    """See the module docstring.  ``amp_bytes`` is 8 for complex64."""
+    """See the module docstring.  ``amp`` is 8 bytes for complex64."""
 
     def __init__(self, dtype: int = B.SV_C64, budget_bytes: float = 150e9, workers: int = 6,
                  max_small_batch: int = 1024, max_queue: int = 20000, fuse_max_k: int = 5,
-                 small_max_n: int = 12):
+                 small_max_n: Optional[int] = None, small_mode: str = "session", session_wait_s: float = 0.05):
         import torch
         self.torch = torch
         self.dtype = dtype
@@ -98,16 +110,25 @@ class Server:
         self.max_small_batch = max_small_batch
         self.max_queue = max_queue
         self.fuse = fuse_max_k
-        self.small_max_n = min(small_max_n, 12)
+        self.small_mode = small_mode
+        cap = (B.SV_SESSION_MAX_QUBITS if dtype == B.SV_C64 else 12) if small_mode == "session" else 12
+        self.small_max_n = cap if small_max_n is None else min(small_max_n, cap)
+        self.session_wait_s = session_wait_s
         self._lock = threading.Condition()
-        self._inflight = 0
+        self._resident = 0
         self._peak = 0
 
     # ------------------------------------------------------------ large path
+    def _release(self, r: Request):
+        need = (1 << r.n) * self.amp
+        r.state = None
+        with self._lock:
+            self._resident -= need
+            self._lock.notify_all()
+
     def _worker(self, q: "queue.Queue", t0: float, stop: threading.Event):
         torch = self.torch
         stream = torch.cuda.Stream()
-        bufs: Dict[int, "torch.Tensor"] = {}
         zout = torch.zeros(64, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
             while not stop.is_set():
@@ -117,17 +138,8 @@ class Server:
                     continue
                 if r is None:
                     break
-                need = (1 << r.n) * self.amp
-                with self._lock:
-                    while self._inflight + need > self.budget and not stop.is_set():
-                        self._lock.wait(0.005)
-                    self._inflight += need
-                    self._peak = max(self._peak, self._inflight)
                 try:
-                    st = bufs.get(r.n)
-                    if st is None:
-                        st = torch.empty(1 << r.n, dtype=self.tdt, device="cuda")
-                        bufs[r.n] = st
+                    st = r.state
                     g = request_gates(r)
                     B.sv_init_basis(st, 0, stream=stream)
                     B.sv_apply_circuit(st, g, fuse_max_k=self.fuse, stream=stream)
@@ -144,9 +156,7 @@ class Server:
                     r.path = "failed"
                     r.done = time.perf_counter() - t0
                 finally:
-                    with self._lock:
-                        self._inflight -= need
-                        self._lock.notify_all()
+                    self._release(r)
 
     # ------------------------------------------------------------ loop
     def run(self, stream, time_limit: Optional[float] = None, realtime: bool = True) -> (ServeStats, List[Request]):
@@ -160,19 +170,40 @@ class Server:
         torch = self.torch
         reqs = [Request(i, float(a) if realtime else 0.0, int(n), int(d), int(s))
                 for i, (a, n, d, s) in enumerate(stream)]
-        stats = ServeStats(offered=len(reqs))
-        small_q: collections.deque = collections.deque()
-        large_q: "queue.Queue" = queue.Queue()
+        stats = ServeStats(offered=len(reqs), rejected_by={"over_budget": 0, "queue_full": 0})
+        host_q: collections.deque = collections.deque()  # large requests waiting for budget
+        small_new: List[Request] = []                     # small requests not yet submitted
+        small_live: List[Request] = []                    # submitted, not done
+        work_q: "queue.Queue" = queue.Queue()
         stop = threading.Event()
+        session = None
+        if self.small_mode == "session":
+            session = B.SmallSession(self.dtype, wait_limit_s=self.session_wait_s)
         t0 = time.perf_counter()
-        threads = [threading.Thread(target=self._worker, args=(large_q, t0, stop), daemon=True)
+        threads = [threading.Thread(target=self._worker, args=(work_q, t0, stop), daemon=True)
                    for _ in range(self.workers)]
         for t in threads:
             t.start()
-        small_stream = torch.cuda.Stream()
-        inflight_small = []  # (event, requests, out tensor)
-        admitted_large: List[Request] = []
+        small_stream = torch.cuda.Stream() if session is None else None
+        inflight_small = []  # packed mode: (event, requests, out tensor)
+        admitted: List[Request] = []
         nxt = 0
+
+        def waiting():
+            return len(host_q) + len(small_new)
+
+        def admit(r):  # gives r its device state if the budget has room
+            need = (1 << r.n) * self.amp
+            with self._lock:
+                if self._resident + need > self.budget:
+                    return False
+                self._resident += need
+                self._peak = max(self._peak, self._resident)
+            r.state = torch.empty(1 << r.n, dtype=self.tdt, device="cuda")
+            admitted.append(r)
+            work_q.put(r)
+            return True
+
         try:
             while True:
                 now = time.perf_counter() - t0
@@ -182,60 +213,102 @@ class Server:
                 while nxt < len(reqs) and reqs[nxt].arrival <= now:
                     r = reqs[nxt]
                     nxt += 1
-                    if (1 << r.n) * self.amp > self.budget or len(small_q) + large_q.qsize() >= self.max_queue:
+                    if (1 << r.n) * self.amp > self.budget:
                         r.path = "rejected"
-                        stats.rejected += 1
-                        continue
-                    if r.n <= self.small_max_n:
-                        small_q.append(r)
+                        stats.rejected_by["over_budget"] += 1
+                    elif r.n > self.small_max_n and not host_q and admit(r):
+                        pass
+                    elif waiting() >= self.max_queue:
+                        r.path = "rejected"
+                        stats.rejected_by["queue_full"] += 1
+                    elif r.n <= self.small_max_n:
+                        small_new.append(r)
                     else:
-                        admitted_large.append(r)
-                        large_q.put(r)
-                # completed small batches
-                keep = []
-                for ev, rs, out in inflight_small:
-                    if ev.query():
-                        vals = out.cpu().numpy()
+                        host_q.append(r)
+                # admission of the queued large requests, in arrival order
+                while host_q and admit(host_q[0]):
+                    host_q.popleft()
+                # small requests
+                if session is not None:
+                    if small_new:
+                        batch = small_new[: self.max_small_batch]
+                        try:
+                            tickets = session.submit([r.n for r in batch], [request_gates(r) for r in batch])
+                        except B.SvError as e:
+                            if e.status != 3:  # SV_ERR_OOM: the session is full, try again next turn
+                                raise
+                        else:
+                            for r, t in zip(batch, tickets):
+                                r.ticket = t
+                            small_live.extend(batch)
+                            del small_new[: len(batch)]
+                            stats.small_batches += 1
+                    if small_live:
                         tdone = time.perf_counter() - t0
-                        for r, v in zip(rs, vals):
-                            r.result, r.done, r.path = float(v), tdone, "small"
-                    else:
-                        keep.append((ev, rs, out))
-                inflight_small = keep
-                # launch the next packed batch (at most two in flight)
-                if small_q and len(inflight_small) < 2:
-                    batch = [small_q.popleft() for _ in range(min(len(small_q), self.max_small_batch))]
-                    out = torch.empty(len(batch), dtype=torch.float64, device="cuda")
-                    B.sv_run_batch_small([r.n for r in batch], [request_gates(r) for r in batch], self.dtype,
-                                         out=out, stream=small_stream)
-                    ev = torch.cuda.Event()
-                    ev.record(small_stream)
-                    inflight_small.append((ev, batch, out))
-                    stats.small_batches += 1
-                # large completions are recorded by the workers
-                if nxt == len(reqs) and not small_q and not inflight_small:
-                    while admitted_large and admitted_large[-1].done is not None:
-                        admitted_large.pop()
-                    if all(r.done is not None for r in admitted_large):
+                        keep = []
+                        for r in small_live:
+                            ok, v = session.poll(r.ticket)
+                            if ok:
+                                r.result, r.done, r.path = v, tdone, "small"
+                            else:
+                                keep.append(r)
+                        small_live = keep
+                else:
+                    keep = []
+                    for ev, rs, out in inflight_small:
+                        if ev.query():
+                            vals = out.cpu().numpy()
+                            tdone = time.perf_counter() - t0
+                            for r, v in zip(rs, vals):
+                                r.result, r.done, r.path = float(v), tdone, "small"
+                        else:
+                            keep.append((ev, rs, out))
+                    inflight_small = keep
+                    if small_new and len(inflight_small) < 2:
+                        batch = small_new[: self.max_small_batch]
+                        del small_new[: len(batch)]
+                        out = torch.empty(len(batch), dtype=torch.float64, device="cuda")
+                        B.sv_run_batch_small([r.n for r in batch], [request_gates(r) for r in batch], self.dtype,
+                                             out=out, stream=small_stream)
+                        ev = torch.cuda.Event()
+                        ev.record(small_stream)
+                        inflight_small.append((ev, batch, out))
+                        stats.small_batches += 1
+                # finished?
+                small_busy = small_new or small_live or inflight_small
+                if nxt == len(reqs) and not host_q and not small_busy:
+                    while admitted and admitted[-1].done is not None:
+                        admitted.pop()
+                    if all(r.done is not None for r in admitted):
                         break
                     time.sleep(0.0005)
-                elif not small_q:
+                elif not small_busy:
                     wait = reqs[nxt].arrival - now if nxt < len(reqs) else 0.0005
                     time.sleep(min(0.0005, max(0.0, wait)))
         finally:
             stop.set()
             for _ in threads:
-                large_q.put(None)
+                work_q.put(None)
             for t in threads:
                 t.join(timeout=30)
+            if session is not None:
+                try:
+                    session.stop()
+                except B.SvError as e:
+                    if e.status != 5:  # SV_ERR_TIMEOUT: the session sat idle past its limit; results stand
+                        raise
             torch.cuda.synchronize()
+            for r in reqs:  # states of requests left in the queues
+                if r.state is not None:
+                    self._release(r)
+        stats.rejected = sum(stats.rejected_by.values())
         stats.failed = sum(1 for r in reqs if r.path == "failed")
         done = [r for r in reqs if r.done is not None and r.path != "failed"]
         stats.completed = len(done)
         stats.unfinished = stats.offered - stats.completed - stats.rejected - stats.failed
         stats.small = sum(1 for r in done if r.path == "small")
         stats.large = sum(1 for r in done if r.path == "large")
-        stats.peak_inflight_bytes = int(self._peak)
+        stats.peak_resident_bytes = int(self._peak)
         if done:
             lat = np.array([r.done - r.arrival for r in done]) * 1e3
             last = max(r.done for r in done)
@@ -252,7 +325,6 @@ def run_sequential(stream, dtype: int = B.SV_C64, fuse_max_k: int = 5, time_limi
     """Baseline: one request at a time, one circuit launch sequence after
     another on one stream (no packing, no overlap), same latency definition."""
     import torch
-    amp = 8 if dtype == B.SV_C64 else 16
     tdt = torch.complex64 if dtype == B.SV_C64 else torch.complex128
     reqs = [Request(i, float(a) if realtime else 0.0, int(n), int(d), int(s))
             for i, (a, n, d, s) in enumerate(stream)]
@@ -277,7 +349,6 @@ def run_sequential(stream, dtype: int = B.SV_C64, fuse_max_k: int = 5, time_limi
         r.result = float(zout[r.n].item())
         r.done = time.perf_counter() - t0
         r.path = "sequential"
-    del amp
     done = [r for r in reqs if r.done is not None]
     stats.completed = len(done)
     stats.unfinished = stats.offered - stats.completed

@@ -1,7 +1,9 @@
-"""The serving loop's host logic on the CPU: admission against the HBM budget,
-routing by size, queue-limit and over-budget rejections, and that every
-request is accounted for.  The device calls are replaced by fakes that take
-time in proportion to the state size (no GPU is touched)."""
+"""The serving loop's host logic on the CPU: admission against the HBM budget
+(each admitted large request holds its own state until its result is read),
+routing by size to the small-state session or the packed launch,
+queue-limit and over-budget rejections by cause, and that every request is
+accounted for.  The device calls are replaced by fakes that take time in
+proportion to the state size (no GPU is touched)."""
 import time
 
 import pytest
@@ -55,6 +57,27 @@ def fake_device(monkeypatch):
         out.copy_(torch.tensor([float(n) for n in nq], dtype=out.dtype))  # sum <Z_q> of |0..0> = n
         return out
 
+    class FakeSession:
+        """Tickets finish a little after submission; results as for |0..0>."""
+
+        def __init__(self, dtype=0, capacity=16384, wait_limit_s=5.0, **k):
+            self.t, self.res, self.stopped = [], [], False
+
+        def submit(self, nq, sets):
+            calls["small"] += len(nq)
+            base = len(self.t)
+            now = time.perf_counter()
+            self.t += [now] * len(nq)
+            self.res += [float(n) for n in nq]
+            return list(range(base, base + len(nq)))
+
+        def poll(self, ticket):
+            ok = time.perf_counter() - self.t[ticket] > 0.0003
+            return ok, (self.res[ticket] if ok else 0.0)
+
+        def stop(self):
+            self.stopped = True
+
     def apply(st, gates, *a, **k):
         calls["large"] += 1
         time.sleep(2e-4 * (st.numel() >> 13))
@@ -71,37 +94,56 @@ def fake_device(monkeypatch):
     monkeypatch.setattr(torch, "empty", host_empty)
     monkeypatch.setattr(torch, "zeros", host_zeros)
     monkeypatch.setattr(B, "sv_run_batch_small", small)
+    monkeypatch.setattr(B, "SmallSession", FakeSession)
     monkeypatch.setattr(B, "sv_init_basis", lambda st, i=0, stream=None: None)
     monkeypatch.setattr(B, "sv_apply_circuit", apply)
     monkeypatch.setattr(B, "sv_expect_z_all", expect)
     return calls
 
 
-def test_admission_routing_and_accounting(fake_device):
+@pytest.mark.parametrize("mode", ["session", "packed"])
+def test_admission_routing_and_accounting(fake_device, mode):
     from paper_2608_09733_gb300.serving import Server
     stream = serving_stream(rate=3000.0, duration=0.05, n_lo=8, n_hi=19, d_lo=2, d_hi=6, seed=3)
     budget = 8 * (1 << 18) * 3  # three 18-qubit complex64 states; 19-qubit requests exceed it
-    srv = Server(B.SV_C64, budget_bytes=budget, workers=4, max_small_batch=64)
+    srv = Server(B.SV_C64, budget_bytes=budget, workers=4, max_small_batch=64, small_mode=mode)
     stats, reqs = srv.run(stream, time_limit=30.0)
     assert stats.offered == len(stream)
     assert stats.completed + stats.rejected + stats.failed + stats.unfinished == stats.offered
     assert stats.failed == 0 and stats.unfinished == 0
-    assert 0 < stats.peak_inflight_bytes <= budget
+    assert 0 < stats.peak_resident_bytes <= budget
+    assert srv._resident == 0  # every admitted state was released
+    n19 = sum(1 for r in reqs if 8 * (1 << r.n) > budget)
+    assert stats.rejected_by == {"over_budget": n19, "queue_full": 0} and stats.rejected == n19
+    assert srv.small_max_n == (13 if mode == "session" else 12)
     for r in reqs:
         if 8 * (1 << r.n) > budget:
             assert r.path == "rejected"
-        elif r.path != "rejected":
+        else:
             assert r.path == ("small" if r.n <= srv.small_max_n else "large")
             assert r.result == float(r.n)  # the fake's sum <Z_q> for |0..0>
-            assert r.done >= r.arrival
+            assert r.done >= r.arrival and r.state is None
     assert fake_device["small"] == stats.small and fake_device["large"] == stats.large
     assert stats.small > 0 and stats.large > 0
+
+
+def test_budget_holds_the_resident_states(fake_device):
+    """With a burst of large requests the admitted states fill the budget and
+    no further request is admitted until one is released."""
+    from paper_2608_09733_gb300.serving import Server
+    stream = [(0.0, 16, 2, i) for i in range(40)]
+    budget = 8 * (1 << 16) * 5  # five 16-qubit states at once
+    srv = Server(B.SV_C64, budget_bytes=budget, workers=2)
+    stats, reqs = srv.run(stream, time_limit=30.0)
+    assert stats.completed == 40 and stats.rejected == 0
+    assert stats.peak_resident_bytes == budget  # the budget, not the worker count, bounds residency
+    assert srv._resident == 0
 
 
 def test_queue_limit_rejects(fake_device):
     from paper_2608_09733_gb300.serving import Server
     stream = serving_stream(rate=20000.0, duration=0.02, n_lo=16, n_hi=17, d_lo=2, d_hi=3, seed=4)
-    srv = Server(B.SV_C64, budget_bytes=1e9, workers=1, max_queue=5)
+    srv = Server(B.SV_C64, budget_bytes=8 * (1 << 17) * 2, workers=1, max_queue=5)
     stats, _ = srv.run(stream, time_limit=30.0)
-    assert stats.rejected > 0
+    assert stats.rejected_by["queue_full"] > 0 and stats.rejected_by["over_budget"] == 0
     assert stats.completed + stats.rejected == stats.offered
