@@ -14,15 +14,16 @@ keeps many on the device at once:
   also bounds how long a device-wide synchronization waits for them.  (``small_mode="packed"`` uses the
   one-launch-per-batch ``sv_run_batch_small`` instead, for n <= 12.)
 * large requests are admitted against the HBM budget: an admitted request
-  gets its own device state (2^n amplitudes), which counts against the budget
-  until its result has been read, and waits on the device for one of the
-  worker threads.  Each worker has its own CUDA stream and runs
+  gets its own device state (2^n amplitudes) from a pool of the budget's size
+  allocated when the run starts (``StatePool``); the state counts against the
+  budget until its result has been read, and waits on the device for one of
+  the worker threads.  Each worker has its own CUDA stream and runs
   ``sv_init_basis`` + ``sv_apply_circuit`` + ``sv_expect_z_all`` on it; the
   workers plan in the C library with the GIL released, so their work overlaps
   on the device.  A request that does not fit yet waits in the host queue.
 
-Rejections, by cause: ``over_budget`` (one state larger than the whole
-budget) and ``queue_full`` (the host queue already holds ``max_queue``
+Rejections, by cause: ``over_budget`` (one state larger than the pool's
+largest block) and ``queue_full`` (the host queue already holds ``max_queue``
 requests).  Latency is completion time minus arrival time on the host clock.
 ``peak_resident_bytes`` is the most device memory the admitted states held at
 once.
@@ -57,6 +58,7 @@ class Request:
     path: str = ""
     error: Optional[str] = None
     state: object = None
+    offset: int = -1
     ticket: int = -1
 
 
@@ -85,6 +87,85 @@ class ServeStats:
         return d
 
 
+class StatePool:
+    """Device memory for the admitted states, allocated once when a run starts
+    and carved into power-of-two blocks (a buddy allocator), so admitting and
+    releasing requests never calls the CUDA allocator mid-run: a cudaFree there
+    synchronizes the device, which would wait for the resident session kernel.
+
+    The budget is cut into root blocks (its binary decomposition, in units of
+    ``min_bytes``, roots at most ``max_block``); a request takes the smallest
+    free block that holds it, split in halves on the way down, and a released
+    block merges with its free buddy within its root."""
+
+    def __init__(self, budget_bytes: float, min_bytes: int = 1 << 16, max_block: int = 1 << 30, alloc=None):
+        units = int(budget_bytes) // min_bytes
+        self.min = min_bytes
+        self.roots = []  # (base, size)
+        base = 0
+        size = max_block
+        while units and size >= min_bytes:
+            k = size // min_bytes
+            while units >= k:
+                self.roots.append((base, size))
+                base += size
+                units -= k
+            size //= 2
+        self.capacity = base
+        self.free: Dict[int, set] = collections.defaultdict(set)
+        for b, sz in self.roots:
+            self.free[sz].add(b)
+        self.used = 0
+        self.peak = 0
+        self.buf = alloc(self.capacity) if (alloc is not None and self.capacity) else None
+
+    def _root(self, off):
+        lo, hi = 0, len(self.roots) - 1
+        while lo < hi:
+            mid = (lo + hi + 1) // 2
+            if self.roots[mid][0] <= off:
+                lo = mid
+            else:
+                hi = mid - 1
+        return self.roots[lo]
+
+    def block_size(self, nbytes: int) -> int:
+        sz = self.min
+        while sz < nbytes:
+            sz *= 2
+        return sz
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        """Offset of a free block of at least nbytes, or None."""
+        want = self.block_size(nbytes)
+        sz = want
+        while sz not in self.free or not self.free[sz]:
+            sz *= 2
+            if sz > max((r[1] for r in self.roots), default=0):
+                return None
+        off = min(self.free[sz])
+        self.free[sz].discard(off)
+        while sz > want:  # split, keeping the low half
+            sz //= 2
+            self.free[sz].add(off + sz)
+        self.used += want
+        self.peak = max(self.peak, self.used)
+        return off
+
+    def release(self, off: int, nbytes: int):
+        sz = self.block_size(nbytes)
+        self.used -= sz
+        base, rsz = self._root(off)
+        while sz < rsz:
+            buddy = base + ((off - base) ^ sz)
+            if buddy not in self.free[sz]:
+                break
+            self.free[sz].discard(buddy)
+            off = min(off, buddy)
+            sz *= 2
+        self.free[sz].add(off)
+
+
 def _angles(n, depth, seed):
     from workloads import serving_angles  # input generator (seeded)
     return serving_angles(n, depth, seed)
@@ -98,7 +179,7 @@ class Server:
     """See the module docstring.  ``amp`` is 8 bytes for complex64."""
 
     def __init__(self, dtype: int = B.SV_C64, budget_bytes: float = 150e9, workers: int = 6,
-                 max_small_batch: int = 1024, max_queue: int = 20000, fuse_max_k: int = 5,
+                 max_small_batch: int = 256, max_queue: int = 20000, fuse_max_k: int = 5,
                  small_max_n: Optional[int] = None, small_mode: str = "session", session_wait_s: float = 0.05):
         import torch
         self.torch = torch
@@ -123,6 +204,7 @@ class Server:
         need = (1 << r.n) * self.amp
         r.state = None
         with self._lock:
+            self._pool.release(r.offset, need)
             self._resident -= need
             self._lock.notify_all()
 
@@ -171,6 +253,7 @@ class Server:
         reqs = [Request(i, float(a) if realtime else 0.0, int(n), int(d), int(s))
                 for i, (a, n, d, s) in enumerate(stream)]
         stats = ServeStats(offered=len(reqs), rejected_by={"over_budget": 0, "queue_full": 0})
+        self._pool = StatePool(self.budget, alloc=lambda nb: torch.empty(nb, dtype=torch.uint8, device="cuda"))
         host_q: collections.deque = collections.deque()  # large requests waiting for budget
         small_new: List[Request] = []                     # small requests not yet submitted
         small_live: List[Request] = []                    # submitted, not done
@@ -192,14 +275,16 @@ class Server:
         def waiting():
             return len(host_q) + len(small_new)
 
-        def admit(r):  # gives r its device state if the budget has room
+        def admit(r):  # gives r its device state if the pool has room
             need = (1 << r.n) * self.amp
             with self._lock:
-                if self._resident + need > self.budget:
+                off = self._pool.alloc(need)
+                if off is None:
                     return False
                 self._resident += need
                 self._peak = max(self._peak, self._resident)
-            r.state = torch.empty(1 << r.n, dtype=self.tdt, device="cuda")
+            r.offset = off
+            r.state = self._pool.buf[off:off + need].view(self.tdt)
             admitted.append(r)
             work_q.put(r)
             return True
@@ -213,7 +298,8 @@ class Server:
                 while nxt < len(reqs) and reqs[nxt].arrival <= now:
                     r = reqs[nxt]
                     nxt += 1
-                    if (1 << r.n) * self.amp > self.budget:
+                    if self._pool.block_size((1 << r.n) * self.amp) > max((z for _, z in self._pool.roots),
+                                                                          default=0):
                         r.path = "rejected"
                         stats.rejected_by["over_budget"] += 1
                     elif r.n > self.small_max_n and not host_q and admit(r):
@@ -301,6 +387,7 @@ class Server:
             for r in reqs:  # states of requests left in the queues
                 if r.state is not None:
                     self._release(r)
+            self._pool.buf = None
         stats.rejected = sum(stats.rejected_by.values())
         stats.failed = sum(1 for r in reqs if r.path == "failed")
         done = [r for r in reqs if r.done is not None and r.path != "failed"]

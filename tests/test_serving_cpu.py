@@ -147,3 +147,38 @@ def test_queue_limit_rejects(fake_device):
     stats, _ = srv.run(stream, time_limit=30.0)
     assert stats.rejected_by["queue_full"] > 0 and stats.rejected_by["over_budget"] == 0
     assert stats.completed + stats.rejected == stats.offered
+
+
+def test_state_pool_buddy_allocator():
+    """Blocks never overlap, stay inside the pool, merge back to the roots
+    when everything is released, and the budget's binary decomposition is
+    what the pool holds."""
+    import random
+    from paper_2608_09733_gb300.serving import StatePool
+    pool = StatePool(5 * (1 << 20) + 3 * (1 << 16), min_bytes=1 << 16, max_block=1 << 21)
+    assert pool.capacity == 5 * (1 << 20) + 3 * (1 << 16)
+    assert all(sz <= (1 << 21) for _, sz in pool.roots)
+    rng = random.Random(7)
+    live = {}
+    for step in range(3000):
+        if live and (rng.random() < 0.45 or len(live) > 40):
+            off = rng.choice(list(live))
+            pool.release(off, live.pop(off))
+        else:
+            nb = rng.choice([1 << 16, 1 << 17, 3 << 16, 1 << 19, 1 << 20, 1 << 21, 1 << 22])
+            off = pool.alloc(nb)
+            if off is None:
+                continue
+            sz = pool.block_size(nb)
+            assert off % sz == 0 or any(b <= off < b + z and (off - b) % sz == 0 for b, z in pool.roots)
+            assert 0 <= off and off + sz <= pool.capacity
+            for o, n2 in live.items():
+                s2 = pool.block_size(n2)
+                assert off + sz <= o or o + s2 <= off, "overlap"
+            live[off] = nb
+        assert pool.used == sum(pool.block_size(v) for v in live.values()) <= pool.capacity
+    for off, nb in list(live.items()):
+        pool.release(off, nb)
+    assert pool.used == 0
+    assert sorted((b, z) for z, offs in pool.free.items() for b in offs) == sorted(pool.roots)
+    assert pool.alloc(1 << 22) is None  # larger than the largest root
