@@ -474,6 +474,40 @@ sv_status sv_profile_read(sv_profile_entry* out, int max_entries, int* n_out, in
  * device synchronize).  Later calls allocate them again. */
 sv_status sv_release_scratch(void);
 
+/* ---- pass kernels compiled at run time -------------------------------------
+ * A pass over a large complex64 state (the tiled gate application of Sec. 5.3
+ * with the gates of one pass applied per tile) normally runs a kernel that
+ * interprets the pass program.  The library can instead write each program
+ * out as straight-line CUDA (every op's kind, register slots, controls and
+ * coefficient offsets as constants), compile it with NVRTC for the current
+ * device and launch that kernel in its place: same tile movement, same
+ * arithmetic in the same order (bit-identical results), fewer instructions.
+ * Compilation runs on host threads (about a second per distinct program) and
+ * its kernels are cached for the life of the process, per device and program.
+ * Only circuits the library caches (sv_apply_circuit and friends with at most
+ * 512 passes) are compiled; on states with fewer than 2^21 amplitudes, for
+ * complex128 states and where NVRTC is missing, the interpreting kernels run.
+ *
+ * mode: 0 never compile; 1 (default) compile a circuit's programs on its second
+ * run; 2 on its first; -1 take the SV_JIT environment variable (0, 1, 2).
+ * Other values are SV_ERR_INVALID. */
+sv_status sv_jit_set_mode(int mode);
+/* Current mode, whether NVRTC was found (available), kernels compiled and
+ * failed so far, launches of compiled kernels, host seconds spent compiling;
+ * message (host, message_cap bytes, NUL-terminated) gets why NVRTC is missing,
+ * else the last compile error (empty if none).  Any pointer may be NULL. */
+sv_status sv_jit_info(int* mode, int* available, long long* compiled, long long* failed, long long* launches,
+                      double* compile_seconds, char* message, size_t message_cap);
+/* Plans a circuit as sv_apply_circuit_ex would and generates the kernel source
+ * of every pass that would run compiled (*n_sources); with compile != 0 also
+ * compiles each for sm_<arch>a (arch e.g. 103) and counts successes in
+ * *n_compiled.  Needs no device.  text (host, text_cap bytes) receives the
+ * first compile error, else the first source.  SV_ERR_UNSUPPORTED if compile
+ * is asked for and NVRTC is missing. */
+sv_status sv_jit_check(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
+                       size_t n_param_values, const sv_exec_opts* opts, int compile, int arch, int* n_sources,
+                       int* n_compiled, char* text, size_t text_cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,9 @@ from .binding import (  # noqa: F401
     sv_profile_enable,
     sv_profile_read,
     sv_release_scratch,
+    sv_jit_set_mode,
+    sv_jit_info,
+    sv_jit_check,
     sv_run_host,
     sv_run_batch_small,
     sv_sample,

@@ -38,7 +38,8 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_release_scratch", "sv_profile_enable", "sv_profile_read", "sv_adjoint_grad", "sv_run_batch_small",
            "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample", "sv_adjoint_grad_rows",
            "sv_batch_expect_z", "sv_adjoint_grad_ex", "sv_adjoint_grad_device", "sv_batch_expect_z_device",
-           "sv_small_session_start", "sv_small_session_submit", "sv_small_session_poll", "sv_small_session_stop"]
+           "sv_small_session_start", "sv_small_session_submit", "sv_small_session_poll", "sv_small_session_stop",
+           "sv_jit_set_mode", "sv_jit_info", "sv_jit_check"]
 
 
 class SvError(RuntimeError):
@@ -133,6 +134,11 @@ def load():
             "sv_small_session_submit": ([vp, ci, P(ci), P(P(SvGate)), P(sz), P(ctypes.c_int64)], ci),
             "sv_small_session_poll": ([vp, ctypes.c_int64, P(cd), P(ci)], ci),
             "sv_small_session_stop": ([vp], ci),
+            "sv_jit_set_mode": ([ci], ci),
+            "sv_jit_info": ([P(ci), P(ci), P(ctypes.c_longlong), P(ctypes.c_longlong), P(ctypes.c_longlong), P(cd),
+                             ctypes.c_char_p, sz], ci),
+            "sv_jit_check": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), ci, ci, P(ci), P(ci), ctypes.c_char_p,
+                              sz], ci),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -438,6 +444,41 @@ class SvState:
 
 def sv_release_scratch():
     _check(load().sv_release_scratch())
+
+
+def sv_jit_set_mode(mode: int):
+    """0: never compile pass programs; 1 (default): compile a cached circuit's
+    programs on its second run; 2: on its first; -1: the SV_JIT environment
+    variable."""
+    _check(load().sv_jit_set_mode(int(mode)))
+
+
+def sv_jit_info() -> dict:
+    """Mode, NVRTC availability, kernels compiled / failed, launches of
+    compiled kernels, host seconds spent compiling and the last message."""
+    mode, av = ctypes.c_int(), ctypes.c_int()
+    comp, fail, launches = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    secs = ctypes.c_double()
+    msg = ctypes.create_string_buffer(4096)
+    _check(load().sv_jit_info(ctypes.byref(mode), ctypes.byref(av), ctypes.byref(comp), ctypes.byref(fail),
+                              ctypes.byref(launches), ctypes.byref(secs), msg, 4096))
+    return {"mode": mode.value, "available": bool(av.value), "compiled": comp.value, "failed": fail.value,
+            "launches": launches.value, "compile_seconds": secs.value, "message": msg.value.decode(errors="replace")}
+
+
+def sv_jit_check(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, compile: bool = True,
+                 arch: int = 103, block_mode: int = 0, ops_per_pass: int = 0, tile_qubits: int = 0):
+    """(sources, compiled, text): the passes of a circuit that would run as
+    compiled kernels, how many compiled for sm_<arch>a (no device needed),
+    and the first compile error or else the first source."""
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    pp, npv, _keep = _params(param_values)
+    o = _opts(fuse_max_k, block_mode, ops_per_pass, tile_qubits)
+    ns, nc = ctypes.c_int(), ctypes.c_int()
+    buf = ctypes.create_string_buffer(1 << 20)
+    _check(load().sv_jit_check(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), 1 if compile else 0, arch,
+                               ctypes.byref(ns), ctypes.byref(nc), buf, 1 << 20))
+    return ns.value, nc.value, buf.value.decode(errors="replace")
 
 
 def sv_profile_enable(on: bool = True):

@@ -21,12 +21,16 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsv.so")
 
-SOURCES = ["sv_plan.cpp", "sv_program.cpp", "sv_api.cpp", "sv_adjoint_host.cpp", "sv_serve.cpp", "sv_sweep.cu",
-           "sv_reduce.cu", "sv_adjoint.cu", "sv_noalloc.cu", "sv_sample.cu"]
-HEADERS = ["sv_internal.h", "sv_adjoint.h"]
+SOURCES = ["sv_plan.cpp", "sv_program.cpp", "sv_api.cpp", "sv_adjoint_host.cpp", "sv_serve.cpp", "sv_jit.cpp",
+           "sv_sweep.cu", "sv_reduce.cu", "sv_adjoint.cu", "sv_noalloc.cu", "sv_sample.cu"]
+# Device headers the run-time compiled pass kernels include (sv_jit.cpp): their
+# text is embedded in the library, so a kernel compiled at run time is built
+# from the same code as the library's own pass kernel.
+JIT_HEADERS = ["sv_prog_layout.h", "sv_pass_ops.cuh", "sv_tma_pass.cuh"]
+HEADERS = ["sv_internal.h", "sv_adjoint.h"] + JIT_HEADERS
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
+         "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-I" + OUT]
 
 
 def nvcc() -> str:
@@ -53,7 +57,7 @@ def _stamp(extra=()) -> str:
 
 # Sources that decide what the pass kernel does (the kernel, the program
 # builder, the planner and the shared structures).
-SWEEP_SOURCES = ["sv_sweep.cu", "sv_program.cpp", "sv_plan.cpp", "sv_internal.h"]
+SWEEP_SOURCES = ["sv_sweep.cu", "sv_program.cpp", "sv_plan.cpp", "sv_internal.h", "sv_jit.cpp"] + JIT_HEADERS
 
 
 def sweep_stamp() -> str:
@@ -69,8 +73,33 @@ def sweep_stamp() -> str:
     return h.hexdigest()
 
 
+def write_jit_headers() -> None:
+    """Writes _build/sv_jit_headers.inc: the device headers as string
+    literals (names and texts) for the run-time compiler."""
+    names, texts = [], []
+    for f in JIT_HEADERS:
+        with open(os.path.join(CSRC, f)) as fh:
+            body = fh.read()
+        if ")svjit\"" in body:
+            raise RuntimeError("%s holds the raw-string delimiter" % f)
+        names.append('"%s"' % f)
+        texts.append('R"svjit(' + body + ')svjit"')
+    out = ("// written by build.py from " + ", ".join(JIT_HEADERS) + "\n"
+           "static const char* const kJitHeaderNames[] = {" + ", ".join(names) + "};\n"
+           "static const char* const kJitHeaderTexts[] = {\n" + ",\n".join(texts) + "};\n")
+    path = os.path.join(OUT, "sv_jit_headers.inc")
+    old = None
+    if os.path.exists(path):
+        with open(path) as fh:
+            old = fh.read()
+    if old != out:
+        with open(path, "w") as fh:
+            fh.write(out)
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT, exist_ok=True)
+    write_jit_headers()
     stamp_file = os.path.join(OUT, "libsv.stamp")
     stamp = _stamp(extra_flags)
     if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
@@ -93,7 +122,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

@@ -222,6 +222,12 @@ struct Compiled {
   int n = 0;
   std::vector<SweepProgram<float>> pf;
   std::vector<SweepProgram<double>> pd;
+  // the programs' compiled pass kernels (sv_jit.cpp), made on the run that
+  // jit_mode() names and kept with the circuit
+  mutable std::mutex jit_mu;
+  mutable int runs = 0;
+  mutable bool jit_made = false;
+  mutable std::vector<const JitKernel*> jit;
 };
 
 constexpr size_t kCompiledMax = 8;                  // circuits kept
@@ -287,18 +293,35 @@ std::shared_ptr<const Compiled> compiled_circuit(int n, sv_dtype dtype, const sv
 }
 
 template <typename R>
-void run_programs(void* state, int n, const std::vector<SweepProgram<R>>& progs, cudaStream_t stream) {
+void run_programs(void* state, int n, const std::vector<SweepProgram<R>>& progs, cudaStream_t stream,
+                  const std::vector<const JitKernel*>* jit = nullptr) {
   const double bytes = 2.0 * (double)sizeof(Cx<R>) * (double)(1ull << n);  // read + write the state
-  for (const SweepProgram<R>& P : progs) {
+  for (size_t i = 0; i < progs.size(); i++) {
     Prof pr(stream, "sweep", bytes);
-    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), P, stream, &pr.family), "sweep launch");
+    const JitKernel* k = jit && i < jit->size() ? (*jit)[i] : nullptr;
+    cuda_check(launch_sweep<R>(reinterpret_cast<Cx<R>*>(state), progs[i], stream, &pr.family, k), "sweep launch");
     pr.done();
   }
 }
 
+// The circuit's compiled pass kernels, made (NVRTC, on the host) on the run
+// jit_mode() names: a circuit run once keeps the interpreting kernel and pays
+// no compilation.
+const std::vector<const JitKernel*>* jit_kernels(const Compiled& c, sv_dtype dtype) {
+  const int mode = jit_mode();
+  if (mode == 0 || dtype != SV_C64) return nullptr;
+  std::lock_guard<std::mutex> lk(c.jit_mu);
+  c.runs++;
+  if (!c.jit_made && c.runs >= (mode == 2 ? 1 : 2)) {
+    c.jit = jit_compile_programs<float>(c.pf);
+    c.jit_made = true;
+  }
+  return c.jit_made ? &c.jit : nullptr;
+}
+
 void run_compiled(void* state, const Compiled& c, sv_dtype dtype, cudaStream_t stream) {
   if (dtype == SV_C64)
-    run_programs<float>(state, c.n, c.pf, stream);
+    run_programs<float>(state, c.n, c.pf, stream, jit_kernels(c, dtype));
   else
     run_programs<double>(state, c.n, c.pd, stream);
 }
@@ -656,6 +679,58 @@ sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits
     else
       run_batch_small<double>(n_requests, dtype, n_qubits, gates, n_gates, out_sum_z, out_on_device,
                               (cudaStream_t)stream);
+  });
+}
+
+sv_status sv_jit_set_mode(int mode) {
+  return guarded([&] {
+    if (mode < -1 || mode > 2) fail(SV_ERR_INVALID, "mode must be -1, 0, 1 or 2");
+    jit_set_mode(mode);
+  });
+}
+
+sv_status sv_jit_info(int* mode, int* available, long long* compiled, long long* failed, long long* launches,
+                      double* compile_seconds, char* message, size_t message_cap) {
+  return guarded([&] {
+    std::string why, last;
+    const bool av = jit_available(&why);
+    jit_stats(compiled, failed, launches, compile_seconds, &last);
+    if (mode) *mode = jit_mode();
+    if (available) *available = av ? 1 : 0;
+    if (message && message_cap) {
+      const std::string& m = av ? last : why;
+      const size_t k = std::min(m.size(), message_cap - 1);
+      std::memcpy(message, m.data(), k);
+      message[k] = '\0';
+    }
+  });
+}
+
+sv_status sv_jit_check(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
+                       size_t n_param_values, const sv_exec_opts* opts, int compile, int arch, int* n_sources,
+                       int* n_compiled, char* text, size_t text_cap) {
+  return guarded([&] {
+    check_dtype_n(n_qubits, dtype);
+    if (!n_sources || !n_compiled) fail(SV_ERR_INVALID, "NULL argument");
+    if (compile && (arch < 100 || arch > 200)) fail(SV_ERR_INVALID, "arch must be a compute capability such as 103");
+    if (compile && !jit_available(nullptr)) fail(SV_ERR_UNSUPPORTED, "the run-time compiler is not available");
+    Plan plan = make_plan(n_qubits, dtype, gates, n_gates, param_values, n_param_values, opts_of(opts));
+    std::string err, src;
+    if (dtype == SV_C64) {
+      std::vector<SweepProgram<float>> progs(plan.sweeps.size());
+      for (size_t i = 0; i < plan.sweeps.size(); i++) build_program<float>(plan, plan.sweeps[i], progs[i]);
+      jit_check_programs<float>(progs, compile != 0, arch, n_sources, n_compiled, &err, &src);
+    } else {
+      std::vector<SweepProgram<double>> progs(plan.sweeps.size());
+      for (size_t i = 0; i < plan.sweeps.size(); i++) build_program<double>(plan, plan.sweeps[i], progs[i]);
+      jit_check_programs<double>(progs, compile != 0, arch, n_sources, n_compiled, &err, &src);
+    }
+    if (text && text_cap) {
+      const std::string& m = err.empty() ? src : err;
+      const size_t k = std::min(m.size(), text_cap - 1);
+      std::memcpy(text, m.data(), k);
+      text[k] = '\0';
+    }
   });
 }
 

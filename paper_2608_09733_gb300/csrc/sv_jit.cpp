@@ -1,0 +1,599 @@
+// sv_jit.cpp -- pass kernels compiled at run time from one program.
+//
+// The library's pass kernel interprets a program: for every op of every
+// register phase it loads the op's dispatch word, branches on its kind and
+// slots, and computes its conditions and table variants, once per tile per
+// thread.  On large states that bookkeeping costs as many issue slots as the
+// arithmetic.  Here a program is written out as straight-line CUDA -- every
+// phase's register positions, every op's kind, slots, controls, coefficient
+// offsets and sign patterns as constants -- calling the same register and
+// shared-memory op functions (sv_pass_ops.cuh) inside the same TMA pass
+// scaffold (sv_tma_pass.cuh), compiled with NVRTC for the device's
+// architecture and launched in place of the interpreting kernel.  The
+// arithmetic is the same sequence of operations, so both kernels give the
+// same bits.
+//
+// NVRTC is opened with dlopen on first use; without it (or the driver's
+// module entry points) every pass keeps the interpreting kernel.  A compiled
+// kernel is cached per (device, source text) for the life of the process.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sv_internal.h"
+#include "sv_jit_headers.inc"  // kJitHeaderNames / kJitHeaderTexts, written by build.py
+
+namespace sv {
+
+struct JitKernel {
+  CUfunction fn = nullptr;
+  int device = -1;
+  size_t smem_configured = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- source
+
+struct Src {
+  std::string s;
+  void line(const char* fmt, ...) __attribute__((format(printf, 2, 3))) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    s += buf;
+    s += '\n';
+  }
+};
+
+constexpr int kJitGroups = 4;        // groups of a CTA, as the interpreting TMA pass
+constexpr int kJitGroupThreads = 128;  // 12-qubit tiles, five register qubits
+
+// The condition of an op on the bits outside the tile and on the thread's
+// bits (empty when the op applies everywhere).
+std::string op_guard(const DevOp& op, uint32_t code) {
+  std::string g;
+  char buf[160];
+  if (code & (OPF_XCOND << 4)) {
+    snprintf(buf, sizeof(buf), "(base & 0x%llxull) == 0x%llxull", (unsigned long long)op.xmask,
+             (unsigned long long)op.xval);
+    g += buf;
+  }
+  if (code & (OPF_TCOND << 4)) {
+    snprintf(buf, sizeof(buf), "(tb & 0x%xu) == 0x%xu", op.tmask, op.tval);
+    if (!g.empty()) g += " && ";
+    g += buf;
+  }
+  return g;
+}
+
+// One register op (not a sign flip), as apply_reg of the interpreting kernel
+// dispatches it, with every dispatch decision taken here.
+template <typename R>
+void emit_reg_op(Src& o, const DevOp& op, int op_index, int rq) {
+  const uint32_t code = op.pad;
+  const uint32_t kind = code & 15u, fl = (code >> 4) & 7u;
+  const uint32_t C = code >> 17, rm = (code >> 7) & 31u, rv = (code >> 12) & 31u;
+  const char* Rn = sizeof(R) == 4 ? "float" : "double";
+  const std::string g = op_guard(op, code);
+  o.line("    %s{  // op %d", g.empty() ? "" : ("if (" + g + ") ").c_str(), op_index);
+  switch (kind) {
+    case OPK_KRON:
+      for (int S = 0; S < rq; S++)
+        if (rm & (1u << S)) {
+          o.line("      r_u1<%s, %d, %d>(v, cf + %u);", Rn, rq, S, C + 4u * S);
+          o.line("      asm volatile(\"\" ::: \"memory\");");
+        }
+      break;
+    case OPK_KROT:
+      for (int S = 0; S < rq; S++)
+        if (rm & (1u << S)) {
+          const bool cot = sizeof(R) == 8 && ((rv >> S) & 1u);
+          o.line("      r_rot<%s, %d, %d, %s>(v, cf[%u]);", Rn, rq, S, cot ? "true" : "false", C + S);
+          o.line("      asm volatile(\"\" ::: \"memory\");");
+        }
+      break;
+    case OPK_PHASE: {
+      std::string var;
+      char buf[96];
+      for (int i = 0; i < op.k; i++) {
+        const uint32_t c = op.gq[i];
+        if (c < 64)
+          snprintf(buf, sizeof(buf), "(((tb >> %u) & 1u) << %d)", c, i);
+        else
+          snprintf(buf, sizeof(buf), "((uint32_t)((base >> %u) & 1ull) << %d)", c - 64, i);
+        if (!var.empty()) var += " | ";
+        var += buf;
+      }
+      if (var.empty())
+        o.line("      r_phase_table<%s, %d>(v, cf + %u);", Rn, rq, C);
+      else
+        o.line("      r_phase_table<%s, %d>(v, cf + %u + (%s) * %du);", Rn, rq, C, var.c_str(),
+               table_stride<R>(rq));
+      break;
+    }
+    case OPK_DENSE:
+    case OPK_REAL:
+      if (op.k == 1)
+        o.line("      r_dense1<%s, %d, %d, %s>(v, cf + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0],
+               kind == OPK_REAL ? "true" : "false", C, rm, rv);
+      else
+        o.line("      r_dense2<%s, %d, %d, %d>(v, cf + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0], op.rs[1], C, rm, rv);
+      break;
+    case OPK_ANTIDIAG:
+      o.line("      r_anti1<%s, %d, %d, %s>(v, cf + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0],
+             (fl & OPF_FLIP) ? "true" : "false", C, rm, rv);
+      break;
+    case OPK_SWAP:
+      o.line("      r_swap<%s, %d, %d, %d>(v, 0x%xu, 0x%xu);", Rn, rq, op.rs[0], op.rs[1], rm, rv);
+      break;
+    case OPK_DIAG:
+      o.line("      r_diag<%s, %d>(v, P.ops[%d], cf + %u, tb, base);", Rn, rq, op_index, C);
+      break;
+    default: break;
+  }
+  o.line("    }");
+}
+
+}  // namespace
+
+// The kernel source of one program (see the top of this file); empty if the
+// program is not one the TMA pass runs (complex64, 12-qubit tiles of 128
+// threads with five register qubits, at least 2^9 tiles).
+template <typename R>
+std::string jit_source(const SweepProgram<R>& P) {
+  const ProgramHeader& h = P.h;
+  const int rq = h.rq;
+  if (sizeof(R) != 4 || rq != 5 || (1 << (h.m - rq)) != kJitGroupThreads || h.n - h.m < 9) return std::string();
+  const char* Rn = sizeof(R) == 4 ? "float" : "double";
+  Src o;
+  o.line("// pass program: n %d, m %d, %d phases, %d ops, %d coefficients", h.n, h.m, h.nphases, h.nops, h.ncoef);
+  o.line("#include \"sv_tma_pass.cuh\"");
+  o.line("namespace sv {");
+  o.line("struct alignas(64) JitTensorMap { unsigned long long opaque[16]; };");
+  o.line("struct JitRunner {");
+  o.line("  const SweepProgram<%s>& P;", Rn);
+  o.line("  template <class Release>");
+  o.line("  __device__ __forceinline__ void operator()(Cx<%s>* s, const Cx<%s>* cf, uint64_t base, const Grp& gr,", Rn,
+         Rn);
+  o.line("                                             Cx<%s>* __restrict__ state, const Release& release) const {", Rn);
+  bool direct_done = false;
+  for (int p = 0; p < h.nphases; p++) {
+    const Phase& ph = P.ph[p];
+    const bool last = p == h.nphases - 1;
+    if (ph.kind == PH_REG) {
+      const bool direct = last;
+      o.line("  {  // phase %d: register slots at local bits %d %d %d %d %d", p, ph.rp[0], ph.rp[1], ph.rp[2],
+             ph.rp[3], ph.rp[4]);
+      const bool all_active = (1 << ph.ntpos) >= kJitGroupThreads;
+      o.line("    uint32_t tb = gr.tid;");
+      for (int i = 0; i < rq; i++) o.line("    tb = ins0(tb, %d);", ph.rp[i]);
+      std::string ms;
+      for (int i = 0; i < rq; i++) ms += (i ? ", " : "") + std::to_string(1u << ph.rp[i]) + "u";
+      o.line("    const uint32_t m[%d] = {%s};", rq, ms.c_str());
+      o.line("    Cx<%s> v[%d];", Rn, 1 << rq);
+      const std::string act = all_active ? "" : "if (gr.tid < " + std::to_string(1u << ph.ntpos) + "u) ";
+      o.line("    %sreg_load<%s, %d>(v, s, tb, m);", act.c_str(), Rn, rq);
+      if (direct) {
+        o.line("    grp_sync(gr);  // every thread has its registers: the stage is free");
+        o.line("    release();");
+      }
+      o.line("    %s{", act.c_str());
+      o.line("    uint32_t neg = 0;");
+      for (int i = 0; i < ph.nops; i++) {
+        const int oi = ph.first + i;
+        const DevOp& op = P.ops[oi];
+        const uint32_t code = op.pad;
+        if ((code & 15u) == OPK_SIGN) {
+          const std::string g = op_guard(op, code);
+          if (g.empty())
+            o.line("    neg ^= 0x%xu;  // op %d", op.coef, oi);
+          else
+            o.line("    if (%s) neg ^= 0x%xu;  // op %d", g.c_str(), op.coef, oi);
+          continue;
+        }
+        o.line("    if (neg) { apply_neg<%s, %d>(v, neg); neg = 0; }", Rn, rq);
+        emit_reg_op<R>(o, op, oi, rq);
+      }
+      o.line("    if (neg) apply_neg<%s, %d>(v, neg);", Rn, rq);
+      if (direct) {
+        std::string gs;
+        for (int i = 0; i < rq; i++) gs += (i ? ", " : "") + std::to_string(1ull << h.tq[ph.rp[i]]) + "ull";
+        o.line("    const uint64_t gs[%d] = {%s};", rq, gs.c_str());
+        // the tile offset of the thread's bits (every local bit outside the
+        // register slots): local bit i is global bit tq[i]
+        o.line("    uint64_t toff = 0;");
+        for (int i = 0; i < h.m; i++) {
+          bool reg = false;
+          for (int j = 0; j < rq; j++) reg = reg || ph.rp[j] == i;
+          if (!reg) o.line("    toff |= (uint64_t)((tb >> %d) & 1u) << %d;", i, h.tq[i]);
+        }
+        o.line("    reg_store_global<%s, %d>(v, state, base | toff, gs, %s);", Rn, rq, ph.rp[0] == 0 ? "true" : "false");
+        direct_done = true;
+      } else {
+        o.line("    reg_store<%s, %d>(v, s, tb, m);", Rn, rq);
+      }
+      o.line("    }");
+      o.line("  }");
+      if (!direct) o.line("  grp_sync(gr);");
+    } else {
+      const DevOp& op = P.ops[ph.first];
+      const uint32_t C = op.coef;
+      o.line("  {  // phase %d: op %d in shared memory", p, ph.first);
+      char cond[128];
+      snprintf(cond, sizeof(cond), "(base & 0x%llxull) == 0x%llxull", (unsigned long long)op.xmask,
+               (unsigned long long)op.xval);
+      const int tsz = 1 << h.m;
+      switch (op.kind) {
+        case OPK_DIAG:
+        case OPK_SIGN:
+          o.line("    if (%s) s_diag<%s>(s, %d, P.ops[%d], cf + %u, base, gr);", cond, Rn, tsz, ph.first, C);
+          break;
+        case OPK_ANTIDIAG:
+        case OPK_SWAP:
+          o.line("    if (%s) s_perm<%s>(s, %d, P.ops[%d], cf + %u, gr);", cond, Rn, tsz, ph.first, C);
+          break;
+        default:
+          o.line("    if (%s) s_denseK<%s, %d>(s, %d, P.ops[%d], cf + %u, gr);", cond, Rn, (int)op.k, tsz, ph.first, C);
+      }
+      o.line("  }");
+      o.line("  grp_sync(gr);");
+    }
+  }
+  if (!direct_done) {
+    o.line("  stage_copy_out<%s>(s, %d, state, base, P.h, gr);", Rn, 1 << h.m);
+    o.line("  grp_sync(gr);");
+    o.line("  release();");
+  }
+  o.line("  }");
+  o.line("};");
+  o.line("}  // namespace sv");
+  o.line("extern \"C\" __global__ void __launch_bounds__(%d, 1)", kJitGroups * kJitGroupThreads);
+  o.line("k_sweep_jit(sv::Cx<%s>* __restrict__ state, const __grid_constant__ sv::JitTensorMap tmap,", Rn);
+  o.line("            const __grid_constant__ sv::TmaBoxes bx, const __grid_constant__ sv::SweepProgram<%s> P,", Rn);
+  o.line("            int ns, int* status) {");
+  o.line("  sv::tma_pass_body<%s, %d, %d>(state, &tmap, bx, P.h, P.coef, ns, status, sv::JitRunner{P});", Rn,
+         kJitGroups, kJitGroupThreads);
+  o.line("}");
+  return o.s;
+}
+
+template std::string jit_source<float>(const SweepProgram<float>&);
+template std::string jit_source<double>(const SweepProgram<double>&);
+
+namespace {
+
+// ---------------------------------------------------------------- NVRTC
+
+struct Nvrtc {
+  bool ok = false;
+  std::string why;
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+};
+
+const Nvrtc& nvrtc() {
+  static Nvrtc n = [] {
+    Nvrtc r;
+    void* h = nullptr;
+    for (const char* name : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"}) {
+      h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
+      if (h) break;
+    }
+    if (!h) {
+      r.why = "libnvrtc not found";
+      return r;
+    }
+    r.create = (decltype(r.create))dlsym(h, "nvrtcCreateProgram");
+    r.compile = (decltype(r.compile))dlsym(h, "nvrtcCompileProgram");
+    r.destroy = (decltype(r.destroy))dlsym(h, "nvrtcDestroyProgram");
+    r.log_size = (decltype(r.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+    r.log = (decltype(r.log))dlsym(h, "nvrtcGetProgramLog");
+    r.cubin_size = (decltype(r.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+    r.cubin = (decltype(r.cubin))dlsym(h, "nvrtcGetCUBIN");
+    r.ok = r.create && r.compile && r.destroy && r.log_size && r.log && r.cubin_size && r.cubin;
+    if (!r.ok) r.why = "libnvrtc lacks an entry point";
+    return r;
+  }();
+  return n;
+}
+
+// Compiles one kernel source to a cubin for sm_<arch>; false with the
+// compiler's log in *log on failure.
+bool compile_cubin(const std::string& src, int arch, std::vector<char>& out, std::string* log) {
+  const Nvrtc& nv = nvrtc();
+  if (!nv.ok) {
+    if (log) *log = nv.why;
+    return false;
+  }
+  constexpr int NH = sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]);
+  nvrtcProgram prog = nullptr;
+  if (nv.create(&prog, src.c_str(), "sv_pass.cu", NH, kJitHeaderTexts, kJitHeaderNames) != NVRTC_SUCCESS) {
+    if (log) *log = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const std::string archopt = "--gpu-architecture=sm_" + std::to_string(arch) + "a";
+  // -default-device: the program-layout header's constexpr helpers are
+  // plain functions (host and device in the library's own build)
+  const char* opts[] = {archopt.c_str(), "-std=c++17", "-default-device"};
+  const nvrtcResult r = nv.compile(prog, 3, opts);
+  bool ok = r == NVRTC_SUCCESS;
+  if (!ok && log) {
+    size_t n = 0;
+    nv.log_size(prog, &n);
+    std::string l(n, '\0');
+    if (n) nv.log(prog, &l[0]);
+    *log = l;
+  }
+  if (ok) {
+    size_t n = 0;
+    ok = nv.cubin_size(prog, &n) == NVRTC_SUCCESS && n > 0;
+    if (ok) {
+      out.resize(n);
+      ok = nv.cubin(prog, out.data()) == NVRTC_SUCCESS;
+    }
+  }
+  nv.destroy(&prog);
+  return ok;
+}
+
+// ---------------------------------------------------------------- driver
+
+using ModuleLoadDataFn = CUresult (*)(CUmodule*, const void*);
+using ModuleGetFunctionFn = CUresult (*)(CUfunction*, CUmodule, const char*);
+using FuncSetAttributeFn = CUresult (*)(CUfunction, CUfunction_attribute, int);
+using LaunchKernelFn = CUresult (*)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                                    CUstream, void**, void**);
+
+struct Driver {
+  bool ok = false;
+  ModuleLoadDataFn load = nullptr;
+  ModuleGetFunctionFn get = nullptr;
+  FuncSetAttributeFn attr = nullptr;
+  LaunchKernelFn launch = nullptr;
+};
+
+template <typename F>
+F entry(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (F)p;
+}
+
+const Driver& driver() {
+  static Driver d = [] {
+    Driver r;
+    r.load = entry<ModuleLoadDataFn>("cuModuleLoadData");
+    r.get = entry<ModuleGetFunctionFn>("cuModuleGetFunction");
+    r.attr = entry<FuncSetAttributeFn>("cuFuncSetAttribute");
+    r.launch = entry<LaunchKernelFn>("cuLaunchKernel");
+    r.ok = r.load && r.get && r.attr && r.launch;
+    return r;
+  }();
+  return d;
+}
+
+// ---------------------------------------------------------------- cache and policy
+
+std::mutex g_jit_mu;
+std::map<std::pair<int, std::string>, std::unique_ptr<JitKernel>> g_jit_kernels;  // (device, source) -> kernel
+std::atomic<int> g_jit_mode{-1};
+std::atomic<long long> g_jit_compiled{0}, g_jit_failed{0}, g_jit_launches{0};
+std::atomic<long long> g_jit_compile_us{0};
+std::string g_jit_last_error;
+
+int device_arch(int dev) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major * 10 + minor;
+}
+
+// Compiles the given sources in parallel (host threads; NVRTC needs no
+// device), each to a cubin.
+void compile_all(const std::vector<const std::string*>& srcs, int arch, std::vector<std::vector<char>>& bins,
+                 std::vector<std::string>& logs, std::vector<char>& ok) {
+  const size_t n = srcs.size();
+  bins.assign(n, {});
+  logs.assign(n, {});
+  ok.assign(n, 0);
+  std::atomic<size_t> next{0};
+  auto work = [&] {
+    for (size_t i; (i = next.fetch_add(1)) < n;) ok[i] = compile_cubin(*srcs[i], arch, bins[i], &logs[i]) ? 1 : 0;
+  };
+  unsigned hw = std::thread::hardware_concurrency();
+  size_t nt = std::min<size_t>(n, hw ? std::min(hw, 16u) : 4u);
+  std::vector<std::thread> th;
+  for (size_t t = 1; t < nt; t++) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+}
+
+}  // namespace
+
+int jit_mode() {
+  int m = g_jit_mode.load();
+  if (m < 0) {
+    const char* e = std::getenv("SV_JIT");
+    m = 1;
+    if (e && e[0] == '0') m = 0;
+    if (e && (e[0] == '2' || std::strcmp(e, "eager") == 0)) m = 2;
+    g_jit_mode.store(m);
+  }
+  return m;
+}
+
+void jit_set_mode(int mode) { g_jit_mode.store(mode < 0 ? -1 : mode); }
+
+template <typename R>
+std::vector<const JitKernel*> jit_compile_programs(const std::vector<SweepProgram<R>>& progs) {
+  std::vector<const JitKernel*> out(progs.size(), nullptr);
+  if (sizeof(R) != 4 || !driver().ok || !nvrtc().ok) return out;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return out;
+  }
+  const int arch = device_arch(dev);
+  std::vector<std::string> src(progs.size());
+  std::vector<const std::string*> todo;
+  std::vector<size_t> todo_idx;
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    std::map<std::string, size_t> seen;
+    for (size_t i = 0; i < progs.size(); i++) {
+      src[i] = jit_source<R>(progs[i]);
+      if (src[i].empty()) continue;
+      auto it = g_jit_kernels.find({dev, src[i]});
+      if (it != g_jit_kernels.end()) {
+        out[i] = it->second.get();
+        continue;
+      }
+      if (seen.emplace(src[i], i).second) {
+        todo.push_back(&src[i]);
+        todo_idx.push_back(i);
+      }
+    }
+  }
+  if (!todo.empty()) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<std::vector<char>> bins;
+    std::vector<std::string> logs;
+    std::vector<char> ok;
+    compile_all(todo, arch, bins, logs, ok);
+    g_jit_compile_us += (long long)std::chrono::duration_cast<std::chrono::microseconds>(
+                            std::chrono::steady_clock::now() - t0)
+                            .count();
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    for (size_t t = 0; t < todo.size(); t++) {
+      if (!ok[t]) {
+        g_jit_failed++;
+        g_jit_last_error = logs[t].substr(0, 4000);
+        continue;
+      }
+      CUmodule mod = nullptr;
+      auto k = std::make_unique<JitKernel>();
+      if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS ||
+          driver().get(&k->fn, mod, "k_sweep_jit") != CUDA_SUCCESS) {
+        g_jit_failed++;
+        g_jit_last_error = "module load failed";
+        continue;
+      }
+      k->device = dev;
+      g_jit_compiled++;
+      g_jit_kernels[{dev, *todo[t]}] = std::move(k);
+    }
+    for (size_t i = 0; i < progs.size(); i++) {
+      if (out[i] || src[i].empty()) continue;
+      auto it = g_jit_kernels.find({dev, src[i]});
+      if (it != g_jit_kernels.end()) out[i] = it->second.get();
+    }
+  }
+  return out;
+}
+
+template std::vector<const JitKernel*> jit_compile_programs<float>(const std::vector<SweepProgram<float>>&);
+template std::vector<const JitKernel*> jit_compile_programs<double>(const std::vector<SweepProgram<double>>&);
+
+cudaError_t jit_launch(const JitKernel* k, void* state, const void* map, const void* bx, const void* prog, int ns,
+                       int* status, unsigned grid, unsigned block, size_t smem, cudaStream_t stream) {
+  const Driver& d = driver();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!k || !k->fn || k->device != dev) return cudaErrorInvalidDeviceFunction;
+  JitKernel* kk = const_cast<JitKernel*>(k);
+  if (smem > kk->smem_configured) {
+    if (d.attr(kk->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+      return cudaErrorInvalidConfiguration;
+    kk->smem_configured = smem;
+  }
+  void* state_arg = state;
+  void* args[] = {&state_arg, const_cast<void*>(map), const_cast<void*>(bx), const_cast<void*>(prog), &ns, &status};
+  const CUresult r = d.launch(kk->fn, grid, 1, 1, block, 1, 1, (unsigned)smem, (CUstream)stream, args, nullptr);
+  if (r != CUDA_SUCCESS) return cudaErrorLaunchFailure;
+  g_jit_launches++;
+  return cudaSuccess;
+}
+
+// Generates (and with compile set, compiles for sm_<arch>) the kernel of every
+// program of a plan without a device: the generator and the run-time
+// compiler can be checked on a machine without a GPU.
+template <typename R>
+void jit_check_programs(const std::vector<SweepProgram<R>>& progs, bool compile, int arch, int* n_sources,
+                        int* n_compiled, std::string* first_error, std::string* first_source) {
+  std::vector<std::string> src;
+  for (const auto& P : progs) {
+    std::string s = jit_source<R>(P);
+    if (!s.empty()) src.push_back(std::move(s));
+  }
+  *n_sources = (int)src.size();
+  *n_compiled = 0;
+  if (first_source && !src.empty()) *first_source = src[0];
+  if (!compile || src.empty()) return;
+  std::vector<const std::string*> ptrs;
+  for (auto& s : src) ptrs.push_back(&s);
+  std::vector<std::vector<char>> bins;
+  std::vector<std::string> logs;
+  std::vector<char> ok;
+  compile_all(ptrs, arch, bins, logs, ok);
+  for (size_t i = 0; i < src.size(); i++) {
+    if (ok[i])
+      (*n_compiled)++;
+    else if (first_error && first_error->empty())
+      *first_error = logs[i].empty() ? std::string("compile failed") : logs[i];
+  }
+}
+
+template void jit_check_programs<float>(const std::vector<SweepProgram<float>>&, bool, int, int*, int*,
+                                        std::string*, std::string*);
+template void jit_check_programs<double>(const std::vector<SweepProgram<double>>&, bool, int, int*, int*,
+                                         std::string*, std::string*);
+
+void jit_stats(long long* compiled, long long* failed, long long* launches, double* compile_seconds,
+               std::string* last_error) {
+  if (compiled) *compiled = g_jit_compiled.load();
+  if (failed) *failed = g_jit_failed.load();
+  if (launches) *launches = g_jit_launches.load();
+  if (compile_seconds) *compile_seconds = 1e-6 * (double)g_jit_compile_us.load();
+  if (last_error) {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    *last_error = g_jit_last_error;
+  }
+}
+
+bool jit_available(std::string* why) {
+  if (!nvrtc().ok) {
+    if (why) *why = nvrtc().why;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace sv

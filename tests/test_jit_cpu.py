@@ -1,0 +1,74 @@
+"""The pass-kernel generator and the run-time compiler, without a GPU.
+
+sv_jit_check plans a circuit, writes the kernel source of every pass the TMA
+pass would run and compiles each with NVRTC for sm_103a; no device is
+touched.  Results of the compiled kernels are checked on the GPU
+(test_gpu_jit.py).
+"""
+
+import re
+
+import pytest
+
+from paper_2608_09733_gb300 import binding as B
+from workloads import fused_layered_u3_cz, random_circuit
+
+
+def _nvrtc_or_skip():
+    info = B.sv_jit_info()
+    if not info["available"]:
+        pytest.skip("NVRTC not available: " + info["message"])
+
+
+def test_sources_only_for_tma_passes(svlib):
+    g = fused_layered_u3_cz(20, 4, seed=1)
+    # 20 qubits with 12-qubit tiles: 2^8 tiles, fewer than the TMA pass takes
+    assert B.sv_jit_check(20, B.SV_C64, g, fuse_max_k=5, compile=False)[0] == 0
+    # complex128 passes are not compiled
+    g = fused_layered_u3_cz(26, 4, seed=1)
+    assert B.sv_jit_check(26, B.SV_C128, g, fuse_max_k=5, compile=False)[0] == 0
+    _, passes, _ = B.sv_plan_info(26, B.SV_C64, g, fuse_max_k=5)
+    ns, nc, src = B.sv_jit_check(26, B.SV_C64, g, fuse_max_k=5, compile=False)
+    assert ns == passes and nc == 0
+    assert "k_sweep_jit" in src and "tma_pass_body" in src
+
+
+def test_generated_source_has_constant_dispatch(svlib):
+    """The layered U3/CZ circuit's passes are phase tables, rotations and sign
+    flips only: no op descriptor is read at run time in a register phase."""
+    g = fused_layered_u3_cz(26, 6, seed=2)
+    _, _, src = B.sv_jit_check(26, B.SV_C64, g, fuse_max_k=5, compile=False)
+    assert "r_rot<float, 5," in src and "r_phase_table<float, 5>" in src
+    assert "P.ops[" not in src
+    # every register phase stages its 32 amplitudes: m[] holds five distinct bits
+    for ms in re.findall(r"const uint32_t m\[5\] = \{([^}]*)\}", src):
+        bits = [int(x.strip().rstrip("u")) for x in ms.split(",")]
+        assert len(set(bits)) == 5 and all(b & (b - 1) == 0 for b in bits)
+
+
+def test_bench_circuit_compiles(svlib):
+    _nvrtc_or_skip()
+    n = 30
+    g = fused_layered_u3_cz(n, 20, seed=0)
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5)
+    ns, nc, text = B.sv_jit_check(n, B.SV_C64, g, fuse_max_k=5, compile=True, arch=103)
+    assert ns == passes and nc == ns, text[:2000]
+
+
+@pytest.mark.parametrize("fuse,mode", [(0, 0), (5, 0), (5, 1)])
+def test_every_op_kind_compiles(svlib, fuse, mode):
+    _nvrtc_or_skip()
+    n = 22
+    g = random_circuit(n, 160, seed=922, max_controls=3, max_unitary_k=5)
+    ns, nc, text = B.sv_jit_check(n, B.SV_C64, g, fuse_max_k=fuse, block_mode=mode, compile=True, arch=103,
+                                  tile_qubits=12)
+    assert ns > 0 and nc == ns, text[:2000]
+
+
+def test_mode_validation(svlib):
+    with pytest.raises(B.SvError):
+        B.sv_jit_set_mode(3)
+    B.sv_jit_set_mode(0)
+    assert B.sv_jit_info()["mode"] == 0
+    B.sv_jit_set_mode(-1)
+    assert B.sv_jit_info()["mode"] in (0, 1, 2)
