@@ -306,10 +306,16 @@ void run_programs(void* state, int n, const std::vector<SweepProgram<R>>& progs,
 
 // The circuit's compiled pass kernels, made (NVRTC, on the host) on the run
 // jit_mode() names: a circuit run once keeps the interpreting kernel and pays
-// no compilation.
+// no compilation.  While a serving session is live the TMA pass is off, so
+// nothing is compiled or loaded then (runs are not counted).
 const std::vector<const JitKernel*>* jit_kernels(const Compiled& c, sv_dtype dtype) {
   const int mode = jit_mode();
   if (mode == 0 || dtype != SV_C64) return nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || session_live(dev)) {
+    cudaGetLastError();
+    return nullptr;
+  }
   std::lock_guard<std::mutex> lk(c.jit_mu);
   c.runs++;
   if (!c.jit_made && c.runs >= (mode == 2 ? 1 : 2)) {
