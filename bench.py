@@ -167,15 +167,49 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)
 
+L2_BYTES = 129e6  # GB300 L2
+
+
+def step_config(args, n, n_gates, nblocks, npasses, amp):
+    """The workload's config dict, the same for both arms."""
+    return {"workload": "fused_layered_u3_cz_%dq_%dlayers_%s" % (n, args.layers, args.dtype),
+            "n_qubits": n, "layers": args.layers, "gates": n_gates, "fuse_max_k": args.fuse,
+            "block_mode": args.block_mode, "fused_blocks": nblocks, "passes_per_step": npasses,
+            "l2": ("inputs larger than L2 (state %.1f GiB)" if (2 ** n) * amp > L2_BYTES else
+                   "state fits in L2 (%.1f GiB), not flushed") % ((2 ** n) * amp / 2 ** 30),
+            "parallelism": "single"}
+
+
+def step_bytes(n, npasses, amp):
+    """The metric's bytes of one step: every pass reads and writes the state,
+    plus the initialisation write and the read-out read."""
+    return (2 * npasses + 2) * (2 ** n) * amp
+
+
 def run_reference(args, ws, rank):
+    """The oracle on the host cores, on the GPU arm's workload and metric: each
+    step applies a bounded sample of the circuit's gates, and the value is the
+    step's bytes (as the GPU arm counts them) times the fraction of the
+    circuit's gates applied per second, i.e. the same effective GB/s a GPU
+    run at the oracle's gate rate would report."""
     if rank != 0:
         return
     import numpy as np
 
     import oracle
+    import paper_2608_09733_gb300 as sv
+    from paper_2608_09733_gb300 import build as _build
     from workloads import fused_layered_u3_cz
     n = args.n
+    amp = 8 if args.dtype == "c64" else 16
     gates = fused_layered_u3_cz(n, args.layers, seed=0)
+    # the plan's block and pass counts name the workload; the host planner
+    # runs no kernel
+    _build.build()
+    sv.load()
+    nblocks, npasses, _ = sv.sv_plan_info(n, sv.SV_C64 if args.dtype == "c64" else sv.SV_C128, sv.Gates(gates),
+                                          fuse_max_k=args.fuse, block_mode=args.block_mode,
+                                          ops_per_pass=args.ops_per_pass, tile_qubits=args.tile_qubits)
     sample = args.cpu_sample_gates or (4 if n >= 28 else 59)
     psi = np.zeros(2 ** n, dtype=np.complex128)
     psi[0] = 1.0
@@ -188,20 +222,19 @@ def run_reference(args, ws, rank):
         if s >= args.warmup:
             t_steps.append(t1 - t0)
     t = sum(t_steps)
-    # the oracle makes one pass per gate over a complex128 state (read + write)
-    bytes_ = args.steps * sample * 2 * (2 ** n) * 16
-    value = bytes_ / t / 1e9
+    gates_per_s = args.steps * sample / t
+    value = gates_per_s * step_bytes(n, npasses, amp) / len(gates) / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic",
-            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers_%s" % (n, args.layers, args.dtype),
-                       "n_qubits": n, "layers": args.layers, "gates": len(gates), "gates_per_step": sample,
-                       "parallelism": "single"},
-            "gates_per_s": args.steps * sample / t,
+            "data": "synthetic", "config": step_config(args, n, len(gates), nblocks, npasses, amp),
+            "gates_per_s": gates_per_s,
+            "oracle_traffic_gbs": args.steps * sample * 2 * (2 ** n) * 16 / t / 1e9,
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.n_threads(), "kind": "oracle",
                              "sample": "%d consecutive gates of the %d-gate circuit per step on a %d-qubit "
-                                       "complex128 state, one pass per gate" % (sample, len(gates), n)},
+                                       "complex128 state, one pass per gate; value = the step's bytes x the "
+                                       "fraction of the circuit's gates applied per second" %
+                                       (sample, len(gates), n)},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -214,8 +247,10 @@ def _oracle_inplace(oracle, n, gates, psi):
     return psi
 
 
-def cpu_baseline_sample(n, gates, sample_gates, plan_bytes_per_gate_gpu):
-    """The oracle on the host cores: a bounded sample of the same workload."""
+def cpu_baseline_sample(n, gates, sample_gates, bytes_per_step):
+    """The oracle on the host cores: a bounded sample of the same workload,
+    reported in the metric's unit (the step's bytes times the fraction of the
+    circuit's gates applied per second)."""
     import numpy as np
 
     import oracle
@@ -230,11 +265,13 @@ def cpu_baseline_sample(n, gates, sample_gates, plan_bytes_per_gate_gpu):
     t0 = time.perf_counter()
     _oracle_inplace(oracle, n, gates[1:1 + sample_gates], psi)
     t = time.perf_counter() - t0
-    bytes_ = sample_gates * 2 * (2 ** n) * 16
-    return {"value": bytes_ / t / 1e9, "unit": "GB/s", "cores": oracle.n_threads(), "kind": "oracle",
-            "gates_per_s": sample_gates / t,
+    gates_per_s = sample_gates / t
+    return {"value": gates_per_s * bytes_per_step / len(gates) / 1e9, "unit": "GB/s", "cores": oracle.n_threads(),
+            "kind": "oracle", "gates_per_s": gates_per_s,
+            "oracle_traffic_gbs": sample_gates * 2 * (2 ** n) * 16 / t / 1e9,
             "sample": "gates 1..%d of the %d-gate circuit on a %d-qubit complex128 state, one pass per gate "
-                      "(%.1f s)" % (sample_gates, len(gates), n, t)}
+                      "(%.1f s); value = the step's bytes x the fraction of the circuit's gates applied per "
+                      "second" % (sample_gates, len(gates), n, t)}
 
 
 def _mem_available_gb():
@@ -746,7 +783,7 @@ def main():
     # the circuit's pass programs were compiled to their own kernels on its
     # second run (a warm-up step); the timed steps launch those
     jit = sv.sv_jit_info()
-    bytes_step = (2 * npasses + 2) * (2 ** n) * amp  # passes r+w, init write, read-out read
+    bytes_step = step_bytes(n, npasses, amp)  # passes r+w, init write, read-out read
     value = job_rate(bytes_step, args.steps, ws, ms) / 1e9
     gates_per_s = job_rate(len(gates), args.steps, ws, ms)
     peaks, peak_src = measured_peaks()
@@ -801,7 +838,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(n, gates, args.cpu_sample_gates or 24, None)
+        cpu = cpu_baseline_sample(n, gates, args.cpu_sample_gates or 24, bytes_step)
 
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras and n == 30 and args.dtype == "c64":
@@ -814,11 +851,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": "fused_layered_u3_cz_%dq_%dlayers_%s" % (n, args.layers, args.dtype),
-                       "n_qubits": n, "layers": args.layers, "gates": len(gates), "fuse_max_k": args.fuse,
-                       "block_mode": args.block_mode, "fused_blocks": nblocks, "passes_per_step": npasses,
-                       "l2": "inputs larger than L2 (state %.1f GiB)" % ((2 ** n) * amp / 2 ** 30),
-                       "parallelism": "replicas" if ws > 1 else "single"},
+            "config": dict(step_config(args, n, len(gates), nblocks, npasses, amp),
+                           parallelism="replicas" if ws > 1 else "single"),
             "gates_per_s": gates_per_s,
             "pct_of_hbm_peak": 100.0 * value / ws / peak,
             "roofline": {"bound": "hbm", "kernel": kernel, "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
