@@ -501,8 +501,9 @@ sv_status sv_jit_info(int* mode, int* available, long long* compiled, long long*
 /* Plans a circuit as sv_apply_circuit_ex would and generates the kernel source
  * of every pass that would run compiled (*n_sources); with compile != 0 also
  * compiles each for sm_<arch>a (arch e.g. 103) and counts successes in
- * *n_compiled.  Needs no device.  text (host, text_cap bytes) receives the
- * first compile error, else the first source.  SV_ERR_UNSUPPORTED if compile
+ * *n_compiled.  Needs no device.  text (host, text_cap bytes, NUL-terminated,
+ * truncated to fit) receives the first compile error, else every source, each
+ * followed by a line "// ----".  SV_ERR_UNSUPPORTED if compile
  * is asked for and NVRTC is missing. */
 sv_status sv_jit_check(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
                        size_t n_param_values, const sv_exec_opts* opts, int compile, int arch, int* n_sources,

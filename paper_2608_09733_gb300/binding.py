@@ -470,14 +470,16 @@ def sv_jit_check(n: int, dtype: int, gates, param_values=None, fuse_max_k: int =
                  arch: int = 103, block_mode: int = 0, ops_per_pass: int = 0, tile_qubits: int = 0):
     """(sources, compiled, text): the passes of a circuit that would run as
     compiled kernels, how many compiled for sm_<arch>a (no device needed),
-    and the first compile error or else the first source."""
+    and the first compile error or else every source (each followed by a
+    "// ----" line)."""
     g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     o = _opts(fuse_max_k, block_mode, ops_per_pass, tile_qubits)
     ns, nc = ctypes.c_int(), ctypes.c_int()
-    buf = ctypes.create_string_buffer(1 << 20)
+    cap = 1 << 23
+    buf = ctypes.create_string_buffer(cap)
     _check(load().sv_jit_check(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), 1 if compile else 0, arch,
-                               ctypes.byref(ns), ctypes.byref(nc), buf, 1 << 20))
+                               ctypes.byref(ns), ctypes.byref(nc), buf, cap))
     return ns.value, nc.value, buf.value.decode(errors="replace")
 
 

@@ -208,7 +208,7 @@ cudaError_t jit_launch(const JitKernel* k, void* state, const void* map, const v
 // without a device.
 template <typename R>
 void jit_check_programs(const std::vector<SweepProgram<R>>& progs, bool compile, int arch, int* n_sources,
-                        int* n_compiled, std::string* first_error, std::string* first_source);
+                        int* n_compiled, std::string* first_error, std::string* sources);
 void jit_stats(long long* compiled, long long* failed, long long* launches, double* compile_seconds,
                std::string* last_error);
 bool jit_available(std::string* why);
