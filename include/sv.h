@@ -508,6 +508,18 @@ sv_status sv_jit_info(int* mode, int* available, long long* compiled, long long*
 sv_status sv_jit_check(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, const double* param_values,
                        size_t n_param_values, const sv_exec_opts* opts, int compile, int arch, int* n_sources,
                        int* n_compiled, char* text, size_t text_cap);
+/* The adjoint's batched passes (sv_adjoint_grad and the calls that share its
+ * sweeps) are compiled the same way, per circuit template: a template's calls
+ * are counted by its structure (gates without their angles, checkpoint
+ * interval and state size), and on the call the mode names every
+ * batched program of the call is compiled and its kernel launched in place
+ * of the interpreting one (bit-identical gradients and values).
+ * sv_jit_check_adjoint writes (and with compile != 0 compiles for sm_<arch>a)
+ * the distinct kernels of a template's forward and reverse passes without a
+ * device, as sv_jit_check; n_params bounds the gates' parameter slots. */
+sv_status sv_jit_check_adjoint(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates, int n_params,
+                               int checkpoint_every, int compile, int arch, int* n_sources, int* n_compiled,
+                               char* text, size_t text_cap);
 
 #ifdef __cplusplus
 }

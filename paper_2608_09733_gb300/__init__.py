@@ -36,6 +36,7 @@ from .binding import (  # noqa: F401
     sv_jit_set_mode,
     sv_jit_info,
     sv_jit_check,
+    sv_jit_check_adjoint,
     sv_run_host,
     sv_run_batch_small,
     sv_sample,

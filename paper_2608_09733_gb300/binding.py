@@ -39,7 +39,7 @@ EXPORTS = ["sv_version", "sv_last_error", "sv_init_basis", "sv_apply_circuit", "
            "sv_expect_z_all_noalloc", "sv_emulate_apply", "sv_probabilities", "sv_sample", "sv_adjoint_grad_rows",
            "sv_batch_expect_z", "sv_adjoint_grad_ex", "sv_adjoint_grad_device", "sv_batch_expect_z_device",
            "sv_small_session_start", "sv_small_session_submit", "sv_small_session_poll", "sv_small_session_stop",
-           "sv_jit_set_mode", "sv_jit_info", "sv_jit_check"]
+           "sv_jit_set_mode", "sv_jit_info", "sv_jit_check", "sv_jit_check_adjoint"]
 
 
 class SvError(RuntimeError):
@@ -139,6 +139,7 @@ def load():
                              ctypes.c_char_p, sz], ci),
             "sv_jit_check": ([ci, ci, P(SvGate), sz, P(cd), sz, P(SvExecOpts), ci, ci, P(ci), P(ci), ctypes.c_char_p,
                               sz], ci),
+            "sv_jit_check_adjoint": ([ci, ci, P(SvGate), sz, ci, ci, ci, ci, P(ci), P(ci), ctypes.c_char_p, sz], ci),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -480,6 +481,21 @@ def sv_jit_check(n: int, dtype: int, gates, param_values=None, fuse_max_k: int =
     buf = ctypes.create_string_buffer(cap)
     _check(load().sv_jit_check(n, dtype, g.arr, g.n, pp, npv, ctypes.byref(o), 1 if compile else 0, arch,
                                ctypes.byref(ns), ctypes.byref(nc), buf, cap))
+    return ns.value, nc.value, buf.value.decode(errors="replace")
+
+
+def sv_jit_check_adjoint(n: int, dtype: int, gates, n_params: int, checkpoint_every: int = 0, compile: bool = True,
+                         arch: int = 103):
+    """(sources, compiled, text) for the batched forward and reverse passes of
+    an adjoint template: the distinct kernels written, how many compiled for
+    sm_<arch>a (no device needed), and the first compile error or else every
+    source."""
+    g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
+    ns, nc = ctypes.c_int(), ctypes.c_int()
+    cap = 1 << 23
+    buf = ctypes.create_string_buffer(cap)
+    _check(load().sv_jit_check_adjoint(n, dtype, g.arr, g.n, int(n_params), int(checkpoint_every),
+                                       1 if compile else 0, arch, ctypes.byref(ns), ctypes.byref(nc), buf, cap))
     return ns.value, nc.value, buf.value.decode(errors="replace")
 
 

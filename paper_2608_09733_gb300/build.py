@@ -26,7 +26,7 @@ SOURCES = ["sv_plan.cpp", "sv_program.cpp", "sv_api.cpp", "sv_adjoint_host.cpp",
 # Device headers the run-time compiled pass kernels include (sv_jit.cpp): their
 # text is embedded in the library, so a kernel compiled at run time is built
 # from the same code as the library's own pass kernel.
-JIT_HEADERS = ["sv_prog_layout.h", "sv_pass_ops.cuh", "sv_tma_pass.cuh"]
+JIT_HEADERS = ["sv_prog_layout.h", "sv_pass_ops.cuh", "sv_tma_pass.cuh", "sv_batch_layout.h", "sv_batch_ops.cuh"]
 HEADERS = ["sv_internal.h", "sv_adjoint.h"] + JIT_HEADERS
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

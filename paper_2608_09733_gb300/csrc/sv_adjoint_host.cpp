@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <memory>
 
 #include "sv_adjoint.h"
@@ -119,6 +121,82 @@ bool expand_gate(const sv_gate& g, std::vector<sv_gate>& out) {
   out.push_back(ry);
   for (int k = 3; k >= 0; k--) out.push_back(perm[k]);
   return true;
+}
+
+// A circuit template lowered for the adjoint: gate i becomes ag[start[i]] ..
+// ag[start[i+1]-1] (one gate, or the nine of a double excitation); npg
+// parameterised gates.  Segments and checkpoints count the caller's gates.
+struct AdjTemplate {
+  std::vector<size_t> start;
+  std::vector<AGate> ag;
+  int npg = 0;
+};
+
+AdjTemplate lower_template(const sv_gate* gates, size_t ng) {
+  AdjTemplate T;
+  // ---- lower the template: gate i becomes ag[start[i]] .. ag[start[i+1]-1]
+  // (one gate, or the nine of a double excitation); segments and checkpoints
+  // count the caller's gates
+  std::vector<sv_gate> eg;
+  std::vector<size_t>& start = T.start;
+  start.assign(ng + 1, 0);
+  eg.reserve(ng);
+  for (size_t i = 0; i < ng; i++) {
+    start[i] = eg.size();
+    if (!expand_gate(gates[i], eg))
+      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) + ": a double excitation in the adjoint takes at most " +
+                                   std::to_string(SV_MAX_CONTROLS - 3) + " controls");
+  }
+  start[ng] = eg.size();
+  std::vector<AGate>& ag = T.ag;
+  ag.resize(eg.size());
+  int& npg = T.npg;
+  npg = 0;
+  for (size_t i = 0; i < eg.size(); i++) {
+    const sv_gate& g = eg[i];
+    ag[i].rec = g;
+    bool any_slot = false;
+    const int nang = g.type == SV_GATE_U3 ? 3 : g.type == SV_GATE_U2 ? 2 : is_rotation(g.type) ? 1 : 0;
+    for (int a = 0; a < nang; a++)
+      if (g.param_slot[a] >= 0) any_slot = true;
+    const size_t src = (size_t)(std::upper_bound(start.begin(), start.end(), i) - start.begin()) - 1;
+    if (g.n_targets > 2)
+      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(src) + ": the adjoint path takes gates of <= 2 targets "
+                                                               "(double excitations aside)");
+    AGate& a = ag[i];
+    if (any_slot) {
+      if (!is_rotation(g.type) || g.param_slot[0] < 0)
+        fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(src) +
+                                     ": a parameterised gate needs a generator, exp(-i theta G / 2) "
+                                     "(RX, RY, RZ, P, RXX, RYY, RZZ, EXC1, EXC2)");
+      a.param = true;
+      a.slot = g.param_slot[0];
+      a.pidx = npg++;
+      a.gen = generator_of(g.type);
+      LOp& op = a.op;
+      op.k = g.n_targets;
+      for (int t = 0; t < op.k; t++) op.q[t] = g.targets[t];
+      op.nc = g.n_controls;
+      for (int c = 0; c < op.nc; c++) {
+        op.c[c] = g.controls[c];
+        op.cs[c] = ((g.control_zero_mask >> c) & 1u) ? 0 : 1;
+      }
+      op.kind = rotation_is_diagonal(g.type) ? OPK_DIAG : OPK_DENSE;
+      op.touch = 0;
+      uint64_t tm = 0;
+      for (int t = 0; t < op.k; t++) tm |= 1ull << op.q[t];
+      for (int c = 0; c < op.nc; c++) op.touch |= 1ull << op.c[c];
+      op.touch |= tm;
+      op.need = op.kind == OPK_DIAG ? 0 : tm;
+      op.m.assign(op.kind == OPK_DIAG ? (1 << op.k) : (1 << (2 * op.k)), 0.0);  // sizes the pool use
+    } else {
+      a.op = lower_gate(g, nullptr, (int)src);
+      if (a.op.kind == OPK_REAL) a.op.kind = OPK_DENSE;
+    }
+    a.op.first_gate = (int)src;
+  }
+
+  return T;
 }
 
 template <typename R>
@@ -288,6 +366,103 @@ void fill_program(const std::vector<AGate>& ag, const std::vector<int>& order, c
   P.h.nphases = nph;
 }
 
+// The batched programs of gates [g0, g1) of a template, one per pass over the
+// batch: applied in order (forward), or un-applied in reverse order with
+// their gradient terms (reverse); each(prog) is called for each in turn (prog
+// is rewritten for the next).
+template <typename R, typename F>
+void segment_programs(const AdjTemplate& T, size_t g0, size_t g1, bool reverse, int n, int batch, int tile_q,
+                      int low_q, BatchProgram<R>& prog, F&& each) {
+  std::vector<int> order;
+  std::vector<LOp> ops;
+  if (!reverse) {
+    for (size_t i = T.start[g0]; i < T.start[g1]; i++) {
+      order.push_back((int)i);
+      ops.push_back(T.ag[i].op);
+    }
+  } else {
+    for (size_t i = T.start[g1]; i-- > T.start[g0];) {
+      order.push_back((int)i);
+      ops.push_back(T.ag[i].op);
+    }
+  }
+  std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, BatchProgram<R>::kPool / 2, 64);
+  for (const Sweep& sw : sws) {
+    fill_program<R>(T.ag, order, sw, n, batch, T.npg, reverse, prog);
+    each(prog);
+  }
+}
+
+// Tile width of the batched sweeps: 2^12 (complex64) or 2^11 (complex128)
+// amplitudes: psi and lambda tiles fit shared memory twice over, and the
+// register phases hold 16 amplitudes per thread with 256 threads.
+int adjoint_tile_q(sv_dtype dtype) { return dtype == SV_C64 ? 12 : 11; }
+
+// Every batched program of a call: forward segments of c gates, then (with
+// reverse) the reverse segments; each(prog, rev).
+template <typename R, typename F>
+void all_programs(const AdjTemplate& T, size_t ng, int c, bool reverse, int n, sv_dtype dtype, int batch,
+                  BatchProgram<R>& prog, F&& each) {
+  const int tile_q = adjoint_tile_q(dtype), low_q = low_qubits_for(dtype);
+  for (size_t a = 0; a < ng; a += c)
+    segment_programs<R>(T, a, std::min(ng, a + c), false, n, batch, tile_q, low_q, prog,
+                        [&](const BatchProgram<R>& P) { each(P, false); });
+  if (!reverse) return;
+  const int nseg = ng ? (int)((ng + c - 1) / c) : 0;
+  for (int seg = nseg - 1; seg >= 0; seg--) {
+    const size_t g0 = (size_t)seg * c, g1 = std::min(ng, g0 + c);
+    segment_programs<R>(T, g0, g1, true, n, batch, tile_q, low_q, prog,
+                        [&](const BatchProgram<R>& P) { each(P, true); });
+  }
+}
+
+// Compiled batched kernels for a template: a template's calls are counted by
+// its structure (gates without their angles, checkpoint interval, state size);
+// on the call jit_mode() names (the second, or the first) every program of
+// the call is written out and compiled, in parallel, and later launches find
+// their kernels by program.  Returns whether launches should look them up.
+std::mutex g_adj_jit_mu;
+std::map<std::string, std::pair<int, int>> g_adj_jit;  // key -> (calls, parts compiled: 1 forward, 2 reverse)
+
+template <typename R>
+bool adjoint_jit(const AdjTemplate& T, const sv_gate* gates, size_t ng, int n, sv_dtype dtype, int batch, int c,
+                 bool reverse) {
+  const int mode = jit_mode();
+  if (mode == 0) return false;
+  std::string key;
+  const int32_t hdr[3] = {n, (int32_t)dtype, c};  // the batch size changes no kernel
+  key.append((const char*)hdr, sizeof(hdr));
+  for (size_t i = 0; i < ng; i++) {
+    sv_gate g = gates[i];
+    g.matrix = nullptr;
+    for (double& a : g.params) a = 0.0;
+    key.append((const char*)&g, sizeof(g));
+  }
+  const int need = reverse ? 3 : 1;
+  bool compile = false;
+  {
+    std::lock_guard<std::mutex> lk(g_adj_jit_mu);
+    auto& e = g_adj_jit[key];
+    e.first++;
+    if (e.first < (mode == 2 ? 1 : 2)) return false;
+    compile = (e.second & need) != need;
+    e.second |= need;
+  }
+  if (compile) {
+    std::vector<std::unique_ptr<BatchProgram<R>>> keep;
+    std::vector<const BatchProgram<R>*> progs;
+    std::vector<char> rev;
+    std::unique_ptr<BatchProgram<R>> scratch(new BatchProgram<R>());
+    all_programs<R>(T, ng, c, reverse, n, dtype, batch, *scratch, [&](const BatchProgram<R>& P, bool r) {
+      keep.emplace_back(new BatchProgram<R>(P));
+      progs.push_back(keep.back().get());
+      rev.push_back(r ? 1 : 0);
+    });
+    jit_batch_prepare<R>(progs, rev);
+  }
+  return true;
+}
+
 template <typename R>
 // With row_coeffs (host, batch x nterms) state b uses H_b = sum_j c_{b,j} P_j.
 // With out_z (host, batch x (n + 1)) only the forward pass runs and
@@ -303,64 +478,9 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
                  const sv_pauli_term* terms, size_t nterms, int ckpt, int stored, double* out_grad,
                  double* out_value, const double* row_coeffs, double* out_z, cudaStream_t stream, bool dev = false,
                  bool values_only = false) {
-  // ---- lower the template: gate i becomes ag[start[i]] .. ag[start[i+1]-1]
-  // (one gate, or the nine of a double excitation); segments and checkpoints
-  // count the caller's gates
-  std::vector<sv_gate> eg;
-  std::vector<size_t> start(ng + 1, 0);
-  eg.reserve(ng);
-  for (size_t i = 0; i < ng; i++) {
-    start[i] = eg.size();
-    if (!expand_gate(gates[i], eg))
-      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(i) + ": a double excitation in the adjoint takes at most " +
-                                   std::to_string(SV_MAX_CONTROLS - 3) + " controls");
-  }
-  start[ng] = eg.size();
-  std::vector<AGate> ag(eg.size());
-  int npg = 0;
-  for (size_t i = 0; i < eg.size(); i++) {
-    const sv_gate& g = eg[i];
-    ag[i].rec = g;
-    bool any_slot = false;
-    const int nang = g.type == SV_GATE_U3 ? 3 : g.type == SV_GATE_U2 ? 2 : is_rotation(g.type) ? 1 : 0;
-    for (int a = 0; a < nang; a++)
-      if (g.param_slot[a] >= 0) any_slot = true;
-    const size_t src = (size_t)(std::upper_bound(start.begin(), start.end(), i) - start.begin()) - 1;
-    if (g.n_targets > 2)
-      fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(src) + ": the adjoint path takes gates of <= 2 targets "
-                                                               "(double excitations aside)");
-    AGate& a = ag[i];
-    if (any_slot) {
-      if (!is_rotation(g.type) || g.param_slot[0] < 0)
-        fail(SV_ERR_UNSUPPORTED, "gate " + std::to_string(src) +
-                                     ": a parameterised gate needs a generator, exp(-i theta G / 2) "
-                                     "(RX, RY, RZ, P, RXX, RYY, RZZ, EXC1, EXC2)");
-      a.param = true;
-      a.slot = g.param_slot[0];
-      a.pidx = npg++;
-      a.gen = generator_of(g.type);
-      LOp& op = a.op;
-      op.k = g.n_targets;
-      for (int t = 0; t < op.k; t++) op.q[t] = g.targets[t];
-      op.nc = g.n_controls;
-      for (int c = 0; c < op.nc; c++) {
-        op.c[c] = g.controls[c];
-        op.cs[c] = ((g.control_zero_mask >> c) & 1u) ? 0 : 1;
-      }
-      op.kind = rotation_is_diagonal(g.type) ? OPK_DIAG : OPK_DENSE;
-      op.touch = 0;
-      uint64_t tm = 0;
-      for (int t = 0; t < op.k; t++) tm |= 1ull << op.q[t];
-      for (int c = 0; c < op.nc; c++) op.touch |= 1ull << op.c[c];
-      op.touch |= tm;
-      op.need = op.kind == OPK_DIAG ? 0 : tm;
-      op.m.assign(op.kind == OPK_DIAG ? (1 << op.k) : (1 << (2 * op.k)), 0.0);  // sizes the pool use
-    } else {
-      a.op = lower_gate(g, nullptr, (int)src);
-      if (a.op.kind == OPK_REAL) a.op.kind = OPK_DENSE;
-    }
-    a.op.first_gate = (int)src;
-  }
+  const AdjTemplate tpl = lower_template(gates, ng);
+  const std::vector<AGate>& ag = tpl.ag;
+  const int npg = tpl.npg;
 
   // ---- per-state tables of the parameterised gates (double, then narrowed)
   const size_t N = 1ull << n;
@@ -387,10 +507,7 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   // ---- device buffers (library-owned, per stream, grow-only)
   const int c = ckpt > 0 ? ckpt : (int)ng + 1;
   const int nck = ng > 0 ? (int)((ng - 1) / c) : 0;  // stored states after c, 2c, ... gates
-  // 2^12 (complex64) or 2^11 (complex128) amplitudes per tile: psi and lambda
-  // tiles fit shared memory twice over, and the register phases hold 16
-  // amplitudes per thread with 256 threads
-  const int tile_q = dtype == SV_C64 ? 12 : 11, low_q = low_qubits_for(dtype);
+  const int tile_q = adjoint_tile_q(dtype), low_q = low_qubits_for(dtype);
   const int m = std::min(n, tile_q);
   const int grid_x = batch_grid_x(n, m, batch);
   Cx<R>* psi = (Cx<R>*)scratch_buffer(stream, "adj_psi", sbytes);
@@ -427,27 +544,25 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   }
 
   std::unique_ptr<BatchProgram<R>> prog(new BatchProgram<R>());
-  const int pool_cap = BatchProgram<R>::kPool / 2;
   const double sweep_bytes_f = 2.0 * (double)sbytes, sweep_bytes_r = 4.0 * (double)sbytes;
+  // the programs' compiled kernels, from the call jit_mode() names on
+  const bool jit = adjoint_jit<R>(tpl, gates, ng, n, dtype, batch, c, !out_z && !values_only);
+  auto sweep = [&](const BatchProgram<R>& P, bool rev) {
+    const JitKernel* k = jit ? jit_batch_lookup<R>(P, rev) : nullptr;
+    Prof pr(stream, rev ? (k ? "batch_sweep_rev_jit" : "batch_sweep_rev") : (k ? "batch_sweep_fwd_jit" : "batch_sweep_fwd"),
+            rev ? sweep_bytes_r : sweep_bytes_f);
+    cuda_check(launch_batch_sweep<R>(psi, rev ? lam : nullptr, dtab, gscr, grid_x, P, rev, stream, k),
+               rev ? "reverse sweep" : "forward sweep");
+    pr.done();
+  };
 
   // ---- forward over gates [g0, g1) in segments of c, keeping the chosen
   // segment-start states when `keep`
   auto forward = [&](size_t g0, size_t g1, bool keep) {
     for (size_t a = g0; a < g1; a += c) {
       const size_t b = std::min(g1, a + c);
-      std::vector<int> order;
-      std::vector<LOp> ops;
-      for (size_t i = start[a]; i < start[b]; i++) {
-        order.push_back((int)i);
-        ops.push_back(ag[i].op);
-      }
-      std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, pool_cap, 64);
-      for (const Sweep& sw : sws) {
-        fill_program<R>(ag, order, sw, n, batch, npg, false, *prog);
-        Prof pr(stream, "batch_sweep_fwd", sweep_bytes_f);
-        cuda_check(launch_batch_sweep<R>(psi, nullptr, dtab, gscr, grid_x, *prog, false, stream), "forward sweep");
-        pr.done();
-      }
+      segment_programs<R>(tpl, a, b, false, n, batch, tile_q, low_q, *prog,
+                          [&](const BatchProgram<R>& P) { sweep(P, false); });
       const int j = (int)(b / c);  // boundary reached (state after j*c gates)
       if (keep && b % c == 0 && j >= 1 && j <= nck && slot_of[j] >= 0)
         cuda_check(cudaMemcpyAsync(ck + (size_t)slot_of[j] * N * batch, psi, sbytes, cudaMemcpyDeviceToDevice, stream),
@@ -509,19 +624,8 @@ void run_adjoint(int n, sv_dtype dtype, const sv_gate* gates, size_t ng, const d
   int nseg = ng ? (int)((ng + c - 1) / c) : 0;
   for (int seg = nseg - 1; seg >= 0; seg--) {
     size_t g0 = (size_t)seg * c, g1 = std::min(ng, g0 + c);
-    std::vector<int> order;
-    std::vector<LOp> ops;
-    for (size_t i = start[g1]; i-- > start[g0];) {
-      order.push_back((int)i);
-      ops.push_back(ag[i].op);
-    }
-    std::vector<Sweep> sws = schedule_sweeps(n, ops, tile_q, low_q, pool_cap, 64);
-    for (const Sweep& sw : sws) {
-      fill_program<R>(ag, order, sw, n, batch, npg, true, *prog);
-      Prof pr(stream, "batch_sweep_rev", sweep_bytes_r);
-      cuda_check(launch_batch_sweep<R>(psi, lam, dtab, gscr, grid_x, *prog, true, stream), "reverse sweep");
-      pr.done();
-    }
+    segment_programs<R>(tpl, g0, g1, true, n, batch, tile_q, low_q, *prog,
+                        [&](const BatchProgram<R>& P) { sweep(P, true); });
     if (seg >= 1 && seg <= nck) {  // psi is now psi after seg*c gates: re-anchor it
       if (slot_of[seg] >= 0) {
         cuda_check(cudaMemcpyAsync(psi, ck + (size_t)slot_of[seg] * N * batch, sbytes, cudaMemcpyDeviceToDevice,
@@ -623,6 +727,54 @@ void check_adjoint_args_dev(int n_qubits, sv_dtype dtype, const sv_gate* gates, 
 }
 
 }  // namespace
+
+namespace {
+
+template <typename R>
+void check_adjoint_kernels(const AdjTemplate& T, size_t ng, int c, int n, sv_dtype dtype, bool compile, int arch,
+                           int* n_sources, int* n_compiled, std::string* err, std::string* src) {
+  std::vector<std::unique_ptr<BatchProgram<R>>> keep;
+  std::vector<const BatchProgram<R>*> progs;
+  std::vector<char> rev;
+  std::unique_ptr<BatchProgram<R>> scratch(new BatchProgram<R>());
+  all_programs<R>(T, ng, c, true, n, dtype, 1, *scratch, [&](const BatchProgram<R>& P, bool r) {
+    keep.emplace_back(new BatchProgram<R>(P));
+    progs.push_back(keep.back().get());
+    rev.push_back(r ? 1 : 0);
+  });
+  jit_check_batch<R>(progs, rev, compile, arch, n_sources, n_compiled, err, src);
+}
+
+}  // namespace
+
+extern "C" sv_status sv_jit_check_adjoint(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
+                                          int n_params, int checkpoint_every, int compile, int arch, int* n_sources,
+                                          int* n_compiled, char* text, size_t text_cap) {
+  return guarded([&] {
+    if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_INVALID, "unknown dtype");
+    if (n_qubits < 1 || n_qubits > 30) fail(SV_ERR_INVALID, "n_qubits must be in 1..30 for the adjoint");
+    if (n_params < 0 || checkpoint_every < 0) fail(SV_ERR_INVALID, "n_params and checkpoint_every must be >= 0");
+    if (!n_sources || !n_compiled) fail(SV_ERR_INVALID, "NULL argument");
+    if (compile && (arch < 100 || arch > 200)) fail(SV_ERR_INVALID, "arch must be a compute capability such as 103");
+    if (compile && !jit_available(nullptr)) fail(SV_ERR_UNSUPPORTED, "the run-time compiler is not available");
+    validate_gates(n_qubits, gates, n_gates, (size_t)n_params);
+    const AdjTemplate T = lower_template(gates, n_gates);
+    const int c = checkpoint_every > 0 ? checkpoint_every : (int)n_gates + 1;
+    std::string err, src;
+    if (dtype == SV_C64)
+      check_adjoint_kernels<float>(T, n_gates, c, n_qubits, dtype, compile != 0, arch, n_sources, n_compiled, &err,
+                                   &src);
+    else
+      check_adjoint_kernels<double>(T, n_gates, c, n_qubits, dtype, compile != 0, arch, n_sources, n_compiled, &err,
+                                    &src);
+    if (text && text_cap) {
+      const std::string& m = err.empty() ? src : err;
+      const size_t k = std::min(m.size(), text_cap - 1);
+      std::memcpy(text, m.data(), k);
+      text[k] = '\0';
+    }
+  });
+}
 
 extern "C" sv_status sv_adjoint_grad(int n_qubits, sv_dtype dtype, const sv_gate* gates, size_t n_gates,
                                      const double* params, int batch, int n_params, const sv_pauli_term* terms,

@@ -33,8 +33,10 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
+#include "sv_adjoint.h"
 #include "sv_internal.h"
 #include "sv_jit_headers.inc"  // kJitHeaderNames / kJitHeaderTexts, written by build.py
 
@@ -284,6 +286,170 @@ template std::string jit_source<double>(const SweepProgram<double>&);
 
 namespace {
 
+// A BOp as an aggregate initializer, with the fields the tile code reads;
+// coef, gen, gidx and table (read once per CTA from the program in parameter
+// space) are left zero so that programs differing only there share a kernel.
+std::string bop_literal(const BOp& d) {
+  char b[512];
+  snprintf(b, sizeof(b),
+           "{%u, %u, {%u, %u}, {%u, %u}, {%u, %u}, {%u, %u}, 0, %u, %u, %u, %u, %u, 0x%xu, 0x%xu, 0x%xu, 0x%xu, "
+           "0x%llxull, 0x%llxull, 0, 0, 0, %u, %u}",
+           d.kind, d.k, d.pos[0], d.pos[1], d.spos[0], d.spos[1], d.gq[0], d.gq[1], d.rs[0], d.rs[1], d.dagger, d.grad,
+           d.gacc, d.rmask, d.rval, d.lmask, d.lval, d.tmask, d.tval, (unsigned long long)d.xmask,
+           (unsigned long long)d.xval, d.flags, d.soff);
+  return b;
+}
+
+// A register phase as an aggregate initializer (kind, register positions and
+// the count of thread positions: what the tile code reads).
+std::string phase_literal(const Phase& ph) {
+  std::string s = "{" + std::to_string(ph.kind) + ", 0, 0, " + std::to_string(ph.ntpos) + ", " +
+                  std::to_string(ph.nrp) + ", {";
+  for (int i = 0; i < kMaxRegQ; i++) s += (i ? ", " : "") + std::to_string(ph.rp[i]);
+  s += "}, {";
+  for (int i = 0; i < kMaxTileQ; i++) s += (i ? ", " : "") + std::to_string(ph.tpos[i]);
+  return s + "}}";
+}
+
+// The register-op call b_apply (sv_batch_ops.cuh) makes for op d, with its
+// dispatch decided here: the function and its template arguments.
+std::string batch_reg_call(const BOp& d, bool rev, const char* Rn) {
+  const char* RV = rev ? "true" : "false";
+  char b[256];
+  const bool grad = rev && d.grad;
+  const bool plain = d.rmask == 0 && d.rs[0] != 0xFF;
+  if (plain && d.k == 1 && (d.kind == OPK_DENSE || d.kind == OPK_REAL)) {
+    const bool real = d.flags & OPF_REALM;
+    const int gk = !grad ? 0 : (d.flags & OPF_GX) ? 1 : (d.flags & OPF_GY) ? 2 : 3;
+    if (gk != 3) {
+      const bool r = real && (gk == 2 || gk == 0);
+      snprintf(b, sizeof(b), "b_u1<%s, %d, %s, %s, %d>(p, l, op, M, acc);", Rn, d.rs[0] > 3 ? 3 : d.rs[0], RV,
+               r ? "true" : "false", gk);
+      return b;
+    }
+  }
+  if (plain && d.k == 1 && d.kind == OPK_DIAG) {
+    const bool gz = grad && (d.flags & OPF_GZ);
+    if (gz || !grad) {
+      snprintf(b, sizeof(b), "b_d1<%s, %d, %s, %s>(p, l, op, M, acc);", Rn, d.rs[0] > 3 ? 3 : d.rs[0], RV,
+               gz ? "true" : "false");
+      return b;
+    }
+  }
+  switch (d.kind) {
+    case OPK_DENSE:
+    case OPK_REAL:
+      if (d.k == 1) {
+        snprintf(b, sizeof(b), "b_dense1<%s, %d, %s>(p, l, op, M, G, acc);", Rn, d.rs[0] > 3 ? 3 : d.rs[0], RV);
+      } else {
+        int A = d.rs[0], B = d.rs[1];
+        const int code = A * 4 + B;  // the interpreter's pair switch: unlisted codes take (3, 2)
+        if (!(code == 1 || code == 2 || code == 3 || code == 4 || code == 6 || code == 7 || code == 8 || code == 9 ||
+              code == 11 || code == 12 || code == 13)) {
+          A = 3;
+          B = 2;
+        }
+        snprintf(b, sizeof(b), "b_dense2<%s, %d, %d, %s>(p, l, op, M, G, acc);", Rn, A, B, RV);
+      }
+      return b;
+    case OPK_ANTIDIAG:
+      snprintf(b, sizeof(b), "b_anti1<%s, %d, %s, %s>(p, l, op, M);", Rn, d.rs[0] > 3 ? 3 : d.rs[0], RV,
+               (d.flags & OPF_FLIP) ? "true" : "false");
+      return b;
+    case OPK_SWAP: {
+      const int a = d.rs[0] < d.rs[1] ? d.rs[0] : d.rs[1], c = d.rs[0] < d.rs[1] ? d.rs[1] : d.rs[0];
+      const int code = a * 4 + c;
+      const int A = (code == 1 || code == 2 || code == 3) ? 0 : (code == 6 || code == 7) ? 1 : 2;
+      const int B = code == 1 ? 1 : (code == 2 || code == 6) ? 2 : 3;
+      snprintf(b, sizeof(b), "b_swap<%s, %d, %d, %s>(p, l, op);", Rn, A, B, RV);
+      return b;
+    }
+    case OPK_DIAG:
+      snprintf(b, sizeof(b), "b_diag<%s, %s>(p, l, op, M, G, tb, base, acc);", Rn, RV);
+      return b;
+    default: return "";
+  }
+}
+
+}  // namespace
+
+// The kernel source of one batched adjoint program: every phase and op as a
+// constant, the same tile functions and tile loop as the interpreting kernel.
+template <typename R>
+std::string jit_batch_source(const BatchProgram<R>& P, bool rev) {
+  const BatchHeader& h = P.h;
+  const char* Rn = sizeof(R) == 4 ? "float" : "double";
+  const char* RV = rev ? "true" : "false";
+  Src o;
+  o.line("// batched %s program: %d phases, %d ops", rev ? "reverse" : "forward", h.nphases, h.nops);
+  o.line("#include \"sv_batch_ops.cuh\"");
+  o.line("namespace sv {");
+  o.line("struct JitBatchRunner {");
+  o.line("  __device__ __forceinline__ void operator()(Cx<%s>* sp, Cx<%s>* sl, int tsz, const Cx<%s>* scoef,", Rn, Rn,
+         Rn);
+  o.line("                                             uint64_t base, double (*gacc)[8], int warp, int lane) const {");
+  for (int p = 0; p < h.nphases; p++) {
+    const Phase& ph = P.ph[p];
+    if (ph.kind == PH_REG) {
+      o.line("  {  // phase %d", p);
+      o.line("    const Phase ph = %s;", phase_literal(ph).c_str());
+      o.line("    batch_reg_phase<%s, %s>(ph, sp, sl, [&](Cx<%s>(&p)[NR], Cx<%s>(&l)[NR], uint32_t tb, bool active) {",
+             Rn, RV, Rn, Rn);
+      for (int i = 0; i < ph.nops; i++) {
+        // batch_reg_op of the interpreting kernel, its dispatch and
+        // conditions decided here
+        const BOp& d = P.ops[ph.first + i];
+        const int dd = 1 << d.k;
+        std::string cond = "active";
+        char cb[160];
+        if (d.xmask) {
+          snprintf(cb, sizeof(cb), " && (base & 0x%llxull) == 0x%llxull", (unsigned long long)d.xmask,
+                   (unsigned long long)d.xval);
+          cond += cb;
+        }
+        if (d.tmask) {
+          snprintf(cb, sizeof(cb), " && (tb & 0x%xu) == 0x%xu", d.tmask, d.tval);
+          cond += cb;
+        }
+        o.line("      {  // op %d", ph.first + i);
+        o.line("        const BOp op = %s;", bop_literal(d).c_str());
+        o.line("        %s acc = %s(0);", Rn, Rn);
+        o.line("        if (%s) {", cond.c_str());
+        o.line("          const Cx<%s>* M = scoef + %u;", Rn, (unsigned)d.soff);
+        o.line("          const Cx<%s>* G = M + %d;", Rn, d.kind == OPK_DIAG ? dd : dd * dd);
+        o.line("          (void)G;");
+        o.line("          %s", batch_reg_call(d, rev, Rn).c_str());
+        o.line("        }");
+        if (rev && d.grad) o.line("        batch_grad_add<%s>(acc, gacc[%u], warp, lane);", Rn, (unsigned)d.gacc);
+        o.line("      }");
+      }
+      o.line("    });");
+      o.line("  }");
+    } else {
+      o.line("  {  // phase %d, in shared memory", p);
+      o.line("    const BOp op = %s;", bop_literal(P.ops[ph.first]).c_str());
+      o.line("    batch_smem_op<%s, %s>(op, sp, sl, tsz, scoef, base, gacc, warp, lane);", Rn, RV);
+      o.line("  }");
+    }
+    o.line("  __syncthreads();");
+  }
+  o.line("  }");
+  o.line("};");
+  o.line("}  // namespace sv");
+  o.line("extern \"C\" __global__ void __launch_bounds__(256, %d)", sizeof(R) == 4 ? 2 : 1);
+  o.line("k_batch_sweep_jit(sv::Cx<%s>* __restrict__ psi, sv::Cx<%s>* __restrict__ lam,", Rn, Rn);
+  o.line("                  const sv::Cx<%s>* __restrict__ table, double* __restrict__ gscratch,", Rn);
+  o.line("                  const __grid_constant__ sv::BatchProgram<%s> P) {", Rn);
+  o.line("  sv::batch_sweep_body<%s, %s>(psi, lam, table, gscratch, P, sv::JitBatchRunner{});", Rn, RV);
+  o.line("}");
+  return o.s;
+}
+
+template std::string jit_batch_source<float>(const BatchProgram<float>&, bool);
+template std::string jit_batch_source<double>(const BatchProgram<double>&, bool);
+
+namespace {
+
 // ---------------------------------------------------------------- NVRTC
 
 struct Nvrtc {
@@ -456,72 +622,189 @@ int jit_mode() {
 
 void jit_set_mode(int mode) { g_jit_mode.store(mode < 0 ? -1 : mode); }
 
-template <typename R>
-std::vector<const JitKernel*> jit_compile_programs(const std::vector<SweepProgram<R>>& progs) {
-  std::vector<const JitKernel*> out(progs.size(), nullptr);
-  if (sizeof(R) != 4 || !driver().ok || !nvrtc().ok) return out;
+namespace {
+
+// Kernels for the given sources (empty: none) on the current device, named
+// `name` in their modules: compiles, in parallel, the distinct sources the
+// cache lacks, then loads them.  NULL where a source is empty or failed.
+std::vector<const JitKernel*> kernels_for(const std::vector<std::string>& src, const char* name) {
+  std::vector<const JitKernel*> out(src.size(), nullptr);
+  if (!driver().ok || !nvrtc().ok) return out;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return out;
   }
   const int arch = device_arch(dev);
-  std::vector<std::string> src(progs.size());
   std::vector<const std::string*> todo;
-  std::vector<size_t> todo_idx;
   {
     std::lock_guard<std::mutex> lk(g_jit_mu);
     std::map<std::string, size_t> seen;
-    for (size_t i = 0; i < progs.size(); i++) {
-      src[i] = jit_source<R>(progs[i]);
+    for (size_t i = 0; i < src.size(); i++) {
       if (src[i].empty()) continue;
       auto it = g_jit_kernels.find({dev, src[i]});
       if (it != g_jit_kernels.end()) {
         out[i] = it->second.get();
         continue;
       }
-      if (seen.emplace(src[i], i).second) {
-        todo.push_back(&src[i]);
-        todo_idx.push_back(i);
-      }
+      if (seen.emplace(src[i], i).second) todo.push_back(&src[i]);
     }
   }
-  if (!todo.empty()) {
-    const auto t0 = std::chrono::steady_clock::now();
-    std::vector<std::vector<char>> bins;
-    std::vector<std::string> logs;
-    std::vector<char> ok;
-    compile_all(todo, arch, bins, logs, ok);
-    g_jit_compile_us += (long long)std::chrono::duration_cast<std::chrono::microseconds>(
-                            std::chrono::steady_clock::now() - t0)
-                            .count();
-    std::lock_guard<std::mutex> lk(g_jit_mu);
-    for (size_t t = 0; t < todo.size(); t++) {
-      if (!ok[t]) {
-        g_jit_failed++;
-        g_jit_last_error = logs[t].substr(0, 4000);
-        continue;
-      }
-      CUmodule mod = nullptr;
-      auto k = std::make_unique<JitKernel>();
-      if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS ||
-          driver().get(&k->fn, mod, "k_sweep_jit") != CUDA_SUCCESS) {
-        g_jit_failed++;
-        g_jit_last_error = "module load failed";
-        continue;
-      }
-      k->device = dev;
-      g_jit_compiled++;
-      g_jit_kernels[{dev, *todo[t]}] = std::move(k);
+  if (todo.empty()) return out;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<std::vector<char>> bins;
+  std::vector<std::string> logs;
+  std::vector<char> ok;
+  compile_all(todo, arch, bins, logs, ok);
+  g_jit_compile_us +=
+      (long long)std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  for (size_t t = 0; t < todo.size(); t++) {
+    if (!ok[t]) {
+      g_jit_failed++;
+      g_jit_last_error = logs[t].substr(0, 4000);
+      continue;
     }
-    for (size_t i = 0; i < progs.size(); i++) {
-      if (out[i] || src[i].empty()) continue;
-      auto it = g_jit_kernels.find({dev, src[i]});
-      if (it != g_jit_kernels.end()) out[i] = it->second.get();
+    CUmodule mod = nullptr;
+    auto k = std::make_unique<JitKernel>();
+    if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS || driver().get(&k->fn, mod, name) != CUDA_SUCCESS) {
+      g_jit_failed++;
+      g_jit_last_error = "module load failed";
+      continue;
     }
+    k->device = dev;
+    g_jit_compiled++;
+    g_jit_kernels[{dev, *todo[t]}] = std::move(k);
+  }
+  for (size_t i = 0; i < src.size(); i++) {
+    if (out[i] || src[i].empty()) continue;
+    auto it = g_jit_kernels.find({dev, src[i]});
+    if (it != g_jit_kernels.end()) out[i] = it->second.get();
   }
   return out;
 }
+
+// Batched programs: (device, direction, precision, the op and phase bytes) ->
+// kernel, so that a launch finds its kernel without writing the source.
+std::unordered_map<std::string, const JitKernel*> g_batch_kernels;
+
+template <typename R>
+std::string batch_key(const BatchProgram<R>& P, bool rev, int dev) {
+  std::string k;
+  const int32_t hdr[4] = {dev, rev ? 1 : 0, (int32_t)sizeof(R), P.h.nphases};
+  k.append((const char*)hdr, sizeof(hdr));
+  k.append((const char*)P.ops, sizeof(BOp) * (size_t)P.h.nops);
+  k.append((const char*)P.ph, sizeof(Phase) * (size_t)P.h.nphases);
+  return k;
+}
+
+}  // namespace
+
+template <typename R>
+std::vector<const JitKernel*> jit_compile_programs(const std::vector<SweepProgram<R>>& progs) {
+  std::vector<std::string> src(progs.size());
+  if (sizeof(R) == 4)
+    for (size_t i = 0; i < progs.size(); i++) src[i] = jit_source<R>(progs[i]);
+  return kernels_for(src, "k_sweep_jit");
+}
+
+template <typename R>
+void jit_batch_prepare(const std::vector<const BatchProgram<R>*>& progs, const std::vector<char>& rev) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  std::vector<std::string> src(progs.size()), keys(progs.size());
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    for (size_t i = 0; i < progs.size(); i++) {
+      keys[i] = batch_key<R>(*progs[i], rev[i] != 0, dev);
+      if (!g_batch_kernels.count(keys[i])) src[i] = jit_batch_source<R>(*progs[i], rev[i] != 0);
+    }
+  }
+  std::vector<const JitKernel*> k = kernels_for(src, "k_batch_sweep_jit");
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  for (size_t i = 0; i < progs.size(); i++)
+    if (k[i]) g_batch_kernels[keys[i]] = k[i];
+}
+
+template <typename R>
+const JitKernel* jit_batch_lookup(const BatchProgram<R>& P, bool rev) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const std::string key = batch_key<R>(P, rev, dev);
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  auto it = g_batch_kernels.find(key);
+  return it == g_batch_kernels.end() ? nullptr : it->second;
+}
+
+template void jit_batch_prepare<float>(const std::vector<const BatchProgram<float>*>&, const std::vector<char>&);
+template void jit_batch_prepare<double>(const std::vector<const BatchProgram<double>*>&, const std::vector<char>&);
+template const JitKernel* jit_batch_lookup<float>(const BatchProgram<float>&, bool);
+template const JitKernel* jit_batch_lookup<double>(const BatchProgram<double>&, bool);
+
+cudaError_t jit_batch_launch(const JitKernel* k, void* psi, void* lam, const void* table, double* gscratch,
+                             const void* prog, unsigned grid_x, unsigned batch, size_t smem, cudaStream_t stream) {
+  const Driver& d = driver();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!k || !k->fn || k->device != dev) return cudaErrorInvalidDeviceFunction;
+  JitKernel* kk = const_cast<JitKernel*>(k);
+  if (smem > kk->smem_configured) {
+    if (smem > 48 * 1024 &&
+        d.attr(kk->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+      return cudaErrorInvalidConfiguration;
+    kk->smem_configured = smem;
+  }
+  void* a0 = psi;
+  void* a1 = lam;
+  const void* a2 = table;
+  double* a3 = gscratch;
+  void* args[] = {&a0, &a1, &a2, &a3, const_cast<void*>(prog)};
+  const CUresult r = d.launch(kk->fn, grid_x, batch, 1, 256, 1, 1, (unsigned)smem, (CUstream)stream, args, nullptr);
+  if (r != CUDA_SUCCESS) return cudaErrorLaunchFailure;
+  g_jit_launches++;
+  return cudaSuccess;
+}
+
+// Writes (and with compile, compiles) the kernels of the given batched
+// programs without a device.
+template <typename R>
+void jit_check_batch(const std::vector<const BatchProgram<R>*>& progs, const std::vector<char>& rev, bool compile,
+                     int arch, int* n_sources, int* n_compiled, std::string* first_error, std::string* sources) {
+  std::vector<std::string> src;
+  std::map<std::string, int> seen;
+  for (size_t i = 0; i < progs.size(); i++) {
+    std::string s = jit_batch_source<R>(*progs[i], rev[i] != 0);
+    if (seen.emplace(s, 1).second) src.push_back(std::move(s));
+  }
+  *n_sources = (int)src.size();
+  *n_compiled = 0;
+  if (sources)
+    for (const std::string& s : src) *sources += s + "// ----\n";
+  if (!compile || src.empty()) return;
+  std::vector<const std::string*> ptrs;
+  for (auto& s : src) ptrs.push_back(&s);
+  std::vector<std::vector<char>> bins;
+  std::vector<std::string> logs;
+  std::vector<char> ok;
+  compile_all(ptrs, arch, bins, logs, ok);
+  for (size_t i = 0; i < src.size(); i++) {
+    if (ok[i])
+      (*n_compiled)++;
+    else if (first_error && first_error->empty())
+      *first_error = logs[i].empty() ? std::string("compile failed") : logs[i];
+  }
+}
+
+template void jit_check_batch<float>(const std::vector<const BatchProgram<float>*>&, const std::vector<char>&, bool,
+                                     int, int*, int*, std::string*, std::string*);
+template void jit_check_batch<double>(const std::vector<const BatchProgram<double>*>&, const std::vector<char>&,
+                                      bool, int, int*, int*, std::string*, std::string*);
 
 template std::vector<const JitKernel*> jit_compile_programs<float>(const std::vector<SweepProgram<float>>&);
 template std::vector<const JitKernel*> jit_compile_programs<double>(const std::vector<SweepProgram<double>>&);

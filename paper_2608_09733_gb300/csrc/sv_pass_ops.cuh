@@ -13,8 +13,8 @@
 namespace sv {
 
 template <typename R>
-__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {  // rounding fixed: one product, one fma per part
+  return {fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> cfma(Cx<R> a, Cx<R> b, Cx<R> acc) {  // acc + a*b

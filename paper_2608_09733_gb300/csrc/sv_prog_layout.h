@@ -11,6 +11,7 @@ typedef unsigned long long uint64_t;
 typedef int int32_t;
 typedef signed char int8_t;
 typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
 #else
 #include <stdint.h>
 #endif

@@ -72,3 +72,31 @@ def test_mode_validation(svlib):
     assert B.sv_jit_info()["mode"] == 0
     B.sv_jit_set_mode(-1)
     assert B.sv_jit_info()["mode"] in (0, 1, 2)
+
+
+def test_adjoint_template_kernels_compile(svlib):
+    """The batched forward and reverse passes of the 20-qubit HEA template
+    (checkpoints every two layers) and of a circuit with every generator
+    family, controls, bit flips and swaps, and a 3-qubit template (tiles too
+    small for register phases: shared-memory phases) all compile."""
+    _nvrtc_or_skip()
+    from workloads import Gate, hea_ring
+    n, layers = 20, 10
+    ns, nc, text = B.sv_jit_check_adjoint(n, B.SV_C64, hea_ring(n, layers), 2 * n * layers,
+                                          checkpoint_every=6 * n, compile=True)
+    assert ns > 0 and nc == ns, text[:2000]
+    assert "batch_sweep_body<float, true>" in text and "batch_grad_add<float>" in text
+    gates = [Gate("h", [q]) for q in range(6)]
+    for i, f in enumerate(["rx", "ry", "rz", "p", "rxx", "ryy", "rzz", "exc1"]):
+        k = 2 if f in ("rxx", "ryy", "rzz", "exc1") else 1
+        t = [i % 6, (i + 1) % 6][:k]
+        c = [(i + 3) % 6] if i % 2 else []
+        gates.append(Gate(f, t, c, [i % 2] * len(c), params=[0.0], slots=[i % 3]))
+        gates.append(Gate("x", [(i + 2) % 6], [(i + 4) % 6]))
+        gates.append(Gate("swap", [i % 6, (i + 5) % 6]))
+    gates.append(Gate("exc2", [0, 1, 2, 3], params=[0.0], slots=[1]))
+    for dt in (B.SV_C64, B.SV_C128):
+        ns, nc, text = B.sv_jit_check_adjoint(6, dt, gates, 3, checkpoint_every=7, compile=True)
+        assert ns > 0 and nc == ns, text[:2000]
+    ns, nc, text = B.sv_jit_check_adjoint(3, B.SV_C64, hea_ring(3, 2), 12, compile=True)
+    assert ns > 0 and nc == ns and "in shared memory" in text, text[:2000]
