@@ -57,7 +57,8 @@ def _stamp(extra=()) -> str:
 
 # Sources that decide what the pass kernel does (the kernel, the program
 # builder, the planner and the shared structures).
-SWEEP_SOURCES = ["sv_sweep.cu", "sv_program.cpp", "sv_plan.cpp", "sv_internal.h", "sv_jit.cpp"] + JIT_HEADERS
+SWEEP_SOURCES = ["sv_sweep.cu", "sv_program.cpp", "sv_plan.cpp", "sv_internal.h", "sv_jit.cpp", "sv_prog_layout.h",
+                 "sv_pass_ops.cuh", "sv_tma_pass.cuh"]
 
 
 def sweep_stamp() -> str:
