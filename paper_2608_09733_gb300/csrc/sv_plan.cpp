@@ -45,14 +45,34 @@ int popc(uint64_t x) { return __builtin_popcountll(x); }
 #ifndef SV_C64_SMALL_TILE_MIN_N
 #define SV_C64_SMALL_TILE_MIN_N 26
 #endif
+#ifndef SV_C64_TMA_MIN_N
+#define SV_C64_TMA_MIN_N 21  // 2^9 tiles of 12 qubits: the TMA pass
+#endif
 // complex64 states of 2^26 amplitudes and more run 12-qubit tiles: four
 // 128-thread CTAs per SM instead of two 256-thread ones hide the tile copies
 // and barriers better (measured 6-8 % less time per step at 26-30 qubits on
-// layered circuits, despite about 15 % more passes); smaller states keep the
-// wider tile, whose fewer passes matter more there.
+// layered circuits, despite about 15 % more passes).  States of 21 to 25
+// qubits take 12-qubit tiles too when their passes can run compiled (the
+// compiled kernels are on and NVRTC is present): the TMA pass on 12-qubit
+// tiles with compiled programs beats the interpreted pass on 13-qubit tiles
+// by 1.27x at 22 and 24 qubits and 1.5x at 25 on layered circuits, with
+// 10-15 % more passes, and interpreted (a circuit's first run) it is no
+// slower.  While a serving session is live the TMA pass is off, and mid-size
+// states keep the wider tile, whose fewer passes matter more there (the CNOT
+// ladders of serving circuits take up to twice the passes on 12 qubits);
+// smaller states keep it as well.
 int tile_qubits_for(sv_dtype dtype, int n) {
   if (dtype != SV_C64) return 11;
-  return n >= SV_C64_SMALL_TILE_MIN_N ? SV_C64_TILE_Q - 1 : SV_C64_TILE_Q;
+  if (n >= SV_C64_SMALL_TILE_MIN_N) return SV_C64_TILE_Q - 1;
+  if (n >= SV_C64_TMA_MIN_N && jit_mode() != 0 && jit_available(nullptr)) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {  // no device here: plan as if none were live
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (!session_live(dev)) return SV_C64_TILE_Q - 1;
+  }
+  return SV_C64_TILE_Q;
 }
 #ifndef SV_RQ5_MIN_M
 #define SV_RQ5_MIN_M 12  // tiles of at least this many qubits use five register qubits

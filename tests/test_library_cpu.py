@@ -69,7 +69,9 @@ def test_pass_counts_of_layered_circuits(svlib, n, depth):
     are the whole-gate schedule's (or fewer)."""
     from workloads import serving_circuit
     whole = {(16, 20): 8, (20, 30): 57, (24, 40): 91}[(n, depth)]
-    _, ns, _ = B.sv_plan_info(n, B.SV_C64, serving_circuit(n, depth, 3), fuse_max_k=5)
+    # (serving states of 21 to 25 qubits run 13-qubit tiles: the TMA pass is
+    # off while a serving session is live)
+    _, ns, _ = B.sv_plan_info(n, B.SV_C64, serving_circuit(n, depth, 3), fuse_max_k=5, tile_qubits=13)
     assert ns <= whole
     if n == 24:  # 30 qubits run 12-qubit tiles (states of 26 qubits and more)
         _, ns30, _ = B.sv_plan_info(30, B.SV_C64, fused_layered_u3_cz(30, 20, 0), fuse_max_k=5)
@@ -123,7 +125,16 @@ def test_tile_width_option(svlib):
     _, t13, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5, tile_qubits=13)
     _, t12, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5, tile_qubits=12)
     _, t8, _ = B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5, tile_qubits=8)
-    assert auto == t13 and t8 >= t12 >= t13 >= 1
+    assert t8 >= t12 >= t13 >= 1
+    # 22 qubits: 12-qubit tiles while the compiled pass kernels are on (the
+    # TMA pass with compiled programs), 13 with them off
+    jit = B.sv_jit_info()
+    assert auto == (t12 if jit["mode"] != 0 and jit["available"] else t13)
+    B.sv_jit_set_mode(0)
+    try:
+        assert B.sv_plan_info(n, B.SV_C64, g, fuse_max_k=5)[1] == t13
+    finally:
+        B.sv_jit_set_mode(-1)
     _, c11, _ = B.sv_plan_info(n, B.SV_C128, g, fuse_max_k=5, tile_qubits=11)
     assert c11 >= 1
     for dt, bad in ((B.SV_C64, 7), (B.SV_C64, 14), (B.SV_C128, 12), (B.SV_C64, -1)):
