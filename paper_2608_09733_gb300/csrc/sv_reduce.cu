@@ -15,8 +15,12 @@
 // an x mask share one pass.
 //
 // Precision (complex64): each thread sums p in float over a short run (64
-// amplitudes), then adds the run total into double; warp, block and grid
-// reductions are in double.  complex128 accumulates in double throughout.
+// amplitudes); the warp adds its 32 runs in float (a chunk of 2048
+// amplitudes: relative error below 70 float roundings, 4e-6, of the chunk's
+// sum) and the chunk sums go into double, as do the block and grid
+// reductions.  (Warp sums in double took most of the kernel's time: the FP64
+// pipe of this part runs a warp-wide add in about 16 cycles.)  complex128
+// accumulates in double throughout.
 // The grid writes one partial per block and a one-block kernel adds them in a
 // fixed order, so results are identical run to run.
 #include <cuda_runtime.h>
@@ -46,6 +50,11 @@ struct Acc<double> {
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -91,14 +100,15 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_z_all(const Cx<R>* __res
       if (j & 8) jb3 += p;
       if (j & 16) jb4 += p;
     }
-    // fold the lane's run into double and reduce across the warp
-    double t = warp_sum((double)tot);
-    double v_e1 = EB ? warp_sum((double)e1) : 0.0;
-    double v_j[5] = {warp_sum((double)jb0), warp_sum((double)jb1), warp_sum((double)jb2), warp_sum((double)jb3),
-                     warp_sum((double)jb4)};
+    // reduce the lanes' runs across the warp (in the run's precision), then
+    // into double
+    const double t = (double)warp_sum(tot);
+    const double v_e1 = EB ? (double)warp_sum(e1) : 0.0;
+    const double v_j[5] = {(double)warp_sum(jb0), (double)warp_sum(jb1), (double)warp_sum(jb2),
+                           (double)warp_sum(jb3), (double)warp_sum(jb4)};
     double v_l[5];
 #pragma unroll
-    for (int b = 0; b < 5; b++) v_l[b] = warp_sum(((lane >> b) & 1) ? (double)tot : 0.0);
+    for (int b = 0; b < 5; b++) v_l[b] = (double)warp_sum(((lane >> b) & 1) ? tot : T(0));
     // lane q picks S_q for its qubits q = lane and lane + 32
 #pragma unroll
     for (int rep = 0; rep < 2; rep++) {
