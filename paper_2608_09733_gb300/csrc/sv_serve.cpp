@@ -13,8 +13,8 @@
 //     published count (tail), the exit flag, the results and the done words;
 //   - the device holds the programs (a ring arena), the claim counter (head)
 //     and the status word;
-//   - the kernel runs on a stream of its own and uploads go on another, both
-//     non-blocking, so they overlap;
+//   - the kernel runs on a stream of its own (the device's highest priority)
+//     and uploads go on another, both non-blocking, so they overlap;
 //   - a ticket's slot (ticket mod capacity) and its arena range are reused
 //     only once its done word is set.
 // A session whose kernel has ended (its waits ran out while idle) is
@@ -229,7 +229,13 @@ extern "C" sv_status sv_small_session_start(sv_dtype dtype, int capacity, int ar
     cuda_check(cudaGetDevice(&s->device), "cudaGetDevice");
     const int sms = device_sm_count();
     s->grid = n_ctas > 0 ? std::min(n_ctas, sms) : std::max(2, sms / 16);
-    cuda_check(cudaStreamCreateWithFlags(&s->run, cudaStreamNonBlocking), "cudaStreamCreate");
+    // The kernel's stream has the device's highest priority: a relaunch after
+    // an idle exit queues behind the CTAs of whatever pass kernels other
+    // streams have launched, and the block scheduler serves higher-priority
+    // streams first as SMs free up.
+    int least = 0, greatest = 0;
+    cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+    cuda_check(cudaStreamCreateWithPriority(&s->run, cudaStreamNonBlocking, greatest), "cudaStreamCreate");
     cuda_check(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking), "cudaStreamCreate");
     cuda_check(cudaEventCreateWithFlags(&s->finished, cudaEventDisableTiming), "cudaEventCreate");
     // one mapped block: entries | tail | exit | results | done
