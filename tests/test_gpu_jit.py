@@ -114,3 +114,26 @@ def test_jit_off_keeps_interpreter(svlib, cuda_dev):
     _, l2, fam = run(n, gates, 0, fuse=5, profile=True)
     assert l1 == 0 and l2 == 0
     assert "sweep_jit" not in fam and "sweep_tma" in fam, fam
+
+
+def test_default_tiles_compile_mid_size_states(svlib, cuda_dev):
+    """With no tile width given, a 22-qubit complex64 state plans 12-qubit
+    tiles while the compiled kernels are on, so its passes run on the TMA path
+    and compile; the state matches the oracle."""
+    import torch
+    n = 22
+    gates = fused_layered_u3_cz(n, 10, seed=44)
+    B.sv_jit_set_mode(2)
+    try:
+        _, passes, _ = B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=5)
+        assert passes == B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=5, tile_qubits=12)[1]
+        before = B.sv_jit_info()["launches"]
+        st = torch.empty(2 ** n, dtype=torch.complex64, device="cuda")
+        B.sv_init_basis(st, 0)
+        B.sv_apply_circuit(st, gates, fuse_max_k=5)
+        torch.cuda.synchronize()
+        assert B.sv_jit_info()["launches"] - before == passes
+    finally:
+        B.sv_jit_set_mode(-1)
+    ref = oracle.run(n, gates)
+    assert maxabs(st.cpu().numpy(), ref) < TOL_C64
