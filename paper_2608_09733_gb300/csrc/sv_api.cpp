@@ -222,12 +222,10 @@ struct Compiled {
   int n = 0;
   std::vector<SweepProgram<float>> pf;
   std::vector<SweepProgram<double>> pd;
-  // the programs' compiled pass kernels (sv_jit.cpp), made on the run that
-  // jit_mode() names and kept with the circuit
+  // the programs' structure keys (sv_jit.cpp), made on the first run
   mutable std::mutex jit_mu;
-  mutable int runs = 0;
-  mutable bool jit_made = false;
-  mutable std::vector<const JitKernel*> jit;
+  mutable bool keys_made = false;
+  mutable std::vector<std::string> keys;
 };
 
 constexpr size_t kCompiledMax = 8;                  // circuits kept
@@ -304,32 +302,32 @@ void run_programs(void* state, int n, const std::vector<SweepProgram<R>>& progs,
   }
 }
 
-// The circuit's compiled pass kernels, made (NVRTC, on the host) on the run
-// jit_mode() names: a circuit run once keeps the interpreting kernel and pays
-// no compilation.  While a serving session is live the TMA pass is off, so
-// nothing is compiled or loaded then (runs are not counted).
-const std::vector<const JitKernel*>* jit_kernels(const Compiled& c, sv_dtype dtype) {
+// The circuit's compiled pass kernels, by program structure: a structure is
+// compiled (NVRTC, on the host) on its second use by any circuit (jit_mode()
+// 1) or its first (2), and every later program of that structure -- this
+// circuit run again, or another circuit of the same gates at other angles --
+// launches the compiled kernel.  Until then the interpreting kernel runs.
+std::vector<const JitKernel*> jit_kernels(const Compiled& c, sv_dtype dtype) {
   const int mode = jit_mode();
-  if (mode == 0 || dtype != SV_C64) return nullptr;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || session_live(dev)) {
-    cudaGetLastError();
-    return nullptr;
+  if (mode == 0 || dtype != SV_C64) return {};
+  {
+    std::lock_guard<std::mutex> lk(c.jit_mu);
+    if (!c.keys_made) {
+      c.keys.resize(c.pf.size());
+      for (size_t i = 0; i < c.pf.size(); i++) c.keys[i] = jit_program_key(c.pf[i]);
+      c.keys_made = true;
+    }
   }
-  std::lock_guard<std::mutex> lk(c.jit_mu);
-  c.runs++;
-  if (!c.jit_made && c.runs >= (mode == 2 ? 1 : 2)) {
-    c.jit = jit_compile_programs<float>(c.pf);
-    c.jit_made = true;
-  }
-  return c.jit_made ? &c.jit : nullptr;
+  return jit_program_kernels(c.pf, c.keys, mode == 2 ? 1 : 2);
 }
 
 void run_compiled(void* state, const Compiled& c, sv_dtype dtype, cudaStream_t stream) {
-  if (dtype == SV_C64)
-    run_programs<float>(state, c.n, c.pf, stream, jit_kernels(c, dtype));
-  else
+  if (dtype == SV_C64) {
+    const std::vector<const JitKernel*> k = jit_kernels(c, dtype);
+    run_programs<float>(state, c.n, c.pf, stream, &k);
+  } else {
     run_programs<double>(state, c.n, c.pd, stream);
+  }
 }
 
 sv_exec_opts opts_of(const sv_exec_opts* o) {

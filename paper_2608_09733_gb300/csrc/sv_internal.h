@@ -161,13 +161,17 @@ struct SmallSessionDev {
 template <typename R>
 cudaError_t launch_small_session(const SmallSessionDev& d, const SweepProgram<R>* progs, int max_n, int grid,
                                  cudaStream_t stream);
-// Live sessions per device.  A session's resident CTAs hold their SMs, so
-// while one is live the pass kernels avoid the TMA kernel (one CTA per SM, a
-// fixed share of tiles each) for the cp.async one, whose many small CTAs fill
-// what the session leaves free.
-void session_opened(int device);
-void session_closed(int device);
+// Live sessions per device and their resident CTAs.  A session's CTAs hold
+// their SMs, so while one is live the TMA pass (one CTA per SM, a fixed share
+// of tiles each) launches on the SMs the sessions leave free.
+void session_opened(int device, int ctas);
+void session_closed(int device, int ctas);
 bool session_live(int device);
+// Ends the kernels of the device's live sessions and holds them (their locks)
+// until sessions_release, which relaunches those with requests not done
+// (sv_serve.cpp): a module load waits for every resident kernel to end.
+void sessions_quiesce(int device, std::vector<sv_small_session*>& held);
+void sessions_release(std::vector<sv_small_session*>& held);
 
 // Reductions write fixed-order per-block partials into `scratch` and a final
 // kernel folds them into `out` (device doubles).
@@ -200,6 +204,14 @@ std::string jit_source(const SweepProgram<R>& P);
 // kernel runs that pass); compiles what the cache lacks, in parallel.
 template <typename R>
 std::vector<const JitKernel*> jit_compile_programs(const std::vector<SweepProgram<R>>& progs);
+// A program's structure key (empty if the TMA pass would not run it): all its
+// kernel source is written from, none of its coefficient values.
+std::string jit_program_key(const SweepProgram<float>& P);
+// The programs' kernels by structure key: counts a use of each key, compiles
+// (in the calling thread, in parallel) the keys used at least `threshold`
+// times that have no kernel yet; NULL entries interpret.
+std::vector<const JitKernel*> jit_program_kernels(const std::vector<SweepProgram<float>>& progs,
+                                                  const std::vector<std::string>& keys, int threshold);
 // Launches a compiled pass kernel with the interpreting TMA kernel's
 // arguments (map: the CUtensorMap, bx: the TmaBoxes).
 cudaError_t jit_launch(const JitKernel* k, void* state, const void* map, const void* bx, const void* prog, int ns,

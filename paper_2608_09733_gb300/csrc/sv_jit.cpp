@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -586,8 +587,22 @@ int device_arch(int dev) {
   return major * 10 + minor;
 }
 
+// Compiles in flight across the process: callers on several threads (the
+// workers of a serving loop) share one budget of host cores.
+std::mutex g_slots_mu;
+std::condition_variable g_slots_cv;
+int g_slots_used = 0;
+
+int compile_slots() {
+  static const int n = [] {
+    const unsigned hw = std::thread::hardware_concurrency();
+    return (int)(hw ? std::min(hw, 16u) : 4u);
+  }();
+  return n;
+}
+
 // Compiles the given sources in parallel (host threads; NVRTC needs no
-// device), each to a cubin.
+// device), each to a cubin, at most compile_slots() at a time in the process.
 void compile_all(const std::vector<const std::string*>& srcs, int arch, std::vector<std::vector<char>>& bins,
                  std::vector<std::string>& logs, std::vector<char>& ok) {
   const size_t n = srcs.size();
@@ -596,10 +611,21 @@ void compile_all(const std::vector<const std::string*>& srcs, int arch, std::vec
   ok.assign(n, 0);
   std::atomic<size_t> next{0};
   auto work = [&] {
-    for (size_t i; (i = next.fetch_add(1)) < n;) ok[i] = compile_cubin(*srcs[i], arch, bins[i], &logs[i]) ? 1 : 0;
+    for (size_t i; (i = next.fetch_add(1)) < n;) {
+      {
+        std::unique_lock<std::mutex> lk(g_slots_mu);
+        g_slots_cv.wait(lk, [] { return g_slots_used < compile_slots(); });
+        g_slots_used++;
+      }
+      ok[i] = compile_cubin(*srcs[i], arch, bins[i], &logs[i]) ? 1 : 0;
+      {
+        std::lock_guard<std::mutex> lk(g_slots_mu);
+        g_slots_used--;
+      }
+      g_slots_cv.notify_one();
+    }
   };
-  unsigned hw = std::thread::hardware_concurrency();
-  size_t nt = std::min<size_t>(n, hw ? std::min(hw, 16u) : 4u);
+  const size_t nt = std::min<size_t>(n, (size_t)compile_slots());
   std::vector<std::thread> th;
   for (size_t t = 1; t < nt; t++) th.emplace_back(work);
   work();
@@ -658,24 +684,40 @@ std::vector<const JitKernel*> kernels_for(const std::vector<std::string>& src, c
   compile_all(todo, arch, bins, logs, ok);
   g_jit_compile_us +=
       (long long)std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
-  std::lock_guard<std::mutex> lk(g_jit_mu);
-  for (size_t t = 0; t < todo.size(); t++) {
-    if (!ok[t]) {
-      g_jit_failed++;
-      g_jit_last_error = logs[t].substr(0, 4000);
-      continue;
+  // a module load waits for every resident kernel of the device, so the
+  // device's serving sessions are paused around the loads
+  struct Pause {
+    std::vector<sv_small_session*> held;
+    explicit Pause(int d) { sessions_quiesce(d, held); }
+    ~Pause() { sessions_release(held); }
+  };
+  {
+    Pause pause(dev);
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    for (size_t t = 0; t < todo.size(); t++) {
+      if (!ok[t]) {
+        g_jit_failed++;
+        g_jit_last_error = logs[t].substr(0, 4000);
+        continue;
+      }
+      // another thread may have compiled and loaded the same source meanwhile:
+      // its kernel stays (callers may hold it), this one is not loaded
+      if (g_jit_kernels.count({dev, *todo[t]})) continue;
+      CUmodule mod = nullptr;
+      auto k = std::make_unique<JitKernel>();
+      if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS || driver().get(&k->fn, mod, name) != CUDA_SUCCESS ||
+          driver().attr(k->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, 227 * 1024) != CUDA_SUCCESS) {
+        g_jit_failed++;
+        g_jit_last_error = "module load failed";
+        continue;
+      }
+      k->device = dev;
+      k->smem_configured = 227 * 1024;
+      g_jit_compiled++;
+      g_jit_kernels.emplace(std::make_pair(dev, *todo[t]), std::move(k));
     }
-    CUmodule mod = nullptr;
-    auto k = std::make_unique<JitKernel>();
-    if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS || driver().get(&k->fn, mod, name) != CUDA_SUCCESS) {
-      g_jit_failed++;
-      g_jit_last_error = "module load failed";
-      continue;
-    }
-    k->device = dev;
-    g_jit_compiled++;
-    g_jit_kernels[{dev, *todo[t]}] = std::move(k);
   }
+  std::lock_guard<std::mutex> lk(g_jit_mu);
   for (size_t i = 0; i < src.size(); i++) {
     if (out[i] || src[i].empty()) continue;
     auto it = g_jit_kernels.find({dev, src[i]});
@@ -706,6 +748,79 @@ std::vector<const JitKernel*> jit_compile_programs(const std::vector<SweepProgra
   if (sizeof(R) == 4)
     for (size_t i = 0; i < progs.size(); i++) src[i] = jit_source<R>(progs[i]);
   return kernels_for(src, "k_sweep_jit");
+}
+
+// ---- pass programs keyed by structure
+//
+// A program's key is everything its kernel source is written from -- the
+// header (sizes, tile qubits, pool size), its ops and its phases -- and none
+// of its coefficient values, so every circuit of the same structure (the same
+// gates at other angles: a variational template, the requests of a serving
+// family) shares the kernel.  Uses are counted per key (by a 64-bit hash, in a
+// table cleared when it grows past a million keys); a key reaching the
+// threshold is compiled in the calling thread, together with the call's other
+// keys that reached it.
+
+namespace {
+
+std::unordered_map<std::string, const JitKernel*> g_key_kernels;  // device + key -> kernel
+std::unordered_map<uint64_t, int> g_key_uses;                     // hash(device + key) -> uses
+
+uint64_t fnv1a(const std::string& s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : s) h = (h ^ c) * 1099511628211ull;
+  return h;
+}
+
+}  // namespace
+
+std::string jit_program_key(const SweepProgram<float>& P) {
+  const ProgramHeader& h = P.h;
+  if (h.rq != 5 || (1 << (h.m - h.rq)) != kJitGroupThreads || h.n - h.m < 9) return std::string();
+  std::string k;
+  const int32_t hdr[7] = {h.n, h.m, h.L, h.nops, h.ncoef, h.nphases, h.rq};
+  k.append((const char*)hdr, sizeof(hdr));
+  k.append((const char*)h.tq, sizeof(h.tq));
+  k.append((const char*)P.ops, sizeof(DevOp) * (size_t)h.nops);
+  k.append((const char*)P.ph, sizeof(Phase) * (size_t)h.nphases);
+  return k;
+}
+
+std::vector<const JitKernel*> jit_program_kernels(const std::vector<SweepProgram<float>>& progs,
+                                                  const std::vector<std::string>& keys, int threshold) {
+  std::vector<const JitKernel*> out(progs.size(), nullptr);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return out;
+  }
+  const std::string tag((const char*)&dev, sizeof(dev));
+  std::vector<size_t> want;
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    if (g_key_uses.size() > (1u << 20)) g_key_uses.clear();
+    for (size_t i = 0; i < progs.size() && i < keys.size(); i++) {
+      if (keys[i].empty()) continue;
+      const std::string full = tag + keys[i];
+      auto it = g_key_kernels.find(full);
+      if (it != g_key_kernels.end()) {
+        out[i] = it->second;
+        continue;
+      }
+      if (++g_key_uses[fnv1a(full)] >= threshold) want.push_back(i);
+    }
+  }
+  if (want.empty() || !driver().ok || !nvrtc().ok) return out;
+  std::vector<std::string> src(want.size());
+  for (size_t j = 0; j < want.size(); j++) src[j] = jit_source<float>(progs[want[j]]);
+  const std::vector<const JitKernel*> k = kernels_for(src, "k_sweep_jit");
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  for (size_t j = 0; j < want.size(); j++) {
+    if (!k[j]) continue;
+    g_key_kernels[tag + keys[want[j]]] = k[j];
+    out[want[j]] = k[j];
+  }
+  return out;
 }
 
 template <typename R>

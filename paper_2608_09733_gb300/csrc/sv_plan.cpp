@@ -56,22 +56,15 @@ int popc(uint64_t x) { return __builtin_popcountll(x); }
 // compiled kernels are on and NVRTC is present): the TMA pass on 12-qubit
 // tiles with compiled programs beats the interpreted pass on 13-qubit tiles
 // by 1.27x at 22 and 24 qubits and 1.5x at 25 on layered circuits, with
-// 10-15 % more passes, and interpreted (a circuit's first run) it is no
-// slower.  While a serving session is live the TMA pass is off, and mid-size
-// states keep the wider tile, whose fewer passes matter more there (the CNOT
-// ladders of serving circuits take up to twice the passes on 12 qubits);
-// smaller states keep it as well.
+// 10-15 % more passes, and interpreted (a program structure's first run) it
+// is no slower.  The serving circuits' CNOT ladders take 14-28 % more passes
+// on 12-qubit tiles at 21-25 qubits, which their compiled passes (1.5-1.8x
+// faster) more than repay once a structure has run twice.  Smaller states
+// keep the wider tile.
 int tile_qubits_for(sv_dtype dtype, int n) {
   if (dtype != SV_C64) return 11;
   if (n >= SV_C64_SMALL_TILE_MIN_N) return SV_C64_TILE_Q - 1;
-  if (n >= SV_C64_TMA_MIN_N && jit_mode() != 0 && jit_available(nullptr)) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) {  // no device here: plan as if none were live
-      cudaGetLastError();
-      dev = -1;
-    }
-    if (!session_live(dev)) return SV_C64_TILE_Q - 1;
-  }
+  if (n >= SV_C64_TMA_MIN_N && jit_mode() != 0 && jit_available(nullptr)) return SV_C64_TILE_Q - 1;
   return SV_C64_TILE_Q;
 }
 #ifndef SV_RQ5_MIN_M

@@ -70,6 +70,10 @@ struct sv_small_session {
 namespace sv {
 namespace {
 
+// Live sessions (for sessions_quiesce).
+std::mutex g_sessions_mu;
+std::vector<sv_small_session*> g_sessions;
+
 size_t prog_bytes(sv_dtype d) { return d == SV_C64 ? sizeof(SweepProgram<float>) : sizeof(SweepProgram<double>); }
 
 long long load_acquire(const long long* p) {
@@ -195,6 +199,47 @@ void submit_batch(sv_small_session* s, int nreq, const int* nq, const sv_gate* c
   ensure_running(s);
 }
 
+}  // namespace
+
+// Loading a module waits for every resident kernel of the device to end, and
+// a session's kernel stays resident until it idles past its wait limit: so a
+// module load beside a live session would stall for that long (and a busy
+// session never idles).  Quiesce takes each live session of the device (its
+// lock held until release), sets its exit flag and waits for its kernel to
+// end -- requests being simulated finish, claimed ones are claimed again
+// later; release clears the flags and relaunches the sessions that have
+// requests not done (the others relaunch on their next submit).
+void sessions_quiesce(int device, std::vector<sv_small_session*>& held) {
+  g_sessions_mu.lock();
+  for (sv_small_session* s : g_sessions) {
+    if (s->device != device) continue;
+    s->mu.lock();
+    held.push_back(s);
+    if (!s->running) continue;
+    reinterpret_cast<std::atomic<int>*>(s->exit_flag)->store(1, std::memory_order_release);
+    cudaStreamSynchronize(s->run);
+    s->running = false;
+    reinterpret_cast<std::atomic<int>*>(s->exit_flag)->store(0, std::memory_order_release);
+  }
+}
+
+void sessions_release(std::vector<sv_small_session*>& held) {
+  for (sv_small_session* s : held) {
+    retire(s);
+    if (!s->inflight.empty()) {
+      try {
+        ensure_running(s);
+      } catch (const Error&) {  // reported by the session's next call
+      }
+    }
+    s->mu.unlock();
+  }
+  held.clear();
+  g_sessions_mu.unlock();
+}
+
+namespace {
+
 void free_session(sv_small_session* s) {
   if (s->entries) cudaFreeHost(s->entries);
   if (s->staging) cudaFreeHost(s->staging);
@@ -275,7 +320,11 @@ extern "C" sv_status sv_small_session_start(sv_dtype dtype, int capacity, int ar
     cuda_check(cudaMemsetAsync(s->head, 0, 64, s->copy), "cudaMemset");
     cuda_check(cudaStreamSynchronize(s->copy), "cudaStreamSynchronize");
     launch(s.get());
-    session_opened(s->device);
+    session_opened(s->device, s->grid);
+    {
+      std::lock_guard<std::mutex> lk(g_sessions_mu);
+      g_sessions.push_back(s.get());
+    }
     *out = s.release();
   });
 }
@@ -311,6 +360,10 @@ extern "C" sv_status sv_small_session_stop(sv_small_session* s) {
   int st = 0;
   const sv_status rc = guarded([&] {
     if (!s) fail(SV_ERR_INVALID, "session is NULL");
+    {
+      std::lock_guard<std::mutex> lk(g_sessions_mu);
+      g_sessions.erase(std::remove(g_sessions.begin(), g_sessions.end(), s), g_sessions.end());
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     cuda_check(cudaSetDevice(s->device), "cudaSetDevice");
     reinterpret_cast<std::atomic<int>*>(s->exit_flag)->store(1, std::memory_order_release);
@@ -318,7 +371,7 @@ extern "C" sv_status sv_small_session_stop(sv_small_session* s) {
     cuda_check(cudaMemcpy(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
   });
   if (s) {
-    session_closed(s->device);
+    session_closed(s->device, s->grid);
     free_session(s);
   }
   if (rc != SV_OK) return rc;

@@ -714,6 +714,8 @@ static int* sweep_status_ptr() {
   return ptr[dev];
 }
 
+static uint64_t tma_grid(uint64_t ntiles);
+
 template <typename R, int KMAX, int RQ, int OPS>
 static cudaError_t launch_sweep_tma_k(Cx<R>* state, const SweepProgram<R>& prog, const CUtensorMap& map,
                                       const TmaBoxes& bx, cudaStream_t stream) {
@@ -731,9 +733,7 @@ static cudaError_t launch_sweep_tma_k(Cx<R>* state, const SweepProgram<R>& prog,
     if (e != cudaSuccess) return e;
     configured_bytes[dev] = smem;
   }
-  const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
-  uint64_t grid = (uint64_t)device_sm_count();
-  if (grid > ntiles) grid = ntiles;
+  const uint64_t grid = tma_grid(1ull << (prog.h.n - prog.h.m));
   k_sweep_tma<R, KMAX, RQ, OPS, NC>
       <<<(unsigned)grid, NC * tma_group_threads<RQ>(), smem, stream>>>(state, map, bx, prog, ns);
   return cudaGetLastError();
@@ -741,25 +741,40 @@ static cudaError_t launch_sweep_tma_k(Cx<R>* state, const SweepProgram<R>& prog,
 
 // Whether the TMA pass runs this program: complex64 states of at least 2^9
 // tiles whose tile groups are 128 threads (12-qubit tiles with five register
-// qubits), unless a serving session is live on the device or SV_SWEEP_TMA=0
-// in the environment selects the cp.async kernel.  (complex128 passes are bound by the FP64 pipe, and at the 128
+// qubits), unless SV_SWEEP_TMA=0 in the environment selects the cp.async
+// kernel.  (complex128 passes are bound by the FP64 pipe, and at the 128
 // registers of four 128-thread groups per SM their register phases spill.)
 static std::atomic<int> g_live_sessions[64];
+static std::atomic<int> g_session_ctas[64];
 
-void session_opened(int device) {
-  if (device >= 0 && device < 64) g_live_sessions[device]++;
+void session_opened(int device, int ctas) {
+  if (device < 0 || device >= 64) return;
+  g_live_sessions[device]++;
+  g_session_ctas[device] += ctas;
 }
-void session_closed(int device) {
-  if (device >= 0 && device < 64) g_live_sessions[device]--;
+void session_closed(int device, int ctas) {
+  if (device < 0 || device >= 64) return;
+  g_live_sessions[device]--;
+  g_session_ctas[device] -= ctas;
 }
 bool session_live(int device) { return device >= 0 && device < 64 && g_live_sessions[device].load() > 0; }
 
 static bool tma_enabled() {
   const char* e = std::getenv("SV_SWEEP_TMA");
-  if (e && e[0] == '0') return false;
+  return !(e && e[0] == '0');
+}
+
+// CTAs of a TMA pass (one per SM, each with a fixed share of the tiles): the
+// SMs, less one per resident CTA of the device's live serving sessions (their
+// shared memory leaves no room for a TMA CTA beside them), so that every CTA
+// of the pass can be resident at once; at most one per tile.
+static uint64_t tma_grid(uint64_t ntiles) {
   int dev = 0;
   cudaGetDevice(&dev);
-  return !session_live(dev);
+  int64_t sms = device_sm_count();
+  if (dev >= 0 && dev < 64) sms -= g_session_ctas[dev].load();
+  const uint64_t g = sms < 1 ? 1 : (uint64_t)sms;
+  return g < ntiles ? g : ntiles;
 }
 
 template <typename R, int RQ>
@@ -775,9 +790,7 @@ static cudaError_t launch_sweep_tma(Cx<R>* state, const SweepProgram<R>& prog, c
     const int ns = tma_stages<R>(prog.h);
     int* status = sweep_status_ptr();
     if (ns && status) {
-      const uint64_t ntiles = 1ull << (prog.h.n - prog.h.m);
-      uint64_t grid = (uint64_t)device_sm_count();
-      if (grid > ntiles) grid = ntiles;
+      const uint64_t grid = tma_grid(1ull << (prog.h.n - prog.h.m));
       used = used_jit = true;
       return jit_launch(jit, state, &map, &bx, &prog, ns, status, (unsigned)grid,
                         kTmaGroups * tma_group_threads<RQ>(), tma_smem_bytes<R>(prog.h, ns), stream);

@@ -33,7 +33,9 @@ def run(n, gates, mode, fuse=0, block_mode=0, tile=12, profile=False):
         if profile:
             B.sv_profile_enable(True)
         B.sv_apply_circuit_ex(st, gates, fuse_max_k=fuse, block_mode=block_mode, tile_qubits=tile)
-        torch.cuda.synchronize()
+        # the stream, not the device: a live serving session's kernel stays
+        # resident, and a device-wide wait would wait for it
+        torch.cuda.current_stream().synchronize()
         fam = B.sv_profile_read() if profile else None
         if profile:
             B.sv_profile_enable(False)
@@ -96,15 +98,65 @@ def test_jit_serving_circuit_21q_against_oracle(svlib, cuda_dev):
 
 
 def test_jit_second_run_default_mode(svlib, cuda_dev):
-    """Mode 1 (the default): the first run of a circuit interprets, the
-    second compiles and launches the compiled kernels, with the same bits."""
-    n = 24
-    gates = fused_layered_u3_cz(n, 5, seed=77)
-    _, passes, _ = B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=5, tile_qubits=12)
-    a, la, _ = run(n, gates, 1, fuse=5)
-    b, lb, _ = run(n, gates, 1, fuse=5)
+    """Mode 1 (the default): a program structure's first use interprets, its
+    second compiles and launches the compiled kernel, with the same bits (a
+    random circuit, whose passes share no structure with each other or with
+    other tests' circuits)."""
+    n = 23
+    gates = random_circuit(n, 90, seed=2323, max_controls=2, max_unitary_k=2)
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=0, tile_qubits=12)
+    a, la, _ = run(n, gates, 1)
+    b, lb, _ = run(n, gates, 1)
     assert la == 0 and lb == passes, (la, lb, passes)
     assert same_bits(a, b)
+
+
+def test_structure_shared_across_angles(svlib, cuda_dev):
+    """Two circuits with the same gates at other angles share their passes'
+    compiled kernels: after one run of the first, the second (a new circuit)
+    runs compiled on its first run, bit for bit as interpreted and within the
+    bar of the oracle."""
+    n = 22
+    g1 = fused_layered_u3_cz(n, 6, seed=501)
+    g2 = fused_layered_u3_cz(n, 6, seed=502)  # same structure, other Haar angles
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, g2, fuse_max_k=5, tile_qubits=12)
+    run(n, g1, 1, fuse=5)
+    b, lb, _ = run(n, g2, 1, fuse=5)
+    assert lb == passes, (lb, passes)
+    a, _, _ = run(n, g2, 0, fuse=5)
+    assert same_bits(a, b)
+    assert maxabs(b, oracle.run(n, g2)) < TOL_C64
+
+
+def test_compiled_tma_pass_beside_a_live_session(svlib, cuda_dev):
+    """While a serving session's kernel is resident the TMA pass (and its
+    compiled kernels) runs on the SMs the session leaves free; results match
+    the oracle and the session still serves."""
+    n = 22
+    gates = fused_layered_u3_cz(n, 6, seed=611)
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=5, tile_qubits=12)
+    import time
+    ses = B.SmallSession(B.SV_C64, capacity=64, wait_limit_s=10.0, n_ctas=9)
+    sets = [serving_circuit(8, 5, 1), serving_circuit(10, 5, 2)]
+    try:
+        tickets = ses.submit([8, 10], sets)
+        got, launches, fam = run(n, gates, 2, fuse=5, profile=True)
+        assert launches == passes and fam["sweep_jit"]["launches"] == passes, fam
+        res = []
+        t0 = time.time()
+        for tk in tickets:
+            done, v = ses.poll(tk)
+            while not done and time.time() - t0 < 20.0:
+                time.sleep(0.001)
+                done, v = ses.poll(tk)
+            assert done
+            res.append(v)
+    finally:
+        ses.stop()
+    assert maxabs(got, oracle.run(n, gates)) < TOL_C64
+    for nn, g, v in zip((8, 10), sets, res):
+        _, ref = oracle.expect_z_all(oracle.run(nn, g), nn)
+        assert abs(v - ref) < 1e-4
 
 
 def test_jit_off_keeps_interpreter(svlib, cuda_dev):
@@ -137,3 +189,45 @@ def test_default_tiles_compile_mid_size_states(svlib, cuda_dev):
         B.sv_jit_set_mode(-1)
     ref = oracle.run(n, gates)
     assert maxabs(st.cpu().numpy(), ref) < TOL_C64
+
+
+def test_threads_compiling_one_structure_at_once(svlib, cuda_dev):
+    """Four threads run circuits of one new structure at once (each its own
+    state and stream), so they compile the same kernel sources concurrently:
+    the first kernel loaded stays in the cache and every thread's passes run
+    compiled, each state within the bar of the oracle."""
+    import threading
+    import torch
+    n = 21
+    circs = [fused_layered_u3_cz(n, 7, seed=7000 + i) for i in range(4)]  # same structure, other angles
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, circs[0], fuse_max_k=5, tile_qubits=12)
+    states = [torch.empty(2 ** n, dtype=torch.complex64, device="cuda") for _ in circs]
+    errors = []
+    barrier = threading.Barrier(len(circs))
+
+    def work(i):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                B.sv_init_basis(states[i], 0, stream=s)
+                barrier.wait()
+                B.sv_apply_circuit_ex(states[i], circs[i], fuse_max_k=5, tile_qubits=12, stream=s)
+                s.synchronize()
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    B.sv_jit_set_mode(2)
+    try:
+        before = B.sv_jit_info()["launches"]
+        th = [threading.Thread(target=work, args=(i,)) for i in range(len(circs))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        launches = B.sv_jit_info()["launches"] - before
+    finally:
+        B.sv_jit_set_mode(-1)
+    assert not errors, errors
+    assert launches == passes * len(circs), (launches, passes)
+    for st, g in zip(states, circs):
+        assert maxabs(st.cpu().numpy(), oracle.run(n, g)) < TOL_C64
