@@ -482,15 +482,20 @@ sv_status sv_release_scratch(void);
  * coefficient offsets as constants), compile it with NVRTC for the current
  * device and launch that kernel in its place: same tile movement, same
  * arithmetic in the same order (bit-identical results), fewer instructions.
- * Compilation runs on host threads (about a second per distinct program) and
- * its kernels are cached for the life of the process, per device and program.
- * Only circuits the library caches (sv_apply_circuit and friends with at most
- * 512 passes) are compiled; on states with fewer than 2^21 amplitudes, for
- * complex128 states and where NVRTC is missing, the interpreting kernels run.
+ * Kernels are kept by program structure (the gates and their qubits, not their
+ * angles), so every circuit of the same structure -- a variational template at
+ * new parameters, the requests of one serving family -- shares them.
+ * Compilation runs on host threads (about a second per distinct program, at
+ * most one per host core across the process) and its kernels are cached for
+ * the life of the process, per device.  Loading a compiled module waits for
+ * every resident kernel of the device, so live serving sessions on the device
+ * are paused for the load (their kernels end and relaunch; requests in flight
+ * are kept).  On states with fewer than 2^21 amplitudes, for complex128 states
+ * and where NVRTC is missing, the interpreting kernels run.
  *
- * mode: 0 never compile; 1 (default) compile a circuit's programs on its second
- * run; 2 on its first; -1 take the SV_JIT environment variable (0, 1, 2).
- * Other values are SV_ERR_INVALID. */
+ * mode: 0 never compile; 1 (default) compile a program structure on its second
+ * use (by any circuit); 2 on its first; -1 take the SV_JIT environment variable
+ * (0, 1, 2).  Other values are SV_ERR_INVALID. */
 sv_status sv_jit_set_mode(int mode);
 /* Current mode, whether NVRTC was found (available), kernels compiled and
  * failed so far, launches of compiled kernels, host seconds spent compiling;
