@@ -795,7 +795,7 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     clk = clocks.stop(None) if rank == 0 else None
 
-    # the circuit's pass programs were compiled to their own kernels on its
+    # the circuit's pass programs were compiled to their own kernels (by structure) on its
     # second run (a warm-up step); the timed steps launch those
     jit = sv.sv_jit_info()
     bytes_step = step_bytes(n, npasses, amp)  # passes r+w, init write, read-out read

@@ -448,9 +448,9 @@ def sv_release_scratch():
 
 
 def sv_jit_set_mode(mode: int):
-    """0: never compile pass programs; 1 (default): compile a cached circuit's
-    programs on its second run; 2: on its first; -1: the SV_JIT environment
-    variable."""
+    """0: never compile pass programs; 1 (default): compile a program
+    structure on its second use (by any circuit of the same gates, at any
+    angles); 2: on its first; -1: the SV_JIT environment variable."""
     _check(load().sv_jit_set_mode(int(mode)))
 
 

@@ -192,8 +192,8 @@ int device_sm_count();
 int take_sweep_status(cudaStream_t stream);
 
 // ----------------------------------------------------------------- run-time compiled pass kernels
-// (sv_jit.cpp).  jit_mode(): 0 off, 1 compile a cached circuit's programs on
-// its second run, 2 on its first (SV_JIT=0 / 1 / 2 in the environment, or
+// (sv_jit.cpp).  jit_mode(): 0 off, 1 compile a program structure on its
+// second use, 2 on its first (SV_JIT=0 / 1 / 2 in the environment, or
 // jit_set_mode; -1 goes back to the environment).
 int jit_mode();
 void jit_set_mode(int mode);
