@@ -535,6 +535,7 @@ bool compile_cubin(const std::string& src, int arch, std::vector<char>& out, std
 using ModuleLoadDataFn = CUresult (*)(CUmodule*, const void*);
 using ModuleGetFunctionFn = CUresult (*)(CUfunction*, CUmodule, const char*);
 using FuncSetAttributeFn = CUresult (*)(CUfunction, CUfunction_attribute, int);
+using FuncGetAttributeFn = CUresult (*)(int*, CUfunction_attribute, CUfunction);
 using LaunchKernelFn = CUresult (*)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
                                     CUstream, void**, void**);
 
@@ -543,6 +544,7 @@ struct Driver {
   ModuleLoadDataFn load = nullptr;
   ModuleGetFunctionFn get = nullptr;
   FuncSetAttributeFn attr = nullptr;
+  FuncGetAttributeFn getattr = nullptr;
   LaunchKernelFn launch = nullptr;
 };
 
@@ -564,8 +566,9 @@ const Driver& driver() {
     r.load = entry<ModuleLoadDataFn>("cuModuleLoadData");
     r.get = entry<ModuleGetFunctionFn>("cuModuleGetFunction");
     r.attr = entry<FuncSetAttributeFn>("cuFuncSetAttribute");
+    r.getattr = entry<FuncGetAttributeFn>("cuFuncGetAttribute");
     r.launch = entry<LaunchKernelFn>("cuLaunchKernel");
-    r.ok = r.load && r.get && r.attr && r.launch;
+    r.ok = r.load && r.get && r.attr && r.getattr && r.launch;
     return r;
   }();
   return d;
@@ -705,14 +708,22 @@ std::vector<const JitKernel*> kernels_for(const std::vector<std::string>& src, c
       if (g_jit_kernels.count({dev, *todo[t]})) continue;
       CUmodule mod = nullptr;
       auto k = std::make_unique<JitKernel>();
-      if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS || driver().get(&k->fn, mod, name) != CUDA_SUCCESS ||
-          driver().attr(k->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, 227 * 1024) != CUDA_SUCCESS) {
+      if (driver().load(&mod, bins[t].data()) != CUDA_SUCCESS || driver().get(&k->fn, mod, name) != CUDA_SUCCESS) {
         g_jit_failed++;
         g_jit_last_error = "module load failed";
         continue;
       }
+      // the dynamic shared memory a launch may ask for, set here while the
+      // sessions are paused: the block's opt-in limit less the kernel's own
+      // static shared memory (a launch asking for more sets it again)
+      int stat = 0, optin = 0;
+      if (driver().getattr(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, k->fn) == CUDA_SUCCESS &&
+          cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+          optin > stat &&
+          driver().attr(k->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin - stat) == CUDA_SUCCESS)
+        k->smem_configured = (size_t)(optin - stat);
+      cudaGetLastError();
       k->device = dev;
-      k->smem_configured = 227 * 1024;
       g_jit_compiled++;
       g_jit_kernels.emplace(std::make_pair(dev, *todo[t]), std::move(k));
     }
