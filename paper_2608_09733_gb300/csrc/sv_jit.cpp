@@ -46,7 +46,7 @@ namespace sv {
 struct JitKernel {
   CUfunction fn = nullptr;
   int device = -1;
-  size_t smem_configured = 0;
+  std::atomic<size_t> smem_configured{0};  // dynamic shared memory the function allows
 };
 
 namespace {
@@ -721,7 +721,7 @@ std::vector<const JitKernel*> kernels_for(const std::vector<std::string>& src, c
           cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
           optin > stat &&
           driver().attr(k->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin - stat) == CUDA_SUCCESS)
-        k->smem_configured = (size_t)(optin - stat);
+        k->smem_configured.store((size_t)(optin - stat));
       cudaGetLastError();
       k->device = dev;
       g_jit_compiled++;
@@ -873,19 +873,33 @@ template void jit_batch_prepare<double>(const std::vector<const BatchProgram<dou
 template const JitKernel* jit_batch_lookup<float>(const BatchProgram<float>&, bool);
 template const JitKernel* jit_batch_lookup<double>(const BatchProgram<double>&, bool);
 
+namespace {
+
+// Raises a kernel's dynamic shared-memory allowance to `smem` if it is below
+// (normally set at load to the block's limit, so this is rare); raises are
+// serialized so that concurrent launches never lower it.
+std::mutex g_smem_mu;
+bool allow_smem(JitKernel* k, size_t smem) {
+  if (smem <= k->smem_configured.load(std::memory_order_acquire)) return true;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  if (smem <= k->smem_configured.load(std::memory_order_acquire)) return true;
+  if (smem > 48 * 1024 &&
+      driver().attr(k->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+    return false;
+  k->smem_configured.store(smem, std::memory_order_release);
+  return true;
+}
+
+}  // namespace
+
 cudaError_t jit_batch_launch(const JitKernel* k, void* psi, void* lam, const void* table, double* gscratch,
                              const void* prog, unsigned grid_x, unsigned batch, size_t smem, cudaStream_t stream) {
   const Driver& d = driver();
   int dev = 0;
   cudaGetDevice(&dev);
   if (!k || !k->fn || k->device != dev) return cudaErrorInvalidDeviceFunction;
+  if (!allow_smem(const_cast<JitKernel*>(k), smem)) return cudaErrorInvalidConfiguration;
   JitKernel* kk = const_cast<JitKernel*>(k);
-  if (smem > kk->smem_configured) {
-    if (smem > 48 * 1024 &&
-        d.attr(kk->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
-      return cudaErrorInvalidConfiguration;
-    kk->smem_configured = smem;
-  }
   void* a0 = psi;
   void* a1 = lam;
   const void* a2 = table;
@@ -941,12 +955,8 @@ cudaError_t jit_launch(const JitKernel* k, void* state, const void* map, const v
   int dev = 0;
   cudaGetDevice(&dev);
   if (!k || !k->fn || k->device != dev) return cudaErrorInvalidDeviceFunction;
+  if (!allow_smem(const_cast<JitKernel*>(k), smem)) return cudaErrorInvalidConfiguration;
   JitKernel* kk = const_cast<JitKernel*>(k);
-  if (smem > kk->smem_configured) {
-    if (d.attr(kk->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
-      return cudaErrorInvalidConfiguration;
-    kk->smem_configured = smem;
-  }
   void* state_arg = state;
   void* args[] = {&state_arg, const_cast<void*>(map), const_cast<void*>(bx), const_cast<void*>(prog), &ns, &status};
   const CUresult r = d.launch(kk->fn, grid, 1, 1, block, 1, 1, (unsigned)smem, (CUstream)stream, args, nullptr);
