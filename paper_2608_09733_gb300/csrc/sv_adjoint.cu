@@ -272,9 +272,12 @@ cudaError_t launch_batch_sweep(Cx<R>* psi, Cx<R>* lam, const Cx<R>* table, doubl
                                const BatchProgram<R>& prog, bool reverse, cudaStream_t stream, const JitKernel* jit) {
   const int smem = ((int)sizeof(Cx<R>) << prog.h.m << (reverse ? 1 : 0)) + (8 << (prog.h.m - prog.h.L)) +
                    (int)sizeof(Cx<R>) * prog.h.scoef;
+  // one thread per register group of the tile (16 amplitudes), 32..256
+  const int g = prog.h.m - kRegQ;
+  const int threads = g >= 5 && g < 8 ? (1 << g) : 256;
   if (jit)
     return jit_batch_launch(jit, psi, lam, table, gscratch, &prog, (unsigned)grid_x, (unsigned)prog.h.batch,
-                            (size_t)smem, stream);
+                            (unsigned)threads, (size_t)smem, stream);
   static int configured[2][64] = {{0}};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -286,7 +289,7 @@ cudaError_t launch_batch_sweep(Cx<R>* psi, Cx<R>* lam, const Cx<R>* table, doubl
       if (e != cudaSuccess) return e;
       configured[which][dev] = smem;
     }
-    kernel<<<grid, 256, smem, stream>>>(psi, lam, table, gscratch, prog);
+    kernel<<<grid, threads, smem, stream>>>(psi, lam, table, gscratch, prog);
     return cudaGetLastError();
   };
   return reverse ? go(k_batch_sweep<R, true>, 0) : go(k_batch_sweep<R, false>, 1);

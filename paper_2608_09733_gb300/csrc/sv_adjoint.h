@@ -65,7 +65,8 @@ void jit_batch_prepare(const std::vector<const BatchProgram<R>*>& progs, const s
 template <typename R>
 const JitKernel* jit_batch_lookup(const BatchProgram<R>& P, bool rev);
 cudaError_t jit_batch_launch(const JitKernel* k, void* psi, void* lam, const void* table, double* gscratch,
-                             const void* prog, unsigned grid_x, unsigned batch, size_t smem, cudaStream_t stream);
+                             const void* prog, unsigned grid_x, unsigned batch, unsigned threads, size_t smem,
+                             cudaStream_t stream);
 // Writes (and with compile, compiles for sm_<arch>a) the distinct kernels of
 // these programs without a device.
 template <typename R>

@@ -893,7 +893,8 @@ bool allow_smem(JitKernel* k, size_t smem) {
 }  // namespace
 
 cudaError_t jit_batch_launch(const JitKernel* k, void* psi, void* lam, const void* table, double* gscratch,
-                             const void* prog, unsigned grid_x, unsigned batch, size_t smem, cudaStream_t stream) {
+                             const void* prog, unsigned grid_x, unsigned batch, unsigned threads, size_t smem,
+                             cudaStream_t stream) {
   const Driver& d = driver();
   int dev = 0;
   cudaGetDevice(&dev);
@@ -905,7 +906,7 @@ cudaError_t jit_batch_launch(const JitKernel* k, void* psi, void* lam, const voi
   const void* a2 = table;
   double* a3 = gscratch;
   void* args[] = {&a0, &a1, &a2, &a3, const_cast<void*>(prog)};
-  const CUresult r = d.launch(kk->fn, grid_x, batch, 1, 256, 1, 1, (unsigned)smem, (CUstream)stream, args, nullptr);
+  const CUresult r = d.launch(kk->fn, grid_x, batch, 1, threads, 1, 1, (unsigned)smem, (CUstream)stream, args, nullptr);
   if (r != CUDA_SUCCESS) return cudaErrorLaunchFailure;
   g_jit_launches++;
   return cudaSuccess;
