@@ -13,9 +13,17 @@
 // arithmetic is the same sequence of operations, so both kernels give the
 // same bits.
 //
+// The adjoint's batched programs are compiled the same way
+// (jit_batch_source: every phase and op as a constant, direct calls to the
+// register-op functions of sv_batch_ops.cuh inside its tile loop).
+//
 // NVRTC is opened with dlopen on first use; without it (or the driver's
 // module entry points) every pass keeps the interpreting kernel.  A compiled
-// kernel is cached per (device, source text) for the life of the process.
+// kernel is cached per (device, source text) for the life of the process and
+// found by program structure (jit_program_kernels) or batched program
+// (jit_batch_lookup).  Compiles run on host threads, at most one per host core
+// across the process; a module load pauses the device's serving sessions
+// (a load waits for every resident kernel to end).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <dlfcn.h>
@@ -59,9 +67,18 @@ struct Src {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
+    const int n = vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
-    s += buf;
+    if (n >= (int)sizeof(buf)) {  // a longer line: format it again at its length
+      std::string big((size_t)n + 1, '\0');
+      va_start(ap, fmt);
+      vsnprintf(&big[0], big.size(), fmt, ap);
+      va_end(ap);
+      big.resize((size_t)n);
+      s += big;
+    } else if (n > 0) {
+      s += buf;
+    }
     s += '\n';
   }
 };

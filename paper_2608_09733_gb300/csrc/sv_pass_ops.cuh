@@ -2,10 +2,11 @@
 // register ops (every register slot a compile-time constant), the register
 // loads and stores of a phase, the shared-memory ops of wide gates and the
 // direct store of a last register phase to the state.  Included by the
-// library's interpreting pass kernel (sv_sweep.cu) and by the pass kernels
+// library's interpreting pass kernel (sv_sweep.cu), by the pass kernels
 // compiled at run time from one program (sv_jit.cpp), which call the same
-// functions with constant arguments, so both paths round alike.  Device code
-// only, no host headers.
+// functions with constant arguments, so both paths round alike, and by the
+// batched adjoint sweeps (sv_batch_ops.cuh: the complex product and the bit
+// helpers).  Device code only, no host headers.
 #pragma once
 
 #include "sv_prog_layout.h"
