@@ -100,3 +100,16 @@ def test_adjoint_template_kernels_compile(svlib):
         assert ns > 0 and nc == ns, text[:2000]
     ns, nc, text = B.sv_jit_check_adjoint(3, B.SV_C64, hea_ring(3, 2), 12, compile=True)
     assert ns > 0 and nc == ns and "in shared memory" in text, text[:2000]
+
+
+def test_sources_depend_on_structure_not_angles(svlib):
+    """Kernels are kept by program structure: two circuits of the same gates
+    at other angles write the same kernel sources (coefficients are read at
+    run time), while a circuit of another structure writes others."""
+    from workloads import serving_circuit
+    n = 24
+    a = B.sv_jit_check(n, B.SV_C64, fused_layered_u3_cz(n, 4, seed=11), fuse_max_k=5, compile=False)
+    b = B.sv_jit_check(n, B.SV_C64, fused_layered_u3_cz(n, 4, seed=12), fuse_max_k=5, compile=False)
+    assert a[0] > 0 and a == b
+    c = B.sv_jit_check(n, B.SV_C64, serving_circuit(n, 4, 11), fuse_max_k=5, compile=False)
+    assert c[2] != a[2]
