@@ -429,7 +429,16 @@ sv_status sv_small_session_stop(sv_small_session* s);
  * out_z (host, n_qubits + 1 doubles, as sv_expect_z_all) and, when
  * state_out is not NULL, copies the final state back to it (host).  The
  * device buffer is kept per stream and reused by later calls of the same
- * or smaller size.  Synchronizes `stream`. */
+ * or smaller size.  Synchronizes `stream`.
+ * Host state buffers (here and in sv_set_state / sv_get_state) must hold
+ * 2^n amplitudes of dtype.  When one is page-locked memory mapped into the
+ * device at the same address (cudaHostAlloc / cudaMallocHost, pinned torch
+ * tensors) and 16-byte aligned, the copy runs as a kernel of SM loads and
+ * stores over the CPU-GPU link (launched on `stream`, family "host_load" /
+ * "host_store" in the kernel timing below); on GB300 this keeps its rate when
+ * the link has been idle, where a copy-engine transfer started behind the
+ * circuit's kernels was measured several times slower.  Any other host
+ * memory is copied with cudaMemcpyAsync. */
 sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const sv_gate* gates, size_t n_gates,
                       const double* param_values, size_t n_param_values, int fuse_max_k, double* out_z,
                       void* state_out, void* stream);

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
 SV_C64, SV_C128 = 0, 1
 STATUS = {0: "SV_OK", 1: "SV_ERR_INVALID", 2: "SV_ERR_UNSUPPORTED", 3: "SV_ERR_OOM", 4: "SV_ERR_CUDA",
           5: "SV_ERR_TIMEOUT", 6: "SV_ERR_UNBOUND_PARAM"}
+SV_ERR_INVALID = 1
 
 GATE_TYPES = {
     "i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,
@@ -395,14 +396,27 @@ def sv_emulate_apply(state: np.ndarray, n: int, dtype: int, gates, param_values=
     return state
 
 
+def _host_state(a, n: int, dtype: int, what: str, writable: bool = False):
+    """Pointer to a host array holding exactly 2^n amplitudes of dtype: the C
+    side copies that many bytes, so a shorter, strided or read-only target is
+    refused here."""
+    want = np.complex64 if dtype == SV_C64 else np.complex128
+    if not isinstance(a, np.ndarray) or a.dtype != want or a.size != (1 << n) or not a.flags.c_contiguous:
+        raise SvError(SV_ERR_INVALID, "%s must be a C-contiguous %s numpy array of 2^%d amplitudes"
+                      % (what, np.dtype(want).name, n))
+    if writable and not a.flags.writeable:
+        raise SvError(SV_ERR_INVALID, "%s is read-only" % what)
+    return ctypes.c_void_p(a.ctypes.data)
+
+
 def sv_run_host(n: int, dtype: int, gates, param_values=None, fuse_max_k: int = 0, state_in=None,
                 state_out=None, stream=None) -> np.ndarray:
     """End-to-end on host buffers (numpy): returns (<Z_q>..., sum)."""
     g = gates if isinstance(gates, (Gates, GateArray)) else Gates(gates)
     pp, npv, _keep = _params(param_values)
     out = np.zeros(n + 1, dtype=np.float64)
-    sin = ctypes.c_void_p(state_in.ctypes.data) if state_in is not None else None
-    sout = ctypes.c_void_p(state_out.ctypes.data) if state_out is not None else None
+    sin = _host_state(state_in, n, dtype, "state_in") if state_in is not None else None
+    sout = _host_state(state_out, n, dtype, "state_out", writable=True) if state_out is not None else None
     st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
     _check(load().sv_run_host(n, dtype, sin, g.arr, g.n, pp, npv, int(fuse_max_k),
                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sout, st))
@@ -424,7 +438,7 @@ class SvState:
         return load().sv_state_ptr(self.handle)
 
     def set(self, host: np.ndarray):
-        _check(load().sv_set_state(self.handle, ctypes.c_void_p(host.ctypes.data), 0))
+        _check(load().sv_set_state(self.handle, _host_state(host, self.n, self.dtype, "host"), 0))
 
     def get(self) -> np.ndarray:
         out = np.zeros(1 << self.n, dtype=np.complex64 if self.dtype == SV_C64 else np.complex128)

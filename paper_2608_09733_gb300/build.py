@@ -22,7 +22,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsv.so")
 
 SOURCES = ["sv_plan.cpp", "sv_program.cpp", "sv_api.cpp", "sv_adjoint_host.cpp", "sv_serve.cpp", "sv_jit.cpp",
-           "sv_sweep.cu", "sv_reduce.cu", "sv_adjoint.cu", "sv_noalloc.cu", "sv_sample.cu"]
+           "sv_sweep.cu", "sv_reduce.cu", "sv_adjoint.cu", "sv_noalloc.cu", "sv_sample.cu",
+           "sv_hostcopy.cu"]
 # Device headers the run-time compiled pass kernels include (sv_jit.cpp): their
 # text is embedded in the library, so a kernel compiled at run time is built
 # from the same code as the library's own pass kernel.

@@ -21,6 +21,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "sv_hostcopy.h"
 #include "sv_internal.h"
 
 namespace sv {
@@ -498,7 +499,7 @@ sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const 
     const size_t bytes = amp_bytes(dtype) << n_qubits;
     Workspace& w = workspace(s, expect_z_all_scratch_doubles(n_qubits), n_qubits + 1, bytes);
     if (state_in) {
-      cuda_check(cudaMemcpyAsync(w.state, state_in, bytes, cudaMemcpyHostToDevice, s), "state upload");
+      cuda_check(copy_state_host(w.state, state_in, bytes, false, s), "state upload");
     } else if (dtype == SV_C64) {
       cuda_check(launch_init_basis<float>((Cx<float>*)w.state, n_qubits, 0, s), "init launch");
     } else {
@@ -509,7 +510,7 @@ sv_status sv_run_host(int n_qubits, sv_dtype dtype, const void* state_in, const 
     cuda_check(cudaMemcpyAsync(out_z, w.out, (n_qubits + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
                "result copy");
     if (state_out)
-      cuda_check(cudaMemcpyAsync(state_out, w.state, bytes, cudaMemcpyDeviceToHost, s), "state download");
+      cuda_check(copy_state_host(state_out, w.state, bytes, true, s), "state download");
     sync_stream(s);
   });
 }
@@ -551,8 +552,8 @@ sv_status sv_set_state(sv_handle h, const void* src, int src_is_device) {
   return guarded([&] {
     if (!h || !src) fail(SV_ERR_INVALID, "NULL handle or source");
     if (src_is_device) check_device_buffer(src, h->bytes, "src");
-    cuda_check(cudaMemcpyAsync(h->ptr, src, h->bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                               h->stream),
+    cuda_check(src_is_device ? cudaMemcpyAsync(h->ptr, src, h->bytes, cudaMemcpyDeviceToDevice, h->stream)
+                             : copy_state_host(h->ptr, src, h->bytes, false, h->stream),
                "state copy");
     sync_stream(h->stream);
   });
@@ -562,8 +563,8 @@ sv_status sv_get_state(sv_handle h, void* dst, int dst_is_device) {
   return guarded([&] {
     if (!h || !dst) fail(SV_ERR_INVALID, "NULL handle or destination");
     if (dst_is_device) check_device_buffer(dst, h->bytes, "dst");
-    cuda_check(cudaMemcpyAsync(dst, h->ptr, h->bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                               h->stream),
+    cuda_check(dst_is_device ? cudaMemcpyAsync(dst, h->ptr, h->bytes, cudaMemcpyDeviceToDevice, h->stream)
+                             : copy_state_host(dst, h->ptr, h->bytes, true, h->stream),
                "state copy");
     sync_stream(h->stream);
   });

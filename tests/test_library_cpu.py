@@ -163,3 +163,25 @@ def test_double_excitation_lowering_identity():
             ry = Gate("ry", [t0], [t1, t2, t3] + ctrl, [0, 1, 0] + cs, params=[th])
             lowered = oracle.run(n, perm + [ry] + perm[::-1], init=init.copy())
             assert np.abs(direct - lowered).max() < 1e-13
+
+
+def test_host_state_arrays_are_checked_before_the_call(svlib):
+    """sv_run_host and SvState.set copy 2^n amplitudes of the dtype, so the
+    binding refuses a host array that is shorter, of another dtype, strided or
+    (for state_out) read-only before anything reaches the library."""
+    n = 4
+    good = np.zeros(2 ** n, dtype=np.complex64)
+    ro = np.zeros(2 ** n, dtype=np.complex64)
+    ro.flags.writeable = False
+    bad_in = [np.zeros(2 ** n - 1, dtype=np.complex64), np.zeros(2 ** n, dtype=np.complex128),
+              np.zeros(2 ** (n + 1), dtype=np.complex64)[::2], [0j] * 2 ** n]
+    for b in bad_in:
+        with pytest.raises(B.SvError) as e:
+            B.sv_run_host(n, B.SV_C64, [], state_in=b)
+        assert e.value.status == 1
+        with pytest.raises(B.SvError):
+            B.sv_run_host(n, B.SV_C64, [], state_out=b)
+    with pytest.raises(B.SvError):
+        B.sv_run_host(n, B.SV_C64, [], state_out=ro)
+    assert B._host_state(good, n, B.SV_C64, "x").value == good.ctypes.data
+    assert B._host_state(ro, n, B.SV_C64, "x").value == ro.ctypes.data  # reading is fine
