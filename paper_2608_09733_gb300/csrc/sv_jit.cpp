@@ -89,6 +89,68 @@ struct Src {
 constexpr int kJitGroups = 4;
 constexpr int kJitGroupThreads = 128;
 
+// 128-byte lines that warp 0's stores touch, summed over its store
+// instructions, when the last register phase `ph` writes its registers
+// straight to the state (16-byte pairs with local bit 0 in slot 0, else
+// 8-byte stores).  A coalesced store of 32 lanes touches 4 lines (16-byte) or
+// 2 (8-byte): 64 in all.  When the phase holds the tile's low local bits in
+// registers, the lanes differ only in high bits and every store instruction
+// lands in up to 32 lines, each written in part: the L1 data pipe, which also
+// carries the register phases' shared-memory traffic, then takes 8x the
+// wavefronts (measured: 1.4 ms against 0.66 ms for a 28-qubit pass of the
+// same traffic).
+int direct_store_lines(const ProgramHeader& h, const Phase& ph, int rq) {
+  const bool pairs = ph.rp[0] == 0;
+  int lines = 0;
+  for (int j = 0; j < (1 << rq); j += pairs ? 2 : 1) {
+    uint64_t seen[32];
+    int ns = 0;
+    for (uint32_t lane = 0; lane < 32; lane++) {
+      uint32_t l = lane;
+      for (int i = 0; i < rq; i++) {
+        const uint32_t lo = l & ((1u << ph.rp[i]) - 1u);
+        l = ((l >> ph.rp[i]) << (ph.rp[i] + 1)) | lo;
+      }
+      for (int i = 0; i < rq; i++)
+        if ((j >> i) & 1) l |= 1u << ph.rp[i];
+      uint64_t g = 0;
+      for (int b = 0; b < h.m; b++)
+        if ((l >> b) & 1u) g |= 1ull << h.tq[b];
+      const uint64_t line = (g * 8ull) >> 7;
+      bool dup = false;
+      for (int t = 0; t < ns && !dup; t++) dup = seen[t] == line;
+      if (!dup) seen[ns++] = line;
+    }
+    lines += ns;
+  }
+  return lines;
+}
+// The last register phase stores through shared memory and a coalesced copy
+// (one more store and load of the tile in shared memory, 128 + 128 wavefronts
+// a warp at best) when its direct stores would touch more lines than this.
+constexpr int kDirectStoreMaxLines = 256;
+
+// The copy of a tile from its stage in shared memory to the state, in 16-byte
+// chunks: thread t of the group takes chunks t + 128 k (k < 16), so its local
+// bits 1..7 come from t and bits 8..11 from k.  Tile offsets and the swizzle
+// are both linear over XOR, so the thread's part is formed once and each
+// chunk adds a constant.
+void emit_copy_out(Src& o, const ProgramHeader& h) {
+  o.line("  {  // the tile to the state, 16-byte chunks, lanes on consecutive chunks");
+  o.line("    uint64_t t0 = 0;");
+  for (int b = 0; b < 7; b++) o.line("    t0 |= (uint64_t)((gr.tid >> %d) & 1u) << %d;", b, h.tq[b + 1]);
+  o.line("    const uint32_t p0 = phys<float>(gr.tid << 1);");
+  for (int k = 0; k < 16; k++) {
+    uint64_t go = 0;
+    for (int i = 0; i < 4; i++)
+      if ((k >> i) & 1) go |= 1ull << h.tq[8 + i];
+    const uint32_t l = (uint32_t)k << 8, pk = l ^ ((l >> 3) & 14u);
+    o.line("    *reinterpret_cast<uint4*>(state + (base | t0 | 0x%llxull)) = *reinterpret_cast<const uint4*>(s + (p0 ^ %uu));",
+           (unsigned long long)go, pk);
+  }
+  o.line("  }");
+}
+
 // The condition of an op on the bits outside the tile and on the thread's
 // bits (empty when the op applies everywhere).
 std::string op_guard(const DevOp& op, uint32_t code) {
@@ -108,7 +170,12 @@ std::string op_guard(const DevOp& op, uint32_t code) {
 }
 
 // One register op (not a sign flip), as apply_reg of the interpreting kernel
-// dispatches it, with every dispatch decision taken here.
+// dispatches it, with every dispatch decision taken here.  Coefficients at an
+// offset known here are read from the program in kernel-parameter space
+// (`pc`, the constant bank): they are the same for every thread, so they cost
+// no shared-memory instruction, and the values are those of the pool copy in
+// shared memory (`cf`), which keeps the reads whose offset depends on the
+// thread or the tile.
 template <typename R>
 void emit_reg_op(Src& o, const DevOp& op, int op_index, int rq) {
   const uint32_t code = op.pad;
@@ -121,7 +188,7 @@ void emit_reg_op(Src& o, const DevOp& op, int op_index, int rq) {
     case OPK_KRON:
       for (int S = 0; S < rq; S++)
         if (rm & (1u << S)) {
-          o.line("      r_u1<%s, %d, %d>(v, cf + %u);", Rn, rq, S, C + 4u * S);
+          o.line("      r_u1<%s, %d, %d>(v, pc + %u);", Rn, rq, S, C + 4u * S);
           o.line("      asm volatile(\"\" ::: \"memory\");");
         }
       break;
@@ -129,7 +196,7 @@ void emit_reg_op(Src& o, const DevOp& op, int op_index, int rq) {
       for (int S = 0; S < rq; S++)
         if (rm & (1u << S)) {
           const bool cot = sizeof(R) == 8 && ((rv >> S) & 1u);
-          o.line("      r_rot<%s, %d, %d, %s>(v, cf[%u]);", Rn, rq, S, cot ? "true" : "false", C + S);
+          o.line("      r_rot<%s, %d, %d, %s>(v, pc[%u]);", Rn, rq, S, cot ? "true" : "false", C + S);
           o.line("      asm volatile(\"\" ::: \"memory\");");
         }
       break;
@@ -146,7 +213,7 @@ void emit_reg_op(Src& o, const DevOp& op, int op_index, int rq) {
         var += buf;
       }
       if (var.empty())
-        o.line("      r_phase_table<%s, %d>(v, cf + %u);", Rn, rq, C);
+        o.line("      r_phase_table<%s, %d>(v, pc + %u);", Rn, rq, C);
       else
         o.line("      r_phase_table<%s, %d>(v, cf + %u + (%s) * %du);", Rn, rq, C, var.c_str(),
                table_stride<R>(rq));
@@ -155,13 +222,13 @@ void emit_reg_op(Src& o, const DevOp& op, int op_index, int rq) {
     case OPK_DENSE:
     case OPK_REAL:
       if (op.k == 1)
-        o.line("      r_dense1<%s, %d, %d, %s>(v, cf + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0],
+        o.line("      r_dense1<%s, %d, %d, %s>(v, pc + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0],
                kind == OPK_REAL ? "true" : "false", C, rm, rv);
       else
-        o.line("      r_dense2<%s, %d, %d, %d>(v, cf + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0], op.rs[1], C, rm, rv);
+        o.line("      r_dense2<%s, %d, %d, %d>(v, pc + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0], op.rs[1], C, rm, rv);
       break;
     case OPK_ANTIDIAG:
-      o.line("      r_anti1<%s, %d, %d, %s>(v, cf + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0],
+      o.line("      r_anti1<%s, %d, %d, %s>(v, pc + %u, 0x%xu, 0x%xu);", Rn, rq, op.rs[0],
              (fl & OPF_FLIP) ? "true" : "false", C, rm, rv);
       break;
     case OPK_SWAP:
@@ -197,12 +264,13 @@ std::string jit_source(const SweepProgram<R>& P) {
   o.line("  __device__ __forceinline__ void operator()(Cx<%s>* s, const Cx<%s>* cf, uint64_t base, const Grp& gr,", Rn,
          Rn);
   o.line("                                             Cx<%s>* __restrict__ state, const Release& release) const {", Rn);
+  o.line("  const Cx<%s>* __restrict__ pc = P.coef;", Rn);
   bool direct_done = false;
   for (int p = 0; p < h.nphases; p++) {
     const Phase& ph = P.ph[p];
     const bool last = p == h.nphases - 1;
     if (ph.kind == PH_REG) {
-      const bool direct = last;
+      const bool direct = last && direct_store_lines(h, ph, rq) <= kDirectStoreMaxLines;
       o.line("  {  // phase %d: register slots at local bits %d %d %d %d %d", p, ph.rp[0], ph.rp[1], ph.rp[2],
              ph.rp[3], ph.rp[4]);
       const bool all_active = (1 << ph.ntpos) >= kJitGroupThreads;
@@ -281,7 +349,7 @@ std::string jit_source(const SweepProgram<R>& P) {
     }
   }
   if (!direct_done) {
-    o.line("  stage_copy_out<%s>(s, %d, state, base, P.h, gr);", Rn, 1 << h.m);
+    emit_copy_out(o, h);
     o.line("  grp_sync(gr);");
     o.line("  release();");
   }
