@@ -126,25 +126,136 @@ int direct_store_lines(const ProgramHeader& h, const Phase& ph, int rq) {
   return lines;
 }
 // The last register phase stores through shared memory and a coalesced copy
-// (one more store and load of the tile in shared memory, 128 + 128 wavefronts
-// a warp at best) when its direct stores would touch more lines than this.
-constexpr int kDirectStoreMaxLines = 256;
+// when its direct stores would touch more lines than this a warp: the copy
+// costs a warp 64 wavefronts to store the phase in shared memory, 64 to load
+// it back and 64 lines of stores, 192 in all.
+constexpr int kDirectStoreMaxLines = 192;
+
+// ---------------------------------------------------------------- layouts
+//
+// Where a tile sits in shared memory between two phases.  Local amplitude l
+// is at slot l ^ (XOR of col[b - 4] over the set bits b >= 4 of l), every col
+// a value in slot bits 1..3: slot bit 0 is l's own, so 16-byte pairs stay
+// whole and in order, and bits 1..3 change by a function of bits 4..11 only,
+// so the map is one to one.  The TMA copies leave a stage in the 128-byte
+// swizzle (phys()): bits 4, 5, 6 into slot bits 1, 2, 3.  Between two
+// register phases (and before the copy-out) the layout is free, and the one
+// picked lets both the phase that stores the tile and the one that loads it
+// reach every bank: with phys() alone, a phase holding local bits 1..4 in
+// registers and 16-byte pairs (or one whose lanes cannot spread over the
+// 8-byte banks) takes its accesses in two or four times the wavefronts.
+struct Layout {
+  uint32_t col[8];
+};
+constexpr Layout kPhysLayout = {{2u, 4u, 8u, 0u, 0u, 0u, 0u, 0u}};
+
+uint32_t slot_of(const Layout& L, uint32_t l) {
+  uint32_t s = l;
+  for (int b = 4; b < 12; b++)
+    if ((l >> b) & 1u) s ^= L.col[b - 4];
+  return s;
+}
+
+// The local bits a register phase's lanes hold: the thread's bits (the tile
+// bits not in registers, ascending, as ins0 deposits them), the lowest five.
+void lane_bits(const uint8_t* rp, int rq, int (&lb)[5]) {
+  int n = 0;
+  for (int b = 0; b < 12 && n < 5; b++) {
+    bool reg = false;
+    for (int i = 0; i < rq; i++) reg = reg || rp[i] == b;
+    if (!reg) lb[n++] = b;
+  }
+}
+
+// How many times the conflict-free count of wavefronts one warp access takes
+// through L.  16-byte pairs go a quarter-warp at a time (lanes 0..7 should
+// reach the 8 granules of a 128-byte row); 8-byte amplitudes a half-warp at
+// a time (lanes 0..15 over 16 eight-byte banks).  The lanes' other bits add
+// the same XOR to every slot, so they do not matter.
+int access_ways(const Layout& L, const int (&lb)[5], bool pairs) {
+  const int g = pairs ? 3 : 4;
+  int count[16] = {0};
+  int worst = 0;
+  for (int x = 0; x < (1 << g); x++) {
+    uint32_t l = 0;
+    for (int i = 0; i < g; i++)
+      if ((x >> i) & 1) l |= 1u << lb[i];
+    const uint32_t sl = slot_of(L, l);
+    const uint32_t key = pairs ? (sl >> 1) & 7u : sl & 15u;
+    worst = std::max(worst, ++count[key]);
+  }
+  return worst;
+}
+
+// The layout of the boundary after register phase `st`, loaded next by
+// register phase `ld` or (ld == nullptr) by the copy-out, whose lanes take
+// local bits 1..5 in 16-byte pairs.  Candidates come in a fixed order, phys()
+// first, so a program always gets the same source: the first whose accesses
+// on both sides are conflict-free, else the best seen.
+Layout choose_layout(const Phase& st, const Phase* ld, int rq) {
+  int lst[5], lld[5];
+  lane_bits(st.rp, rq, lst);
+  const bool pst = st.rp[0] == 0;
+  bool pld = true;
+  if (ld) {
+    lane_bits(ld->rp, rq, lld);
+    pld = ld->rp[0] == 0;
+  } else {
+    for (int i = 0; i < 5; i++) lld[i] = i + 1;
+  }
+  auto cost = [&](const Layout& L) { return access_ways(L, lst, pst) + access_ways(L, lld, pld); };
+  Layout best = kPhysLayout;
+  int bc = cost(best);
+  uint32_t x = 0x9E3779B9u;
+  for (int t = 0; t < 20000 && bc > 2; t++) {
+    Layout L;
+    for (int b = 0; b < 8; b++) {
+      x ^= x << 13;
+      x ^= x >> 17;
+      x ^= x << 5;
+      L.col[b] = ((x >> 7) & 7u) << 1;
+    }
+    const int c = cost(L);
+    if (c < bc) {
+      best = L;
+      bc = c;
+    }
+  }
+  return best;
+}
+
+// Code forming `name`, the slot of the thread's base index tb in layout L.
+void emit_slot_of_tb(Src& o, const char* name, const Layout& L, const uint8_t* rp, int rq) {
+  o.line("    uint32_t %s = tb;", name);
+  for (int b = 4; b < 12; b++) {
+    bool reg = false;
+    for (int i = 0; i < rq; i++) reg = reg || rp[i] == b;
+    if (!reg && L.col[b - 4]) o.line("    %s ^= (tb & 0x%xu) ? 0x%xu : 0u;", name, 1u << b, L.col[b - 4]);
+  }
+}
+
+std::string slots_of_bits(const Layout& L, const uint8_t* rp, int rq) {
+  std::string ms;
+  for (int i = 0; i < rq; i++) ms += (i ? ", " : "") + std::to_string(slot_of(L, 1u << rp[i])) + "u";
+  return ms;
+}
 
 // The copy of a tile from its stage in shared memory to the state, in 16-byte
 // chunks: thread t of the group takes chunks t + 128 k (k < 16), so its local
 // bits 1..7 come from t and bits 8..11 from k.  Tile offsets and the swizzle
 // are both linear over XOR, so the thread's part is formed once and each
-// chunk adds a constant.
-void emit_copy_out(Src& o, const ProgramHeader& h) {
+// chunk adds a constant.  L is the layout the tile is in.
+void emit_copy_out(Src& o, const ProgramHeader& h, const Layout& L) {
   o.line("  {  // the tile to the state, 16-byte chunks, lanes on consecutive chunks");
   o.line("    uint64_t t0 = 0;");
   for (int b = 0; b < 7; b++) o.line("    t0 |= (uint64_t)((gr.tid >> %d) & 1u) << %d;", b, h.tq[b + 1]);
-  o.line("    const uint32_t p0 = phys<float>(gr.tid << 1);");
+  o.line("    uint32_t p0 = 0;");
+  for (int b = 0; b < 7; b++) o.line("    p0 ^= (gr.tid & 0x%xu) ? 0x%xu : 0u;", 1u << b, slot_of(L, 2u << b));
   for (int k = 0; k < 16; k++) {
     uint64_t go = 0;
     for (int i = 0; i < 4; i++)
       if ((k >> i) & 1) go |= 1ull << h.tq[8 + i];
-    const uint32_t l = (uint32_t)k << 8, pk = l ^ ((l >> 3) & 14u);
+    const uint32_t pk = slot_of(L, (uint32_t)k << 8);
     o.line("    *reinterpret_cast<uint4*>(state + (base | t0 | 0x%llxull)) = *reinterpret_cast<const uint4*>(s + (p0 ^ %uu));",
            (unsigned long long)go, pk);
   }
@@ -266,11 +377,17 @@ std::string jit_source(const SweepProgram<R>& P) {
   o.line("                                             Cx<%s>* __restrict__ state, const Release& release) const {", Rn);
   o.line("  const Cx<%s>* __restrict__ pc = P.coef;", Rn);
   bool direct_done = false;
+  Layout lin = kPhysLayout;  // the layout the next phase finds the tile in
   for (int p = 0; p < h.nphases; p++) {
     const Phase& ph = P.ph[p];
     const bool last = p == h.nphases - 1;
     if (ph.kind == PH_REG) {
       const bool direct = last && direct_store_lines(h, ph, rq) <= kDirectStoreMaxLines;
+      const Layout lout = direct                             ? kPhysLayout
+                          : last                             ? choose_layout(ph, nullptr, rq)
+                          : P.ph[p + 1].kind == PH_REG ? choose_layout(ph, &P.ph[p + 1], rq)
+                                                             : kPhysLayout;
+      const char* pairs = ph.rp[0] == 0 ? "true" : "false";
       o.line("  {  // phase %d: register slots at local bits %d %d %d %d %d", p, ph.rp[0], ph.rp[1], ph.rp[2],
              ph.rp[3], ph.rp[4]);
       const bool all_active = (1 << ph.ntpos) >= kJitGroupThreads;
@@ -281,7 +398,9 @@ std::string jit_source(const SweepProgram<R>& P) {
       o.line("    const uint32_t m[%d] = {%s};", rq, ms.c_str());
       o.line("    Cx<%s> v[%d];", Rn, 1 << rq);
       const std::string act = all_active ? "" : "if (gr.tid < " + std::to_string(1u << ph.ntpos) + "u) ";
-      o.line("    %sreg_load<%s, %d>(v, s, tb, m);", act.c_str(), Rn, rq);
+      emit_slot_of_tb(o, "si", lin, ph.rp, rq);
+      o.line("    const uint32_t mi[%d] = {%s};", rq, slots_of_bits(lin, ph.rp, rq).c_str());
+      o.line("    %sreg_load_at<%s, %d, %s>(v, s, si, mi);", act.c_str(), Rn, rq, pairs);
       if (direct) {
         o.line("    grp_sync(gr);  // every thread has its registers: the stage is free");
         o.line("    release();");
@@ -319,11 +438,14 @@ std::string jit_source(const SweepProgram<R>& P) {
         o.line("    reg_store_global<%s, %d>(v, state, base | toff, gs, %s);", Rn, rq, ph.rp[0] == 0 ? "true" : "false");
         direct_done = true;
       } else {
-        o.line("    reg_store<%s, %d>(v, s, tb, m);", Rn, rq);
+        emit_slot_of_tb(o, "so", lout, ph.rp, rq);
+        o.line("    const uint32_t mo[%d] = {%s};", rq, slots_of_bits(lout, ph.rp, rq).c_str());
+        o.line("    reg_store_at<%s, %d, %s>(v, s, so, mo);", Rn, rq, pairs);
       }
       o.line("    }");
       o.line("  }");
       if (!direct) o.line("  grp_sync(gr);");
+      lin = lout;
     } else {
       const DevOp& op = P.ops[ph.first];
       const uint32_t C = op.coef;
@@ -346,10 +468,11 @@ std::string jit_source(const SweepProgram<R>& P) {
       }
       o.line("  }");
       o.line("  grp_sync(gr);");
+      lin = kPhysLayout;  // the shared-memory ops address the tile through phys()
     }
   }
   if (!direct_done) {
-    emit_copy_out(o, h);
+    emit_copy_out(o, h, lin);
     o.line("  grp_sync(gr);");
     o.line("  release();");
   }

@@ -284,6 +284,62 @@ __device__ __forceinline__ void reg_slots(uint32_t (&off)[(1 << RQ) / STEP], uin
   }
 }
 
+// Register loads and stores through any layout that is linear over XOR, as
+// the kernels compiled from one program use between two register phases:
+// s0 is the slot of the thread's base index tb and ms[i] the slot of
+// register bit i alone, so combination j sits at s0 ^ (XOR of ms[i] over the
+// set bits i of j).  PAIRS: register bit 0 is local bit 0 and the layout
+// keeps pairs (j, j+1) in one 16-byte granule, in order.
+template <int RQ, int STEP>
+__device__ __forceinline__ void reg_slots_at(uint32_t (&off)[(1 << RQ) / STEP], uint32_t s0,
+                                             const uint32_t (&ms)[RQ]) {
+  off[0] = s0;
+#pragma unroll
+  for (int j = STEP; j < (1 << RQ); j += STEP) {
+    const int low = j & -j;
+    const int i = low == 1 ? 0 : low == 2 ? 1 : low == 4 ? 2 : low == 8 ? 3 : 4;
+    off[j / STEP] = off[(j ^ low) / STEP] ^ ms[i];
+  }
+}
+
+template <typename R, int RQ, bool PAIRS>
+__device__ __forceinline__ void reg_load_at(Cx<R> (&v)[1 << RQ], const Cx<R>* s, uint32_t s0,
+                                            const uint32_t (&ms)[RQ]) {
+  if constexpr (PAIRS && sizeof(Cx<R>) == 8) {
+    uint32_t off[(1 << RQ) / 2];
+    reg_slots_at<RQ, 2>(off, s0, ms);
+#pragma unroll
+    for (int j = 0; j < (1 << RQ); j += 2) {
+      const float4 w = *reinterpret_cast<const float4*>(s + off[j / 2]);
+      v[j] = Cx<R>{(R)w.x, (R)w.y};
+      v[j + 1] = Cx<R>{(R)w.z, (R)w.w};
+    }
+  } else {
+    uint32_t off[1 << RQ];
+    reg_slots_at<RQ, 1>(off, s0, ms);
+#pragma unroll
+    for (int j = 0; j < (1 << RQ); j++) v[j] = s[off[j]];
+  }
+}
+
+template <typename R, int RQ, bool PAIRS>
+__device__ __forceinline__ void reg_store_at(const Cx<R> (&v)[1 << RQ], Cx<R>* s, uint32_t s0,
+                                             const uint32_t (&ms)[RQ]) {
+  if constexpr (PAIRS && sizeof(Cx<R>) == 8) {
+    uint32_t off[(1 << RQ) / 2];
+    reg_slots_at<RQ, 2>(off, s0, ms);
+#pragma unroll
+    for (int j = 0; j < (1 << RQ); j += 2)
+      *reinterpret_cast<float4*>(s + off[j / 2]) =
+          make_float4((float)v[j].re, (float)v[j].im, (float)v[j + 1].re, (float)v[j + 1].im);
+  } else {
+    uint32_t off[1 << RQ];
+    reg_slots_at<RQ, 1>(off, s0, ms);
+#pragma unroll
+    for (int j = 0; j < (1 << RQ); j++) s[off[j]] = v[j];
+  }
+}
+
 template <typename R, int RQ>
 __device__ __forceinline__ void reg_load(Cx<R> (&v)[1 << RQ], const Cx<R>* s, uint32_t tb, const uint32_t (&m)[RQ]) {
   if (sizeof(Cx<R>) == 8 && m[0] == 1u) {  // pairs (j, j+1) share a 16-byte granule
