@@ -113,3 +113,118 @@ def test_sources_depend_on_structure_not_angles(svlib):
     assert a[0] > 0 and a == b
     c = B.sv_jit_check(n, B.SV_C64, serving_circuit(n, 4, 11), fuse_max_k=5, compile=False)
     assert c[2] != a[2]
+
+
+# ---- the shared-memory layouts of the compiled passes, executed on the CPU
+
+def _phys(l):
+    return l ^ ((l >> 3) & 14)
+
+
+def _ins0(x, p):
+    return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1))
+
+
+def _xors(block, name, var):
+    return [(int(a, 16), int(b, 16)) for a, b in
+            re.findall(r"%s \^= \(%s & 0x([0-9a-f]+)u\) \? 0x([0-9a-f]+)u : 0u;" % (name, var), block)]
+
+
+def _apply(x, start, xs):
+    for mask, c in xs:
+        if x & mask:
+            start ^= c
+    return start
+
+
+def _consts(block, name):
+    return [int(v.strip().rstrip('u')) for v in
+            re.search(r"const uint32_t %s\[5\] = \{([^}]*)\}" % name, block).group(1).split(',')]
+
+
+def _phase_maps(block):
+    """Local index -> shared-memory slot of a register phase's loads and (if
+    it stores to shared memory) stores, from the source's own constants."""
+    bits = [int(x) for x in re.search(r"register slots at local bits ([\d ]+)", block).group(1).split()]
+    pairs = "true" if bits[0] == 0 else "false"
+    assert "reg_load_at<float, 5, %s>" % pairs in block
+    stores = "reg_store_at<float, 5, %s>" % pairs in block
+    mi, si = _consts(block, "mi"), _xors(block, "si", "tb")
+    mo, so = (_consts(block, "mo"), _xors(block, "so", "tb")) if stores else (None, None)
+    load, store = {}, ({} if stores else None)
+    for tid in range(128):
+        tb = tid
+        for b in bits:
+            tb = _ins0(tb, b)
+        for j in range(32):
+            l, a = tb, _apply(tb, tb, si)
+            c = _apply(tb, tb, so) if stores else None
+            for i in range(5):
+                if (j >> i) & 1:
+                    l |= 1 << bits[i]
+                    a ^= mi[i]
+                    if stores:
+                        c ^= mo[i]
+            load[l] = a
+            if stores:
+                store[l] = c
+    return bits[0] == 0, load, store
+
+
+def _check_pass_layouts(src):
+    phys = {l: _phys(l) for l in range(4096)}
+    starts = [m.start() for m in re.finditer(r"\{  // phase \d+:", src)] + [len(src)]
+    maps = []
+    for a, b in zip(starts, starts[1:]):
+        block = src[a:b]
+        if "register slots" in block:
+            maps.append(_phase_maps(block))
+        else:  # a shared-memory op phase addresses the tile through phys()
+            maps.append((False, phys, phys))
+    for pairs, load, store in maps:
+        for m in (load, store):
+            if m is None:
+                continue
+            assert sorted(m) == list(range(4096)) and sorted(m.values()) == list(range(4096))
+            if pairs:
+                assert all(m[l] % 2 == 0 and m[l + 1] == m[l] + 1 for l in range(0, 4096, 2))
+    assert maps[0][1] == phys  # the TMA copies leave the stage in the 128-byte swizzle
+    for k in range(1, len(maps)):
+        assert maps[k - 1][2] == maps[k][1], "phase %d does not load what phase %d stored" % (k, k - 1)
+    if "the tile to the state" not in src:
+        assert maps[-1][2] is None
+        return False
+    blk = src[src.index("the tile to the state"):]
+    p0 = _xors(blk, "p0", r"gr\.tid")
+    pk = [int(x) for x in re.findall(r"s \+ \(p0 \^ (\d+)u\)", blk)]
+    assert len(p0) == 7 and len(pk) == 16
+    seen = set()
+    for tid in range(128):
+        base = _apply(tid, 0, p0)
+        for k in range(16):
+            l = (tid << 1) | (k << 8)
+            assert base ^ pk[k] == maps[-1][2][l]
+            seen.add(l)
+    assert seen == set(range(0, 4096, 2))
+    return True
+
+
+def test_compiled_pass_layouts_are_consistent(svlib):
+    """Executes, for every thread and register combination, the shared-memory
+    slot arithmetic the generated sources carry: every phase's load and store
+    maps are one to one over the tile (16-byte pairs whole and in order), the
+    first phase reads the TMA copies' swizzle, each phase reads what the one
+    before it stored, and the copy-out reads what the last phase stored
+    (every pair once).  Circuits: the 28-qubit layered circuit (heavy passes
+    with picked layouts and copy-outs) and a random circuit with wide gates in
+    shared-memory phases."""
+    cases = [(28, fused_layered_u3_cz(28, 20, seed=0), 5, 0),
+             (21, random_circuit(21, 160, seed=921, max_controls=3, max_unitary_k=5), 5, 1)]
+    copy_outs = 0
+    for n, g, fuse, mode in cases:
+        ns, _, src = B.sv_jit_check(n, B.SV_C64, g, fuse_max_k=fuse, block_mode=mode, compile=False,
+                                    tile_qubits=12)
+        assert ns > 0
+        for p in src.split("// ----")[:ns]:
+            copy_outs += _check_pass_layouts(p)
+    assert copy_outs > 0
