@@ -391,7 +391,9 @@ sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits
  * sv_run_batch_small does) and writes sum_q <Z_q> and a done word back to
  * mapped memory.  A request costs no kernel launch (Sec. 9.3: small states
  * were launch-bound on the NPU).  Requests up to SV_SESSION_MAX_QUBITS qubits
- * (complex64; 12 for complex128), gates without parameter slots.
+ * (complex64, whose sessions run 512-thread CTAs with 128 KiB of shared
+ * memory for 14-qubit states; 12 qubits and 256 threads for complex128),
+ * gates without parameter slots.
  * Every device-side wait is bounded: a CTA that finds no published request
  * for wait_limit_s seconds records SV_ERR_TIMEOUT and ends; the next submit
  * relaunches the kernel, and sv_small_session_stop reports the timeout.
@@ -402,7 +404,7 @@ sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits
  * While a session is live, apply calls on the same device use the pass kernel
  * of 4 CTAs per SM (the TMA pass needs whole SMs).  A session belongs to the
  * device current at start; its calls are thread-safe. */
-#define SV_SESSION_MAX_QUBITS 13
+#define SV_SESSION_MAX_QUBITS 14
 typedef struct sv_small_session sv_small_session;
 /* capacity: requests in flight at most (1..2^20); arena_programs: pass
  * programs held for them (1..65536, about 32 KB each on the device). */

@@ -652,12 +652,12 @@ def sv_batch_expect_z_device(n: int, dtype: int, gates, params, out=None, stream
     return out
 
 
-SV_SESSION_MAX_QUBITS = 13
+SV_SESSION_MAX_QUBITS = 14
 
 
 class SmallSession:
     """A resident packed kernel fed from a work queue (sv_small_session_*):
-    submit small requests (n <= 13 complex64, 12 complex128), poll tickets,
+    submit small requests (n <= 14 complex64, 12 complex128), poll tickets,
     stop.  ``stop`` raises SvError(SV_ERR_TIMEOUT) when a device-side wait of
     the session ran out (it sat idle past ``wait_limit_s``)."""
 

@@ -137,6 +137,7 @@ void build_request_programs(int n, const sv_gate* gates, size_t ng, std::vector<
   std::memset(&o, 0, sizeof(o));
   Plan plan = make_plan(n, sizeof(R) == 4 ? SV_C64 : SV_C128, gates, ng, nullptr, 0, o, n);
   // whole state in one tile: 16 amplitudes a thread up to 12 qubits, 32 at 13
+  // and 14 (2^9 register groups: the session runs 512-thread CTAs for those)
   const int rq = n >= 13 ? 5 : kRegQ;
   const size_t k0 = out.size();
   out.resize(k0 + plan.sweeps.size());

@@ -484,27 +484,35 @@ __device__ __forceinline__ void run_small_request(const SweepProgram<R>* progs, 
       run_phases<R, 5, kRegQ, kOpsAll>(progs[p], progs[p].coef, s, tsz, 0ull, gr);
     }
   }
+  // the sum runs over the first kRedThreads threads in a fixed order, so a
+  // request's result does not depend on the CTA's size (the packed launch and
+  // both session kernels give the same bits)
+  constexpr int kRedThreads = 256;
   double acc = 0.0;
-  for (int a = threadIdx.x; a < tsz; a += blockDim.x) {
-    const Cx<R> x = s[phys<R>(a)];
-    acc += (double)(x.re * x.re + x.im * x.im) * (double)(n - 2 * __popc(a));
-  }
+  if (threadIdx.x < kRedThreads)
+    for (int a = threadIdx.x; a < tsz; a += kRedThreads) {
+      const Cx<R> x = s[phys<R>(a)];
+      acc += (double)(x.re * x.re + x.im * x.im) * (double)(n - 2 * __popc(a));
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if ((threadIdx.x & 31) == 0 && threadIdx.x < kRedThreads) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    for (int w = 0; w < kRedThreads / 32; w++) t += red[w];
     result = t;
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_small_session(SmallSessionDev d, const SweepProgram<R>* __restrict__ progs) {
+// NT threads a CTA: 256 (a register group of 16 or 32 amplitudes per thread
+// covers states up to 13 qubits), or 512 for sessions that take 14-qubit
+// complex64 requests (2^9 groups of 32; 128 KiB of shared memory).
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_small_session(SmallSessionDev d, const SweepProgram<R>* __restrict__ progs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* s = reinterpret_cast<Cx<R>*>(smem_raw);
-  __shared__ double red[8];
+  __shared__ double red[NT / 32];
   __shared__ long long s_ticket;
   __shared__ int s_stop;
   __shared__ double s_result;
@@ -886,21 +894,29 @@ cudaError_t launch_small_batch(const SweepProgram<R>* progs, const int* first_pr
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_small_session(const SmallSessionDev& d, const SweepProgram<R>* progs, int max_n, int grid,
-                                 cudaStream_t stream) {
-  const int smem = (int)sizeof(Cx<R>) << max_n;
+template <typename R, int NT>
+cudaError_t launch_small_session_nt(const SmallSessionDev& d, const SweepProgram<R>* progs, int smem, int grid,
+                                    cudaStream_t stream) {
   static int configured_bytes[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (smem > 48 * 1024 && smem > configured_bytes[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_small_session<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_small_session<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured_bytes[dev] = smem;
   }
-  k_small_session<R><<<grid, 256, smem, stream>>>(d, progs);
+  k_small_session<R, NT><<<grid, NT, smem, stream>>>(d, progs);
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_small_session(const SmallSessionDev& d, const SweepProgram<R>* progs, int max_n, int grid,
+                                 cudaStream_t stream) {
+  const int smem = (int)sizeof(Cx<R>) << max_n;
+  if constexpr (sizeof(R) == 4)
+    if (max_n >= 14) return launch_small_session_nt<R, 512>(d, progs, smem, grid, stream);
+  return launch_small_session_nt<R, 256>(d, progs, smem, grid, stream);
 }
 
 template cudaError_t launch_small_session<float>(const SmallSessionDev&, const SweepProgram<float>*, int, int,

@@ -4,7 +4,7 @@ Requests (arrival time, n qubits, depth, seed) each ask for sum_q <Z_q> of a
 layered U3 + CNOT-ladder circuit.  The loop admits them as they arrive and
 keeps many on the device at once:
 
-* small requests (n <= 13 for complex64, 12 for complex128) go to a serving
+* small requests (n <= 14 for complex64, 12 for complex128) go to a serving
   session (``SmallSession``): one kernel stays resident on a few SMs and its
   CTAs take requests from a work queue in mapped host memory, each running a
   whole circuit on a state held in shared memory.  The loop submits the

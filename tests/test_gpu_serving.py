@@ -51,7 +51,7 @@ def _wait(session, tickets, limit=20.0):
 
 @pytest.mark.parametrize("dt", [B.SV_C64, B.SV_C128])
 def test_session_results_match_oracle_and_packed_launch(svlib, cuda_dev, dt):
-    top = 13 if dt == B.SV_C64 else 12
+    top = 14 if dt == B.SV_C64 else 12  # 14 qubits: the 512-thread session kernel
     ns = [1, 3, 5, 7, 8, 9, 10, 11, 12, top, 6, top, 2, 12]
     sets = [random_circuit(n, 40, seed=300 + i, max_controls=min(2, n - 1) if n > 1 else 0,
                            max_unitary_k=min(4, n)) for i, n in enumerate(ns)]
@@ -103,7 +103,7 @@ def test_session_rejects_bad_requests(svlib, cuda_dev):
     s = B.SmallSession(B.SV_C64, capacity=4, wait_limit_s=10.0, n_ctas=1)
     try:
         with pytest.raises(B.SvError):
-            s.submit([14], [serving_circuit(14, 2, seed=1)])  # beyond 13 qubits
+            s.submit([15], [serving_circuit(15, 2, seed=1)])  # beyond 14 qubits
         with pytest.raises(B.SvError) as e:
             s.submit([8] * 5, [serving_circuit(8, 2, seed=k) for k in range(5)])  # more than its capacity
         assert e.value.status == 3  # SV_ERR_OOM

@@ -115,7 +115,7 @@ def test_admission_routing_and_accounting(fake_device, mode):
     assert srv._resident == 0  # every admitted state was released
     n19 = sum(1 for r in reqs if 8 * (1 << r.n) > budget)
     assert stats.rejected_by == {"over_budget": n19, "queue_full": 0} and stats.rejected == n19
-    assert srv.small_max_n == (13 if mode == "session" else 12)
+    assert srv.small_max_n == (14 if mode == "session" else 12)
     for r in reqs:
         if 8 * (1 << r.n) > budget:
             assert r.path == "rejected"
