@@ -401,9 +401,10 @@ sv_status sv_run_batch_small(int n_requests, sv_dtype dtype, const int* n_qubits
  * cudaFreeHost ...) waits for the resident kernel, that is until its CTAs
  * have found no work for wait_limit_s: keep the limit short (tens of
  * milliseconds) where such calls can happen while a session is live.
- * While a session is live, apply calls on the same device use the pass kernel
- * of 4 CTAs per SM (the TMA pass needs whole SMs).  A session belongs to the
- * device current at start; its calls are thread-safe. */
+ * While a session is live, the TMA pass of apply calls on the same device
+ * runs on the SMs the session's CTAs leave free, and loading a compiled pass
+ * kernel pauses the session around the load (sv_jit_set_mode).  A session
+ * belongs to the device current at start; its calls are thread-safe. */
 #define SV_SESSION_MAX_QUBITS 14
 typedef struct sv_small_session sv_small_session;
 /* capacity: requests in flight at most (1..2^20); arena_programs: pass
