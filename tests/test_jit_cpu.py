@@ -228,3 +228,27 @@ def test_compiled_pass_layouts_are_consistent(svlib):
         for p in src.split("// ----")[:ns]:
             copy_outs += _check_pass_layouts(p)
     assert copy_outs > 0
+
+
+def test_generator_store_and_coefficient_choices(svlib):
+    """A pass whose last register phase holds local bits 1..4 in registers
+    would store each 16-byte pair of a warp to 32 different lines: such passes
+    copy the tile out through shared memory instead.  Coefficients at offsets
+    known to the generator (rotations, 2x2 blocks, fixed phase tables) come
+    from the program in kernel-parameter space (`pc`); only tables whose row
+    depends on the thread or the tile read the shared-memory copy (`cf`)."""
+    n = 28
+    ns, _, src = B.sv_jit_check(n, B.SV_C64, fused_layered_u3_cz(n, 20, seed=0), fuse_max_k=5, compile=False)
+    passes = src.split("// ----")[:ns]
+    heavy = 0
+    for p in passes:
+        bits = [[int(x) for x in m.split()] for m in re.findall(r"register slots at local bits ([\d ]+)", p)]
+        if {1, 2, 3, 4} <= set(bits[-1]):
+            assert "the tile to the state" in p and "reg_store_global" not in p
+            heavy += 1
+        assert "r_rot<float, 5, " in p and "cf[" not in p  # rotations read pc[...]
+        for line in p.splitlines():
+            if "r_phase_table<" in line:
+                dependent = "tb >>" in line or "base >>" in line
+                assert ("(v, cf + " in line) == dependent and ("(v, pc + " in line) != dependent, line
+    assert heavy > 0
