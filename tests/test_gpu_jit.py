@@ -231,3 +231,33 @@ def test_threads_compiling_one_structure_at_once(svlib, cuda_dev):
     assert launches == passes * len(circs), (launches, passes)
     for st, g in zip(states, circs):
         assert maxabs(st.cpu().numpy(), oracle.run(n, g)) < TOL_C64
+
+
+def test_bench_circuit_30q_compiled_equals_interpreted(svlib, cuda_dev):
+    """At the size and launch configuration the bench times (30 qubits,
+    complex64, the 1180-gate layered circuit fused to k <= 5, 12-qubit tiles):
+    every compiled pass, with its copy-outs and shared-memory layouts, gives
+    the interpreting kernel's bits over the whole 2^30-amplitude state, and
+    the state keeps its norm."""
+    import torch
+    n = 30
+    gates = fused_layered_u3_cz(n, 20, seed=0)
+    _, passes, _ = B.sv_plan_info(n, B.SV_C64, gates, fuse_max_k=5)
+    states = []
+    for mode in (0, 2):
+        B.sv_jit_set_mode(mode)
+        try:
+            before = B.sv_jit_info()["launches"]
+            st = torch.empty(2 ** n, dtype=torch.complex64, device="cuda")
+            B.sv_init_basis(st, 0)
+            B.sv_apply_circuit(st, gates, fuse_max_k=5)
+            torch.cuda.current_stream().synchronize()
+            launches = B.sv_jit_info()["launches"] - before
+        finally:
+            B.sv_jit_set_mode(-1)
+        assert launches == (0 if mode == 0 else passes), (mode, launches, passes)
+        states.append(st)
+    a, b = (s.view(torch.int32) for s in states)
+    assert torch.equal(a, b)
+    norm = float(torch.linalg.vector_norm(states[1].view(torch.float32), dtype=torch.float64))
+    assert abs(norm - 1.0) < 1e-4
